@@ -1,0 +1,202 @@
+"""Seeded synthetic graph generators shared by the oracle tests, the GPU tests and bench.py.
+
+This package draws undirected edge lists and nothing else: it contains none of the motif-counting
+arithmetic.  The paper evaluates on social, web, biological and synthetic R-MAT graphs (Section IV-B,
+Table I); those datasets are not available here, so these generators stand in for the families:
+
+* Barabasi-Albert (social-like skew), R-MAT (a=0.57, b=0.19, c=0.19, d=0.05; social/synthetic skew),
+* Erdos-Renyi (unskewed control), random geometric 2-D (localised, low degree: the biological stand-in),
+* Chung-Lu power law (web-like heavy tail).
+
+All randomness is SplitMix64 implemented in ``graphgen.c`` so a seed yields the same bytes on x86-64
+and AArch64.  Edge lists may contain self-loops and duplicates (R-MAT, Chung-Lu); every consumer drops
+them when it builds its own adjacency.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphgen.c")
+_SO = os.path.join(_HERE, "_graphgen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile graphgen.c into a shared library next to it (host C only, no GPU code)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+            p32 = ctypes.POINTER(ctypes.c_int32)
+            lib.gg_ba.argtypes = [i64, i32, u64, p32, p32, i64]
+            lib.gg_er.argtypes = [i64, dbl, u64, p32, p32, i64]
+            lib.gg_rgg.argtypes = [i64, dbl, u64, p32, p32, i64]
+            lib.gg_rmat.argtypes = [i32, i64, dbl, dbl, dbl, u64, p32, p32, i64]
+            lib.gg_chung_lu.argtypes = [i64, dbl, dbl, dbl, u64, i64, i64, p32, p32, i64]
+            lib.gg_splitmix64_at.argtypes = [u64, u64, i64]
+            for f in (lib.gg_ba, lib.gg_er, lib.gg_rgg, lib.gg_rmat, lib.gg_chung_lu):
+                f.restype = i64
+            lib.gg_splitmix64_at.restype = u64
+            _lib = lib
+    return _lib
+
+
+@dataclass
+class Graph:
+    """An undirected edge list on vertex ids [0, n).  May hold duplicates and self-loops."""
+    n: int
+    src: np.ndarray  # int32[m_in]
+    dst: np.ndarray  # int32[m_in]
+    name: str = ""
+
+    @property
+    def m_in(self) -> int:
+        return int(self.src.shape[0])
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _call_growing(fn, args, cap: int):
+    while True:
+        src = np.empty(max(cap, 1), np.int32)
+        dst = np.empty(max(cap, 1), np.int32)
+        got = fn(*args, _p(src), _p(dst), cap)
+        if got >= 0:
+            return src[:got].copy(), dst[:got].copy()
+        cap = int(-got) + 16
+
+
+def splitmix64_at(seed: int, purpose: int, index: int) -> int:
+    return int(_load().gg_splitmix64_at(seed, purpose, index))
+
+
+def ba(n: int, m: int, seed: int) -> Graph:
+    """Barabasi-Albert graph, seed clique K_{m+1}, m edges per new vertex."""
+    k0 = min(n, m + 1)
+    cap = k0 * (k0 - 1) // 2 + max(0, n - k0) * m
+    src, dst = _call_growing(_load().gg_ba, (n, m, seed), cap)
+    return Graph(n, src, dst, f"ba(n={n},m={m},seed={seed})")
+
+
+def er(n: int, mean_degree: float, seed: int) -> Graph:
+    """Erdos-Renyi G(n, p) with p = k / (n - 1)."""
+    p = min(1.0, mean_degree / max(1, n - 1))
+    cap = int(n * mean_degree / 2 * 1.2) + 64
+    src, dst = _call_growing(_load().gg_er, (n, p, seed), cap)
+    return Graph(n, src, dst, f"er(n={n},k={mean_degree:g},seed={seed})")
+
+
+def rgg_radius(n: int, mean_degree: float) -> float:
+    """Radius giving expected degree k in the unit square, ignoring the boundary: pi r^2 (n-1) = k."""
+    return math.sqrt(mean_degree / (math.pi * max(1, n - 1)))
+
+
+def rgg(n: int, mean_degree: float, seed: int) -> Graph:
+    """Random geometric graph in the unit square (no torus), radius from the target mean degree."""
+    r = rgg_radius(n, mean_degree)
+    cap = int(n * mean_degree / 2 * 1.2) + 64
+    src, dst = _call_growing(_load().gg_rgg, (n, r, seed), cap)
+    return Graph(n, src, dst, f"rgg(n={n},k={mean_degree:g},seed={seed})")
+
+
+def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = 1) -> Graph:
+    """R-MAT with ef * 2^scale draws, then a seeded vertex permutation.  d = 1 - a - b - c."""
+    n = 1 << scale
+    src, dst = _call_growing(_load().gg_rmat, (scale, edge_factor, a, b, c, seed), edge_factor * n)
+    return Graph(n, src, dst, f"rmat(scale={scale},ef={edge_factor},seed={seed})")
+
+
+def chung_lu(n: int, gamma: float, max_weight: float, mean_degree: float, seed: int,
+             rows: tuple[int, int] | None = None) -> Graph:
+    """Chung-Lu power law with w_i = c (i + i0)^(-1/(gamma-1)).
+
+    c and i0 are fixed so that w_0 = max_weight and sum_i w_i ~= n * mean_degree (bisection on i0).
+    ``rows`` restricts sampling to pair rows [lo, hi) (for chunked generation of very large graphs).
+    """
+    ex = -1.0 / (gamma - 1.0)
+    target = n * mean_degree
+
+    def total(i0):
+        c = max_weight * i0 ** (-ex)
+        # integral approximation of sum_{i<n} (i+i0)^ex, plus the first term exactly
+        s = ((n - 1 + i0) ** (ex + 1) - i0 ** (ex + 1)) / (ex + 1) + i0 ** ex
+        return c * s
+
+    lo, hi = 1e-6, float(n)
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        if total(mid) > target:
+            hi = mid
+        else:
+            lo = mid
+    i0 = math.sqrt(lo * hi)
+    c = max_weight * i0 ** (-ex)
+    r0, r1 = rows if rows is not None else (0, n)
+    cap = int((r1 - r0) * mean_degree * 0.6) + 1024
+    src, dst = _call_growing(_load().gg_chung_lu, (n, gamma, c, i0, seed, r0, r1), cap)
+    return Graph(n, src, dst, f"chung_lu(n={n},gamma={gamma},seed={seed})")
+
+
+# ---------------------------------------------------------------------------------------------
+# The named workloads.
+# ---------------------------------------------------------------------------------------------
+
+def ba_2000() -> Graph:
+    """Plain single graph: Barabasi-Albert, n = 2,000, 4 edges per new vertex, seed 1 (~8k edges)."""
+    return ba(2000, 4, 1)
+
+
+def rmat_scale20() -> Graph:
+    """Plain single large skewed graph: R-MAT scale 20, edge factor 16, (0.57, 0.19, 0.19, 0.05), seed 1."""
+    return rmat(20, 16, 0.57, 0.19, 0.19, seed=1)
+
+
+@dataclass
+class BatchSpec:
+    seed: int
+    kind: str      # "er" | "ba" | "rgg"
+    n: int
+    k: float       # mean degree (er, rgg)
+    m: int         # edges per new vertex (ba)
+
+
+def batch_spec(seed: int, n_lo: int = 50, n_hi: int = 20000) -> BatchSpec:
+    """Batched workload member ``seed``: generator uniform over {ER, BA, RGG}; n log-uniform in
+    [n_lo, n_hi]; mean degree uniform in [4, 32] (ER, RGG); BA uses m uniform in {2..8}."""
+    draw = [splitmix64_at(seed, 99, i) for i in range(4)]
+    kind = ("er", "ba", "rgg")[draw[0] % 3]
+    u = (draw[1] >> 11) * (1.0 / 9007199254740992.0)
+    n = int(round(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo)))))
+    k = 4.0 + 28.0 * ((draw[2] >> 11) * (1.0 / 9007199254740992.0))
+    m = 2 + int(draw[3] % 7)
+    return BatchSpec(seed, kind, n, k, m)
+
+
+def batch_graph(seed: int, n_lo: int = 50, n_hi: int = 20000) -> Graph:
+    s = batch_spec(seed, n_lo, n_hi)
+    if s.kind == "er":
+        return er(s.n, s.k, 1000003 * seed + 17)
+    if s.kind == "ba":
+        return ba(s.n, min(s.m, max(1, s.n - 1)), 1000003 * seed + 17)
+    return rgg(s.n, s.k, 1000003 * seed + 17)
