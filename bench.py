@@ -1,0 +1,288 @@
+"""Benchmark: exact induced 4-motif counts, edges/s on one GB300 (and N replicas under torchrun).
+
+Workload (default): the plain single large skewed graph, R-MAT scale 20, edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 1, symmetrised with self-loops and duplicates removed
+(m = 15,702,112 undirected edges).  One step = one harp_count4 on the device-resident CSR: degree
+ordering + relabelled CSR, triangle / 4-clique anchors with per-edge t_e, wedge anchors (4-cycles),
+reduction and closure, counts copied to the host.  L2 is flushed (256 MiB write) between steps.
+
+`value` = m / (device time per step).  `e2e` = the same metric through the public API from pinned
+host edge lists: harp_build_csr (H2D + device CSR build) + harp_count4 (D2H of the counts) per step.
+`roofline` = the dominant kernel's algorithmic bytes (host work meter) / its CUDA-event time, against
+the measured HBM copy bandwidth.  `cpu_baseline` = the CPU oracle on a bounded R-MAT sample.
+
+--impl reference runs the CPU oracle (plain non-induced counts + containment inversion) on the host
+cores instead: each step counts an R-MAT scale-17 sample of the same family.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edges/s, exact induced 4-motif counts (batched vs plain, 1 GB300); % HBM peak"
+UNIT = "edges/s"
+SEGMENTS = ("orient", "tri_warp", "tri_cta_small", "tri_cta_large", "tri_fallback", "c4_small", "c4_mid",
+            "c4_window", "reduce")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample_rate(scale: int, threads: int = 0):
+    """Time the CPU oracle on an R-MAT sample in a fresh process (OpenMP on all host cores)."""
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import graphgen, oracle, os\n"
+        "g = graphgen.rmat(%d, 16, 0.57, 0.19, 0.19, seed=1)\n"
+        "m, _ = oracle.graph_summary(g.n, g.src, g.dst)\n"
+        "t = time.perf_counter(); c = oracle.count4_combo(g.n, g.src, g.dst, %d); t = time.perf_counter() - t\n"
+        "print(json.dumps({'m': m, 'seconds': t, 'cores': os.cpu_count()}))\n" % (ROOT, scale, threads))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    scale = 17
+    times, m = [], None
+    for _ in range(args.warmup):
+        oracle_sample_rate(scale)
+    for _ in range(args.steps):
+        r = oracle_sample_rate(scale)
+        times.append(r["seconds"])
+        m = r["m"]
+        cores = r["cores"]
+    t = sum(times) / len(times)
+    value = m / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "rmat(scale=17, ef=16, a=0.57, b=0.19, c=0.19, seed=1) sample of the "
+                                   "R-MAT scale-20 family", "graph_edges": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"R-MAT scale 17 (m={m}) per step, oracle count4_combo"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="harp", choices=("harp", "reference"))
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of the workload (20 = the bench config)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-meter", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    world, rank, local = dist_env()
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_2607_12074_gb300 import _build, harp, workmeter
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    harp.lib()
+
+    g = graphgen.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed=1)
+    src_d = torch.from_numpy(g.src).cuda()
+    dst_d = torch.from_numpy(g.dst).cuda()
+    stream = torch.cuda.current_stream()
+    csr = harp.harp_build_csr(g.n, src_d, dst_d, stream)
+    info = csr.info()
+    m = info["m"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    # ---- warm-up (also allocates and keeps the counting workspace)
+    for _ in range(args.warmup):
+        harp.harp_count4(csr)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, CUDA events on the launching stream, L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    harp.harp_set_profiling(True)
+    seg_ms = {k: [] for k in SEGMENTS}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = harp.harp_launch_count()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.fill_(k)
+            starts[k].record(stream)
+            counts = harp.harp_count4(csr)
+            ends[k].record(stream)
+            ms, _ = harp.harp_last_stage_times()
+            for name, v in zip(SEGMENTS, ms):
+                seg_ms[name].append(v)
+        torch.cuda.synchronize()
+    launches = harp.harp_launch_count() - launches0
+    harp.harp_set_profiling(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # ---- end to end through the public API from pinned host memory (build + count per step)
+    src_h = torch.from_numpy(g.src).pin_memory()
+    dst_h = torch.from_numpy(g.dst).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(k)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g2 = harp.harp_build_csr(g.n, src_h.numpy(), dst_h.numpy(), stream)
+        c2 = harp.harp_count4(g2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        g2.close()
+        if k >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+        assert np.array_equal(c2, counts)
+    t_e2e = sum(e2e_ms) / len(e2e_ms)
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = load_peaks()
+    seg_avg = {k: (sum(v) / len(v) if v else 0.0) for k, v in seg_ms.items()}
+    roofline = None
+    meter = None
+    if not args.no_meter:
+        meter = workmeter.meter(g.n, g.src, g.dst)
+        kernel_segments = [k for k in SEGMENTS if k != "orient"]
+        dom = max(kernel_segments, key=lambda k: seg_avg[k])
+        alg = meter[dom]["bytes"]
+        achieved = alg / (seg_avg[dom] / 1000) / 1e9
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tfile):
+            with open(tfile) as f:
+                traffic = json.load(f).get(dom)
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                    "algorithmic_bytes": alg, "kernel_ms": seg_avg[dom]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_sample_rate(18)
+        cpu = {"value": r["m"] / r["seconds"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": f"R-MAT scale 18 (same a,b,c, ef 16, seed 1; m={r['m']}), oracle count4_combo, "
+                         f"{r['seconds']:.1f} s"}
+    value = world * m / (t_step / 1000)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"rmat(scale={args.scale}, ef=16, a=0.57, b=0.19, c=0.19, seed=1), symmetrised, "
+                               f"self-loops and duplicates removed", "n": g.n, "m": m,
+                   "max_degree": info["max_degree"], "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "e2e": {"value": world * m / (t_e2e / 1000), "unit": UNIT, "h2d_bytes_per_step": 8 * g.m_in,
+                "d2h_bytes_per_step": 72, "ms_per_step": t_e2e},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "segments_ms": seg_avg,
+        "counts": [int(x) for x in counts],
+        "hbm_pct_alg": (100.0 * sum(meter[k]["bytes"] for k in SEGMENTS) / (t_step / 1000) / 1e9 / peak)
+        if meter else None,
+    }
+    print(json.dumps(line), flush=True)
+    csr.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * harp.h - C ABI of libharp: exact connected induced 4-vertex motif counts on one GB300 (sm_103a).
+ *
+ * Method: HARP-ME (Kumar, Nasre; arXiv 2607.12074).  An anchor basis is enumerated explicitly over a
+ * degree-ordered CSR (Section III-A/B: triangles with per-edge triangle statistics, their 4-clique
+ * extensions, and ordered wedges), driven by sorted-adjacency set intersections (Section III-D), and
+ * the six induced counts follow from exact closure relations (Section III-F).
+ *
+ * Counts (uint64, exact; arithmetic is modulo 2^64 and every result is exact whenever the true
+ * count is below 2^64) are always reported in this order:
+ *   [0] 3-star  [1] 4-path  [2] tailed triangle (paw)  [3] 4-cycle  [4] diamond  [5] 4-clique
+ * An occurrence is a 4-vertex subset S whose induced subgraph G[S] is connected and isomorphic to the
+ * motif (Section II); subsets are counted, not embeddings.
+ *
+ * Conventions for every entry point:
+ *   - No exceptions cross this boundary; every call returns a harp_status.
+ *   - Output arguments are written only when the call returns HARP_OK.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Graphs are simple and undirected.  Input edge lists may list an edge once or twice, may hold
+ *     duplicates and self-loops; duplicates and self-loops are dropped.  Vertex ids are int32 in
+ *     [0, n), n <= 2^31 - 1.  Any id outside [0, n) makes the call fail with HARP_EINVAL.
+ *   - Device memory owned by the library is allocated with the stream-ordered allocator on the
+ *     current device; handles are tied to the device that was current when they were created.
+ */
+#ifndef HARP_H
+#define HARP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HARP_ABI_VERSION 1u
+
+typedef enum harp_status {
+    HARP_OK = 0,
+    HARP_EINVAL = 1,     /* bad argument: NULL pointer, negative size, vertex id out of range      */
+    HARP_ENOMEM = 2,     /* device or host allocation failed, or a request exceeds a memory budget */
+    HARP_ECUDA = 3,      /* a CUDA runtime call failed; harp_last_cuda_error() gives the code      */
+    HARP_EOVERFLOW = 4,  /* a size does not fit the index types (e.g. more than 2^31-1 vertices)   */
+    HARP_EAGAIN = 5,     /* not finished yet / queue full: call again                               */
+    HARP_ETIMEOUT = 6,   /* a bounded device-side wait ran out; the context stays usable            */
+    HARP_ENOTFOUND = 7,  /* unknown ticket or handle                                                */
+    HARP_EDEVICE = 8     /* a device-side consistency check failed (the kernel skipped the access)  */
+} harp_status;
+
+/* where the pointers passed to harp_build_csr live */
+#define HARP_PTR_HOST 0u
+#define HARP_PTR_DEVICE 1u
+
+enum {
+    HARP_STAR3 = 0, HARP_PATH4 = 1, HARP_PAW = 2, HARP_CYCLE4 = 3, HARP_DIAMOND = 4, HARP_CLIQUE4 = 5
+};
+
+/* Intermediate anchor statistics (non-induced pattern counts, modulo 2^64), as reported by
+ * harp_count4_stats.  The closure of Section III-F maps these to the six induced counts. */
+enum {
+    HARP_STAT_TRIANGLES = 0,   /* T = number of triangles                                     */
+    HARP_STAT_K4 = 1,          /* 4-cliques                                                    */
+    HARP_STAT_C4 = 2,          /* 4-cycles as (not necessarily induced) subgraphs              */
+    HARP_STAT_STARS = 3,       /* sum_v C(d_v, 3)                                              */
+    HARP_STAT_PATHS = 4,       /* 3-edge paths: sum_e (d_u - 1)(d_v - 1) - 3T                  */
+    HARP_STAT_PAWS = 5,        /* triangle + pendant edge: sum over triangles (sum of d - 6)   */
+    HARP_STAT_DIAMONDS = 6,    /* two triangles sharing an edge: sum_e C(t_e, 2)               */
+    HARP_STAT_EDGES = 7,       /* m, undirected simple edges                                   */
+    HARP_NSTATS = 8
+};
+
+/* ------------------------------------------------------------------------------------------------
+ * Graph handle (Section II: G = (V, E) simple undirected; Section III-D: sorted CSR adjacency).
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct harp_csr harp_csr;
+
+/* Build a device-resident symmetric CSR (int64 offsets[n+1], int32 cols[2m], every row sorted
+ * ascending, no self-loops, no duplicates) from an undirected edge list of m_in pairs.
+ *   n        number of vertices (ids [0, n)); 0 <= n <= 2^31 - 1
+ *   m_in     number of input pairs (src[i], dst[i]); 0 <= m_in <= 2^31 - 1
+ *   src,dst  int32[m_in]; host memory if flags == HARP_PTR_HOST, device memory if HARP_PTR_DEVICE.
+ *            Read only; the caller keeps ownership.  Host arrays are copied in on `stream`.
+ *   stream   cudaStream_t (as void*) for all work of this call; the call returns after the stream
+ *            has finished it (it reads the deduplicated edge count back to size the result).
+ *   out      receives a new handle owning its device memory; free it with harp_csr_free.
+ * Errors: HARP_EINVAL (NULL pointers with m_in > 0, negative sizes, an id outside [0, n)),
+ * HARP_EOVERFLOW (n or m_in above 2^31 - 1), HARP_ENOMEM, HARP_ECUDA. */
+harp_status harp_build_csr(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                           uint32_t flags, void* stream, harp_csr** out);
+
+/* Release a handle and all device memory it owns (stream-ordered on the handle's stream).
+ * NULL is accepted and ignored. */
+void harp_csr_free(harp_csr* g);
+
+/* Summary of a handle: n, m (undirected simple edges), maximum degree, device bytes held (CSR plus
+ * cached counting workspace).  Any output pointer may be NULL. */
+harp_status harp_csr_info(const harp_csr* g, int64_t* n, int64_t* m_undirected, int64_t* max_degree,
+                          size_t* device_bytes);
+
+/* Device pointers of the CSR arrays (owned by the handle, valid until harp_csr_free):
+ * offsets int64[n+1], cols int32[2m]. */
+harp_status harp_csr_arrays(const harp_csr* g, const int64_t** offsets, const int32_t** cols);
+
+/* ------------------------------------------------------------------------------------------------
+ * Anchor plan (Section III-A, Eq. 1; Section III-B).  A plan chooses which exact anchor basis is
+ * enumerated and how (intersection variant, warp-local vs CTA thresholds, cache sizes).  A plan
+ * never changes the counts, only the work.  All-zero fields mean "library default".
+ * ---------------------------------------------------------------------------------------------- */
+#define HARP_BASIS_TRIANGLE_WEDGE 0u  /* triangles + per-edge t_e + 4-clique extension + wedges  */
+
+#define HARP_PROBE_HASH 1u     /* frontier membership by a shared-memory hash of N+(u)             */
+#define HARP_PROBE_BSEARCH 2u  /* frontier membership by binary search in the sorted N+(u)         */
+
+#define HARP_PLAN_NO_GRAPH 1u  /* flags: launch kernels one by one instead of a captured CUDA graph */
+
+typedef struct harp_plan {
+    uint32_t version;            /* HARP_ABI_VERSION                                               */
+    uint32_t basis;              /* HARP_BASIS_*                                                   */
+    uint32_t tri_probe;          /* HARP_PROBE_* for the triangle / 4-clique anchor                */
+    uint32_t tri_warp_max;       /* out-degree <= this (<= 32): warp-local mode; above: CTA mode   */
+    uint32_t c4_warp_max_work;   /* wedge work W(u) <= this: warp-local hash table                 */
+    uint32_t c4_cta_max_work;    /* W(u) <= this: CTA hash table; above: CTA windowed counters     */
+    uint32_t c4_window_bytes;    /* shared-memory bytes of one dense counter window                */
+    uint32_t flags;              /* HARP_PLAN_*                                                    */
+    /* Eq. 1 terms estimated from a sample of the graph (filled by harp_select_anchors) */
+    double est_enum;             /* explicit anchor-enumeration work (wedges + 2-paths)            */
+    double est_inter;            /* set-intersection probes                                        */
+    double est_halo;             /* halo replication under the current memory budget (1 = none)    */
+    double est_reuse;            /* fraction of frontier reads expected to repeat (reuse)          */
+    double est_yield;            /* closure yield: induced counts recoverable from the statistics */
+    double objective;            /* value of the Eq. 1 objective for the chosen basis              */
+} harp_plan;
+
+typedef struct harp_select_opts {
+    uint64_t sample_vertices;    /* vertices sampled for the estimates (0 = 4096)                  */
+    uint64_t seed;               /* sampling seed                                                  */
+    uint64_t memory_budget;      /* bytes; 0 = free device memory.  Feeds the halo term.           */
+    double lambda_inter, lambda_halo, lambda_reuse, lambda_yield;  /* 0 = normalised defaults     */
+} harp_select_opts;
+
+/* Fill *out with the plan chosen by the Eq. 1 objective for this graph.  opts may be NULL. */
+harp_status harp_select_anchors(const harp_csr* g, const harp_select_opts* opts, harp_plan* out);
+
+/* ------------------------------------------------------------------------------------------------
+ * Counting (the hot path).
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Count the six induced motifs of g.  plan may be NULL (library default plan).  Runs on the
+ * handle's stream and returns after the counts are on the host in counts_out[6]. */
+harp_status harp_count4(const harp_csr* g, const harp_plan* plan, uint64_t counts_out[6]);
+
+/* As harp_count4, and also return the anchor statistics (HARP_STAT_* order) in stats_out[8]. */
+harp_status harp_count4_stats(const harp_csr* g, const harp_plan* plan, uint64_t counts_out[6],
+                              uint64_t stats_out[8]);
+
+/* Asynchronous form: enqueue the whole count on `stream` and return.  d_out is DEVICE memory of at
+ * least 16 uint64: [0..5] the counts, [6..7] reserved, [8..15] the statistics.  It is written when
+ * the stream reaches that point.  The handle's workspace is in use until then: do not start
+ * another count on the same handle on a different stream before it completes. */
+harp_status harp_count4_async(const harp_csr* g, const harp_plan* plan, uint64_t* d_out, void* stream);
+
+/* Per-segment device times of the last count issued with profiling on (milliseconds, measured with
+ * CUDA events recorded on the launching stream between the kernels).  Segments, in launch order:
+ *   0 orientation (degree ranking, relabelled sorted CSR, out-CSR)
+ *   1 triangle anchors, warp-local mode      2 triangle anchors, CTA mode (out-degree <= 256)
+ *   3 triangle anchors, CTA mode (<= 1024)   4 triangle anchors, fallback (out-degree > 1024)
+ *   5 wedge anchors, warp-local mode (+ work estimate of every root)
+ *   6 wedge anchors, CTA hash mode           7 wedge anchors, windowed CTA mode
+ *   8 reduction + closure
+ * Call harp_set_profiling(1) first; the values are those of the last completed count.
+ * launches_out receives the number of kernels the library launched in that count. */
+#define HARP_NSEGMENTS 9
+harp_status harp_set_profiling(int enable);
+harp_status harp_last_stage_times(float ms_out[HARP_NSEGMENTS], int64_t* launches_out);
+
+/* Total number of kernels the library has launched in this process. */
+int64_t harp_launch_count(void);
+
+/* ------------------------------------------------------------------------------------------------
+ * Errors.
+ * ---------------------------------------------------------------------------------------------- */
+const char* harp_status_str(harp_status s);
+/* The last CUDA error code seen by this thread inside the library (0 if none) and its name. */
+int harp_last_cuda_error(void);
+const char* harp_last_cuda_error_str(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HARP_H */

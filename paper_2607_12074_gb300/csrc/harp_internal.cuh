@@ -1,0 +1,224 @@
+// Internal declarations shared by the libharp translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "harp.h"
+
+// ---------------------------------------------------------------------------------------------
+// Error plumbing: every CUDA call is checked; the first failure is recorded per thread and the
+// public entry point returns HARP_ECUDA.  No exceptions are used anywhere in the library.
+// ---------------------------------------------------------------------------------------------
+namespace harp {
+
+void record_cuda_error(cudaError_t e);
+void note_launch(int64_t k = 1);   // counts kernel launches (harp_launch_count)
+// Profiling: records an event closing segment `seg` (0..HARP_NSEGMENTS-1) on stream s when enabled.
+enum : int { SEG_ORIENT = 0, SEG_TRI_WARP, SEG_TRI_CTA_S, SEG_TRI_CTA_L, SEG_TRI_FALLBACK, SEG_C4_SMALL,
+             SEG_C4_MID, SEG_C4_WINDOW, SEG_REDUCE };
+cudaError_t prof_mark(cudaStream_t s, int seg);
+
+#define HARP_CK(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            ::harp::record_cuda_error(e_);             \
+            return HARP_ECUDA;                         \
+        }                                              \
+    } while (0)
+
+#define HARP_TRY(call)                                 \
+    do {                                               \
+        harp_status s_ = (call);                       \
+        if (s_ != HARP_OK) return s_;                  \
+    } while (0)
+
+// after a <<<>>> launch
+#define HARP_LAUNCHED()                                \
+    do {                                               \
+        ::harp::note_launch();                         \
+        cudaError_t e_ = cudaGetLastError();           \
+        if (e_ != cudaSuccess) {                       \
+            ::harp::record_cuda_error(e_);             \
+            return HARP_ECUDA;                         \
+        }                                              \
+    } while (0)
+
+constexpr int kWarp = 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Slots of the device statistics / output vector (uint64[kOutLen]).
+enum : int {
+    OUT_COUNTS = 0,        // [0..5] induced counts
+    OUT_STATS = 8,         // [8..15] HARP_STAT_* order
+    ACC_T = 16,            // raw accumulators written by the kernels
+    ACC_K4 = 17,
+    ACC_C4 = 18,
+    ACC_S = 19,            // sum_v C(d,3)
+    ACC_PW = 20,           // sum_e (d_u-1)(d_v-1)
+    ACC_PAWSUM = 21,       // sum over triangles of (d_a + d_b + d_c)
+    ACC_D = 22,            // sum_e C(t_e, 2)
+    ACC_M = 23,            // m
+    ACC_ERR = 24,          // device-side consistency flags (0 = fine)
+    ACC_DONE = 25,         // last-block counter of the reduction kernel
+    Q_TRI_WARP = 26,       // queue lengths
+    Q_TRI_CTA = 27,
+    Q_C4_MID = 28,
+    Q_C4_WIN = 29,
+    T_TRI_S = 30,          // work tickets of persistent kernels
+    T_TRI_L = 31,
+    T_TRI_F = 32,
+    T_C4_MID = 33,
+    T_C4_WIN = 34,
+    W_TOTAL = 35,          // total window items of the windowed wedge kernel
+    kOutLen = 40
+};
+
+// ---------------------------------------------------------------------------------------------
+// Workspace for one counting pass, sized for (n, m) and cached in the graph handle.
+// ---------------------------------------------------------------------------------------------
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+    int64_t n = -1, m = -1;
+    int32_t* deg = nullptr;        // [n]   degree in rank order
+    int32_t* order = nullptr;      // [n]   new id -> old id
+    int32_t* perm = nullptr;       // [n]   old id -> new id
+    uint64_t* vkeys = nullptr;     // [n]   vertex sort keys
+    uint64_t* vkeys_alt = nullptr; // [n]
+    uint32_t* hist = nullptr;      // radix histograms
+    size_t hist_len = 0;
+    int64_t* off = nullptr;        // [n+1] rank-order CSR offsets
+    int32_t* cols = nullptr;       // [2m]  rank-order CSR columns, rows ascending
+    int32_t* dplus = nullptr;      // [n]   out-degree (neighbours with larger rank)
+    int64_t* offp = nullptr;       // [n+1] out-CSR offsets
+    int32_t* colsp = nullptr;      // [m]   out-CSR columns
+    uint32_t* te = nullptr;        // [m]   per out-arc triangle count t_e (colsp and te are contiguous)
+    int32_t* q_tri = nullptr;      // [n]   CTA-mode triangle anchors
+    int32_t* q_mid = nullptr;      // [n]   CTA-hash wedge roots
+    int32_t* q_win = nullptr;      // [n]   windowed wedge roots
+    int64_t* win_prefix = nullptr; // [n+1] window-item prefix over q_win
+    int64_t* scan_tmp = nullptr;   // scan partials
+    size_t scan_tmp_len = 0;
+    uint64_t* acc = nullptr;       // [kOutLen]
+};
+
+// stream-ordered allocation helpers
+harp_status ws_ensure(Workspace& ws, int64_t n, int64_t m, cudaStream_t s);
+void ws_release(Workspace& ws, cudaStream_t s);
+
+}  // namespace harp
+
+struct harp_csr {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0, m = 0, max_deg = 0;
+    int64_t* off = nullptr;   // [n+1]
+    int32_t* cols = nullptr;  // [2m]
+    size_t csr_bytes = 0;
+    harp::Workspace ws;
+};
+
+namespace harp {
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers (one translation unit each).
+// ---------------------------------------------------------------------------------------------
+
+// scan.cu: out[i] = sum_{j<i} in[j] for i in [0, n]; out has n + 1 entries.
+harp_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* tmp,
+                                      size_t tmp_len, cudaStream_t s);
+harp_status exclusive_scan_u32_inplace(uint32_t* data, int64_t n, int64_t* tmp, size_t tmp_len,
+                                       cudaStream_t s);
+size_t scan_tmp_needed(int64_t n);
+
+// sort.cu: LSD radix sort of 64-bit keys on bits [begin_bit, end_bit); result ends in *keys
+// (the pointer may be swapped with *alt).  hist needs radix_hist_len(n) entries.
+harp_status radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t n, int begin_bit, int end_bit,
+                           uint32_t* hist, int64_t* tmp, size_t tmp_len, cudaStream_t s);
+size_t radix_hist_len(int64_t n);
+
+// csr.cu
+harp_status build_csr_device(harp_csr* g, int64_t n, int64_t m_in, const int32_t* d_src,
+                             const int32_t* d_dst, cudaStream_t s);
+
+// orient.cu: degree ordering + relabelled sorted CSR + out-CSR (step a1)
+harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s);
+
+// tri.cu: triangle + per-edge t_e + 4-clique anchor (steps a3, a4)
+harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s);
+
+// c4.cu: wedge anchor, non-induced 4-cycles (step a5)
+harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s);
+
+// reduce.cu: sum_e C(t_e,2), closure (step a7); writes acc[OUT_COUNTS..], acc[OUT_STATS..]
+harp_status reduce_and_close(const harp_csr* g, Workspace& ws, cudaStream_t s);
+
+// planner.cpp
+void default_plan(harp_plan* p);
+void normalise_plan(const harp_plan* in, harp_plan* out);
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Block-wide sum of a uint64 (all threads participate; result valid in thread 0).
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t* smem32) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) smem32[w] = v;
+    __syncthreads();
+    uint64_t r = 0;
+    if (threadIdx.x < 32) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = (threadIdx.x < nw) ? smem32[threadIdx.x] : 0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// lower_bound in a sorted int32 array a[0..len): first index with a[i] >= key
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t len, int32_t key) {
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) { return x * 0x9E3779B1u; }
+
+// C(x, 2) and C(x, 3) exactly modulo 2^64 (the divisor is removed from a factor first)
+__device__ __forceinline__ uint64_t choose2_u64(uint64_t x) {
+    if (x < 2) return 0;
+    uint64_t a = x, b = x - 1;
+    if ((a & 1) == 0) a >>= 1; else b >>= 1;
+    return a * b;
+}
+__device__ __forceinline__ uint64_t choose3_u64(uint64_t x) {
+    if (x < 3) return 0;
+    uint64_t f0 = x, f1 = x - 1, f2 = x - 2;
+    if (f0 % 3 == 0) f0 /= 3; else if (f1 % 3 == 0) f1 /= 3; else f2 /= 3;
+    if ((f0 & 1) == 0) f0 >>= 1; else if ((f1 & 1) == 0) f1 >>= 1; else f2 >>= 1;
+    return f0 * f1 * f2;
+}
+
+}  // namespace harp

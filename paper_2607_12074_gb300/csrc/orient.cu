@@ -1,0 +1,341 @@
+// Step a1: degree ordering and orientation (Section III-D, "sorted CSR adjacency and canonical
+// ordering constraints").
+//
+// Vertices are renumbered by rank(v) = (d(v), v) ascending, so that in the new numbering
+//   * N+(v) = neighbours ranked above v = the suffix of v's sorted row after v itself,
+//   * N-(v) = neighbours ranked below v = the prefix of the row,
+//   * the neighbours of w ranked below u form a prefix of w's row (the ordered wedges of the
+//     4-cycle anchor, Section III-B, read contiguous memory).
+// Output (workspace): deg, order (new -> old), perm (old -> new), off/cols (relabelled CSR with
+// every row sorted), dplus, offp/colsp (out-CSR: only N+), te zeroed, S = sum_v C(d_v, 3).
+//
+// Rows are sorted by three kernels chosen by degree (rank order makes the tiers contiguous id
+// ranges): a warp bitonic network for d <= 32, a shared-memory bitonic sort for d <= 4096, and a
+// per-row LSD radix sort through global memory for hubs.
+#include "harp_internal.cuh"
+
+namespace harp {
+namespace {
+
+constexpr int kTierA = 32;
+constexpr int kTierB = 4096;
+
+int bits_for(int64_t x) {
+    int b = 0;
+    while (b < 63 && ((int64_t)1 << b) <= x) ++b;
+    return b < 1 ? 1 : b;
+}
+
+unsigned grid_for(int64_t work, int threads, int64_t cap = 152 * 64) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+__global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b,
+                              uint64_t* __restrict__ keys, uint64_t* __restrict__ acc) {
+    uint64_t s3 = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+        keys[v] = (d << b) | (uint64_t)v;
+        s3 += choose3_u64(d);
+    }
+    __shared__ uint64_t red[32];
+    uint64_t t = block_sum_u64(s3, red);
+    if (threadIdx.x == 0 && t) atomicAdd((unsigned long long*)&acc[ACC_S], (unsigned long long)t);
+}
+
+__global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t n, int b, int32_t* __restrict__ order,
+                          int32_t* __restrict__ perm, int32_t* __restrict__ deg) {
+    const uint64_t mask = ((uint64_t)1 << b) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        int32_t old = (int32_t)(k & mask);
+        order[i] = old;
+        perm[old] = (int32_t)i;
+        deg[i] = (int32_t)(k >> b);
+    }
+}
+
+// first index in [0, n) with deg[i] > t (deg is non-decreasing in rank order)
+__device__ __forceinline__ int64_t first_above(const int32_t* __restrict__ deg, int64_t n, int32_t t) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (deg[mid] <= t) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Tier A: rows with 1 <= d <= 32, one warp per row, bitonic network in registers.
+__global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restrict__ goff,
+                                                        const int32_t* __restrict__ gcols,
+                                                        const int32_t* __restrict__ order,
+                                                        const int32_t* __restrict__ perm,
+                                                        const int32_t* __restrict__ deg,
+                                                        const int64_t* __restrict__ off, int64_t n,
+                                                        int32_t* __restrict__ cols,
+                                                        int32_t* __restrict__ dplus) {
+    __shared__ int64_t range[2];
+    if (threadIdx.x == 0) {
+        range[0] = first_above(deg, n, 0);
+        range[1] = first_above(deg, n, kTierA);
+    }
+    __syncthreads();
+    const int64_t lo = range[0], hi = range[1];
+    const int l = lane_id();
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = lo + wid; i < hi; i += nw) {
+        const int d = deg[i];
+        const int64_t src = goff[order[i]];
+        int32_t v = (l < d) ? perm[gcols[src + l]] : 0x7fffffff;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                int32_t o = __shfl_xor_sync(kFull, v, j);
+                bool up = (l & k) == 0;
+                bool lower = (l & j) == 0;
+                v = (lower == up) ? min(v, o) : max(v, o);
+            }
+        }
+        if (l < d) cols[off[i] + l] = v;
+        uint32_t above = __ballot_sync(kFull, l < d && v > (int32_t)i);
+        if (l == 0) dplus[i] = __popc(above);
+    }
+    // rows with d == 0 (a prefix of the rank order)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lo;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dplus[i] = 0;
+}
+
+// Tier B: 32 < d <= 4096, one block per row, bitonic sort in shared memory.
+__global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restrict__ goff,
+                                                         const int32_t* __restrict__ gcols,
+                                                         const int32_t* __restrict__ order,
+                                                         const int32_t* __restrict__ perm,
+                                                         const int32_t* __restrict__ deg,
+                                                         const int64_t* __restrict__ off, int64_t n,
+                                                         int32_t* __restrict__ cols,
+                                                         int32_t* __restrict__ dplus) {
+    __shared__ int32_t buf[kTierB];
+    __shared__ int64_t range[2];
+    __shared__ int cnt_below;
+    if (threadIdx.x == 0) {
+        range[0] = first_above(deg, n, kTierA);
+        range[1] = first_above(deg, n, kTierB);
+    }
+    __syncthreads();
+    const int64_t lo = range[0], hi = range[1];
+    for (int64_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
+        const int d = deg[i];
+        int P = 64;
+        while (P < d) P <<= 1;
+        const int64_t src = goff[order[i]];
+        for (int k = threadIdx.x; k < P; k += blockDim.x) buf[k] = (k < d) ? perm[gcols[src + k]] : 0x7fffffff;
+        if (threadIdx.x == 0) cnt_below = 0;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                    int a = 2 * t - (t & (j - 1));  // index with bit j clear
+                    int c = a + j;
+                    bool up = (a & k) == 0;
+                    int32_t x = buf[a], y = buf[c];
+                    if ((x > y) == up) {
+                        buf[a] = y;
+                        buf[c] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        int below = 0;
+        for (int k = threadIdx.x; k < d; k += blockDim.x) {
+            int32_t x = buf[k];
+            cols[off[i] + k] = x;
+            below += x < (int32_t)i;
+        }
+        below = warp_sum(below);
+        if (lane_id() == 0 && below) atomicAdd(&cnt_below, below);
+        __syncthreads();
+        if (threadIdx.x == 0) dplus[i] = d - cnt_below;
+        __syncthreads();
+    }
+}
+
+// Tier C: hubs (d > 4096), one block per row, LSD radix sort (8-bit digits) through global memory.
+// Pass p reads the previous pass's output; pass 0 reads the old row through perm.  The pass count
+// decides which buffer each pass writes so that the last one lands in `cols`.
+constexpr int kHubThreads = 512;
+constexpr int kHubWarps = kHubThreads / 32;
+
+__global__ void __launch_bounds__(kHubThreads) k_sort_rows_hub(const int64_t* __restrict__ goff,
+                                                               const int32_t* __restrict__ gcols,
+                                                               const int32_t* __restrict__ order,
+                                                               const int32_t* __restrict__ perm,
+                                                               const int32_t* __restrict__ deg,
+                                                               const int64_t* __restrict__ off, int64_t n,
+                                                               int nbits, int32_t* __restrict__ cols,
+                                                               int32_t* __restrict__ tmp,
+                                                               int32_t* __restrict__ dplus) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[kHubWarps][256];
+    __shared__ int64_t range[2];
+    __shared__ int cnt_below;
+    if (threadIdx.x == 0) {
+        range[0] = first_above(deg, n, kTierB);
+        range[1] = n;
+    }
+    __syncthreads();
+    const int64_t lo = range[0], hi = range[1];
+    const int npass = (nbits + 7) / 8;
+    const int w = threadIdx.x >> 5, l = lane_id();
+    const uint32_t lt = lanemask_lt();
+    for (int64_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
+        const int64_t d = deg[i];
+        const int64_t src = goff[order[i]];
+        const int64_t dst0 = off[i];
+        for (int p = 0; p < npass; ++p) {
+            const int shift = 8 * p;
+            const bool to_cols = ((npass - 1 - p) & 1) == 0;
+            int32_t* out = (to_cols ? cols : tmp) + dst0;
+            const int32_t* in = (p == 0) ? nullptr : ((to_cols ? tmp : cols) + dst0);
+            // histogram of the row
+            for (int k = threadIdx.x; k < 256; k += blockDim.x) base[k] = 0;
+            __syncthreads();
+            for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
+                int32_t x = in ? in[k] : perm[gcols[src + k]];
+                atomicAdd(&base[((uint32_t)x >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {  // exclusive scan of 256 counters by one warp
+                uint32_t c[8], s = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { c[q] = base[threadIdx.x * 8 + q]; s += c[q]; }
+                uint32_t inc = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t u = __shfl_up_sync(kFull, inc, o);
+                    if (threadIdx.x >= o) inc += u;
+                }
+                uint32_t run = inc - s;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { base[threadIdx.x * 8 + q] = run; run += c[q]; }
+            }
+            __syncthreads();
+            // stable scatter, tile by tile (tile = kHubThreads keys, warp-contiguous)
+            for (int64_t t0 = 0; t0 < d; t0 += kHubThreads) {
+                for (int k = threadIdx.x; k < kHubWarps * 256; k += blockDim.x) (&wcnt[0][0])[k] = 0;
+                __syncthreads();
+                const int64_t k = t0 + w * 32 + l;
+                const bool valid = k < d;
+                int32_t x = 0;
+                if (valid) x = in ? in[k] : perm[gcols[src + k]];
+                const uint32_t dg = valid ? (((uint32_t)x >> shift) & 255u) : 256u;
+                const uint32_t peers = __match_any_sync(kFull, dg);
+                const uint32_t r = __popc(peers & lt);
+                if (valid && r == 0) wcnt[w][dg] = __popc(peers);
+                __syncthreads();
+                if (threadIdx.x < 256) {  // exclusive over warps, add the running digit base
+                    uint32_t run = base[threadIdx.x];
+                    for (int ww = 0; ww < kHubWarps; ++ww) {
+                        uint32_t c = wcnt[ww][threadIdx.x];
+                        wcnt[ww][threadIdx.x] = run;
+                        run += c;
+                    }
+                    base[threadIdx.x] = run;
+                }
+                __syncthreads();
+                if (valid) out[wcnt[w][dg] + r] = x;
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+        // out-degree: elements above i in the sorted row
+        if (threadIdx.x == 0) cnt_below = 0;
+        __syncthreads();
+        int below = 0;
+        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) below += cols[dst0 + k] < (int32_t)i;
+        below = warp_sum(below);
+        if (l == 0 && below) atomicAdd(&cnt_below, below);
+        __syncthreads();
+        if (threadIdx.x == 0) dplus[i] = (int32_t)(d - cnt_below);
+        __syncthreads();
+    }
+}
+
+// colsp[offp[i] + k] = the k-th neighbour of i ranked above i (the row suffix), one warp per row.
+// The same pass accumulates sum over edges of (d_u - 1)(d_v - 1) (3-edge paths + 3T).
+__global__ void __launch_bounds__(256) k_out_csr(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                                                 const int32_t* __restrict__ dplus,
+                                                 const int32_t* __restrict__ deg,
+                                                 const int64_t* __restrict__ offp, int64_t n,
+                                                 int32_t* __restrict__ colsp, uint64_t* __restrict__ acc) {
+    __shared__ uint64_t red[32];
+    const int l = lane_id();
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t pw = 0;
+    for (int64_t i = wid; i < n; i += nw) {
+        const int64_t dp = dplus[i];
+        if (dp == 0) continue;
+        const int64_t srcb = off[i + 1] - dp;
+        const int64_t dstb = offp[i];
+        const uint64_t di1 = (uint64_t)deg[i] - 1;
+        for (int64_t k = l; k < dp; k += 32) {
+            const int32_t v = cols[srcb + k];
+            colsp[dstb + k] = v;
+            pw += di1 * ((uint64_t)deg[v] - 1);
+        }
+    }
+    pw = block_sum_u64(pw, red);
+    if (threadIdx.x == 0 && pw) atomicAdd((unsigned long long*)&acc[ACC_PW], (unsigned long long)pw);
+}
+
+}  // namespace
+
+harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
+    const int64_t n = g->n, m = g->m;
+    if (n == 0) return HARP_OK;
+    const int b = bits_for(n);
+    const int bd = bits_for(g->max_deg);
+
+    k_vertex_keys<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, b, ws.vkeys, ws.acc);
+    HARP_LAUNCHED();
+    uint64_t* k0 = ws.vkeys;
+    uint64_t* k1 = ws.vkeys_alt;
+    HARP_TRY(radix_sort_u64(&k0, &k1, n, 0, b + bd, ws.hist, ws.scan_tmp, ws.scan_tmp_len, s));
+    k_relabel<<<grid_for(n, 256), 256, 0, s>>>(k0, n, b, ws.order, ws.perm, ws.deg);
+    HARP_LAUNCHED();
+    HARP_TRY(exclusive_scan_i32_to_i64(ws.deg, ws.off, n, ws.scan_tmp, ws.scan_tmp_len, s));
+    if (m > 0) {
+        k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
+                                                                ws.off, n, ws.cols, ws.dplus);
+        HARP_LAUNCHED();
+        k_sort_rows_block<<<152 * 4, 512, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n,
+                                                   ws.cols, ws.dplus);
+        HARP_LAUNCHED();
+        // the out-CSR columns + t_e region (2m int32) is free until k_out_csr: hub sort ping-pong
+        k_sort_rows_hub<<<152, kHubThreads, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n, b,
+                                                     ws.cols, ws.colsp, ws.dplus);
+        HARP_LAUNCHED();
+    } else {
+        HARP_CK(cudaMemsetAsync(ws.dplus, 0, (size_t)n * sizeof(int32_t), s));
+    }
+    HARP_TRY(exclusive_scan_i32_to_i64(ws.dplus, ws.offp, n, ws.scan_tmp, ws.scan_tmp_len, s));
+    if (m > 0) {
+        k_out_csr<<<grid_for(n * 32, 256), 256, 0, s>>>(ws.off, ws.cols, ws.dplus, ws.deg, ws.offp, n, ws.colsp,
+                                                         ws.acc);
+        HARP_LAUNCHED();
+        HARP_CK(cudaMemsetAsync(ws.te, 0, (size_t)m * sizeof(uint32_t), s));
+    }
+    return HARP_OK;
+}
+
+}  // namespace harp

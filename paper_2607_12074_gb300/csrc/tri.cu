@@ -1,0 +1,401 @@
+// Steps a3 + a4: triangle anchors with per-edge triangle statistics, and their 4-clique extension
+// (Section III-B: "for 4-node motifs, anchors include ordered wedges and triangles"; Section III-F:
+// X_3 / 4-cliques; Section III-D: warp-local vs CTA mode, ordered set intersection, compaction,
+// block-local aggregation).
+//
+// In rank order every triangle {u < v < w} is anchored once at its lowest vertex u.  For an anchor
+// vertex u with out-neighbourhood L = N+(u) (sorted, d = |L|) we build the oriented adjacency of
+// G[L] as a bitmap: row i has bit j (j > i) iff L[j] is in N+(L[i]).  Row i is the candidate
+// frontier of the partial embedding (u, L[i]) (its signature: j = 2, frontier generator (u, L[i]),
+// required adjacency to both, no forbidden edge); it is computed once by an ordered intersection of
+// N+(L[i]) with L and then reused for
+//   * triangles:   T_u = sum_i popc(row_i)
+//   * t_e:         arc (u, L[i]) gets popc(row_i) + (# rows with bit i); arc (L[i], L[j]) gets +1
+//                  per set bit (global atomic at the position where the intersection found it)
+//   * 4-cliques:   K4_u = sum over set bits (i, j) of popc(row_i & row_j)   (the X_3 extension)
+//   * paw sums:    sum over triangles of (d_a + d_b + d_c)
+// Warp-local mode: d <= 32, rows are single words, one warp per anchor.
+// CTA mode: 32 < d <= kCtaMax, rows live in shared memory, one block per anchor.
+// Fallback (d > kCtaMax, hubs of very large graphs): per out-arc ordered intersections through
+// global memory with binary-searched membership; 4-cliques by binary search in N+(w).
+#include "harp_internal.cuh"
+
+namespace harp {
+namespace {
+
+constexpr int kCtaSmallMax = 256;
+constexpr int kCtaMax = 1024;
+constexpr int kInf = 0x7fffffff;
+
+// Anchor queues in ws.q_tri (n entries): warp-mode anchors (2 <= d <= 32) from the front,
+// CTA-mode and fallback anchors (d > 32) from the back.  Vertices are scanned in descending rank,
+// so high-degree anchors tend to be queued (and taken) first.
+__device__ __forceinline__ int tri_class(int d) {
+    return d < 2 ? -1 : (d <= 32 ? 0 : (d <= kCtaSmallMax ? 1 : (d <= kCtaMax ? 2 : 3)));
+}
+
+__global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int32_t* __restrict__ q,
+                               unsigned long long* __restrict__ cnt) {
+    const int l = lane_id();
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - l; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = n - 1 - (base + l);
+        int cls = -1;
+        if (u >= 0) cls = tri_class(dplus[u]);
+        cls = cls > 0 ? 1 : cls;  // 0: warp queue, 1: CTA queue
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t mask = __ballot_sync(kFull, cls == c);
+            if (!mask) continue;
+            unsigned long long start = 0;
+            const int leader = __ffs(mask) - 1;
+            if (l == leader) start = atomicAdd(&cnt[c], (unsigned long long)__popc(mask));
+            start = __shfl_sync(kFull, start, leader);
+            if (cls == c) {
+                const unsigned long long k = start + __popc(mask & lanemask_lt());
+                if (c == 0) q[k] = (int32_t)u;
+                else q[n - 1 - (int64_t)k] = (int32_t)u;
+            }
+        }
+    }
+}
+
+// smem lower_bound over a padded sorted array a[0..P) (P a power of two)
+__device__ __forceinline__ int lb_smem(const int32_t* a, int P, int32_t y) {
+    int j = 0;
+    for (int s = P >> 1; s >= 1; s >>= 1)
+        if (a[j + s - 1] < y) j += s;
+    return j;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Warp-local mode.
+// ---------------------------------------------------------------------------------------------
+constexpr int kWarpThreads = 256;
+constexpr int kWarpsPerBlock = kWarpThreads / 32;
+
+__global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __restrict__ offp,
+                                                           const int32_t* __restrict__ colsp,
+                                                           const int32_t* __restrict__ deg,
+                                                           const int32_t* __restrict__ q,
+                                                           const unsigned long long* __restrict__ cnt,
+                                                           uint32_t* __restrict__ te,
+                                                           uint64_t* __restrict__ acc) {
+    __shared__ int32_t sL[kWarpsPerBlock][32];
+    __shared__ uint32_t sRow[kWarpsPerBlock][32];
+    __shared__ uint64_t red[32];
+    const int w = threadIdx.x >> 5, l = lane_id();
+    const int64_t nq = (int64_t)cnt[0];
+    uint64_t tri = 0, k4 = 0, paw = 0;
+    for (int64_t k = ((int64_t)blockIdx.x * kWarpsPerBlock + w); k < nq; k += (int64_t)gridDim.x * kWarpsPerBlock) {
+        const int32_t u = q[k];
+        const int64_t ub = offp[u];
+        const int d = (int)(offp[u + 1] - ub);
+        const int32_t x = (l < d) ? colsp[ub + l] : kInf;
+        sL[w][l] = x;
+        sRow[w][l] = 0;
+        __syncwarp();
+        const int32_t last = sL[w][d - 1];
+        uint32_t col = 0;  // # rows with bit l
+        for (int i = 0; i < d - 1; ++i) {
+            const int32_t v = sL[w][i];
+            const int64_t b = offp[v], e = offp[v + 1];
+            uint32_t row = 0;
+            for (int64_t p0 = b; p0 < e; p0 += 32) {
+                const int64_t p = p0 + l;
+                const int32_t y = (p < e) ? colsp[p] : kInf;
+                bool hit = false;
+                int j = 0;
+                if (y <= last) {
+                    j = lb_smem(sL[w], 32, y);
+                    hit = sL[w][j] == y;
+                }
+                if (hit) {
+                    atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
+                    row |= 1u << j;
+                }
+                // rows are sorted: stop once the chunk passed the largest candidate
+                if (__shfl_sync(kFull, y, 31) >= last) break;
+            }
+            row = __reduce_or_sync(kFull, row);
+            col += (row >> l) & 1u;
+            if (l == i) sRow[w][i] = row;
+        }
+        __syncwarp();
+        const uint32_t myrow = sRow[w][l];
+        const uint32_t own = (l < d) ? (uint32_t)__popc(myrow) + col : 0u;
+        if (own) atomicAdd(&te[ub + l], own);
+        tri += (uint64_t)__popc(myrow);
+        uint32_t bits = myrow;
+        while (bits) {
+            const int j = __ffs(bits) - 1;
+            bits &= bits - 1;
+            k4 += (uint64_t)__popc(myrow & sRow[w][j]);
+        }
+        const uint64_t dx = (l < d) ? (uint64_t)deg[x] : 0;
+        paw += (uint64_t)own * dx + (uint64_t)__popc(myrow) * (uint64_t)deg[u];
+        __syncwarp();
+    }
+    tri = block_sum_u64(tri, red);
+    k4 = block_sum_u64(k4, red);
+    paw = block_sum_u64(paw, red);
+    if (threadIdx.x == 0) {
+        if (tri) atomicAdd((unsigned long long*)&acc[ACC_T], (unsigned long long)tri);
+        if (k4) atomicAdd((unsigned long long*)&acc[ACC_K4], (unsigned long long)k4);
+        if (paw) atomicAdd((unsigned long long*)&acc[ACC_PAWSUM], (unsigned long long)paw);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// CTA mode: rows of the anchor's out-neighbourhood bitmap in shared memory.
+// ---------------------------------------------------------------------------------------------
+template <int DMAX, int THREADS>
+struct CtaSmem {
+    static constexpr int P = DMAX;                  // padded list length (power of two)
+    static constexpr int W = DMAX / 32;             // words per row
+    static constexpr int WS = W | 1;                // odd row stride: no bank conflicts
+    int32_t L[P];
+    uint32_t own[DMAX];
+    uint32_t R[DMAX * WS];
+    uint64_t red[32];
+};
+
+template <int DMAX, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__ offp,
+                                                     const int32_t* __restrict__ colsp,
+                                                     const int32_t* __restrict__ deg,
+                                                     const int32_t* __restrict__ q, int64_t n, int cls,
+                                                     const unsigned long long* __restrict__ cnt,
+                                                     unsigned long long* __restrict__ ticket,
+                                                     uint32_t* __restrict__ te, uint64_t* __restrict__ acc) {
+    using S = CtaSmem<DMAX, THREADS>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S& s = *reinterpret_cast<S*>(smem_raw);
+    __shared__ int64_t s_item;
+    constexpr int NW = THREADS / 32;
+    const int w = threadIdx.x >> 5, l = lane_id();
+    const int64_t nq = (int64_t)cnt[1];
+    uint64_t tri = 0, k4 = 0, paw = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const int64_t k = s_item;
+        __syncthreads();
+        if (k >= nq) break;
+        const int32_t u = q[n - 1 - k];
+        const int64_t ub = offp[u];
+        const int d = (int)(offp[u + 1] - ub);
+        if (tri_class(d) != cls) continue;
+        const int W = (d + 31) >> 5;
+        const int WS = W | 1;
+        int P = 32;
+        while (P < d) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += THREADS) s.L[i] = (i < d) ? colsp[ub + i] : kInf;
+        for (int i = threadIdx.x; i < d; i += THREADS) s.own[i] = 0;
+        for (int i = threadIdx.x; i < d * WS; i += THREADS) s.R[i] = 0;
+        __syncthreads();
+        const int32_t last = s.L[d - 1];
+        // rows: warp per row, ordered intersection of N+(L[i]) with L
+        for (int i = w; i < d - 1; i += NW) {
+            const int32_t v = s.L[i];
+            const int64_t b = offp[v], e = offp[v + 1];
+            uint32_t hits = 0;
+            for (int64_t p0 = b; p0 < e; p0 += 32) {
+                const int64_t p = p0 + l;
+                const int32_t y = (p < e) ? colsp[p] : kInf;
+                if (y <= last) {
+                    const int j = lb_smem(s.L, P, y);
+                    if (s.L[j] == y) {
+                        atomicAdd(&te[p], 1u);
+                        atomicOr(&s.R[i * WS + (j >> 5)], 1u << (j & 31));
+                        atomicAdd(&s.own[j], 1u);
+                        ++hits;
+                    }
+                }
+                if (__shfl_sync(kFull, y, 31) >= last) break;
+            }
+            hits = warp_sum(hits);
+            if (l == 0 && hits) atomicAdd(&s.own[i], hits);
+        }
+        __syncthreads();
+        // 4-cliques: warp per row i, lane per candidate bit j of the current word
+        for (int i = w; i < d - 1; i += NW) {
+            const uint32_t* Ri = &s.R[i * WS];
+            for (int ww = (i + 1) >> 5; ww < W; ++ww) {
+                const uint32_t word = Ri[ww];
+                if (!word) continue;
+                tri += (l == 0) ? (uint64_t)__popc(word) : 0;
+                if ((word >> l) & 1u) {
+                    const int j = (ww << 5) + l;
+                    const uint32_t* Rj = &s.R[j * WS];
+                    uint32_t c = 0;
+                    for (int x = ww; x < W; ++x) c += __popc(Ri[x] & Rj[x]);
+                    k4 += c;
+                }
+            }
+        }
+        for (int i = threadIdx.x; i < d; i += THREADS) {
+            const uint32_t o = s.own[i];
+            if (o) {
+                atomicAdd(&te[ub + i], o);
+                paw += (uint64_t)o * (uint64_t)deg[s.L[i]];
+            }
+        }
+        __syncthreads();
+        // T_u * d_u for the paw sum (T_u = sum of popc over rows; recomputed cheaply)
+        uint32_t tu = 0;
+        for (int i = threadIdx.x; i < d * WS; i += THREADS) tu += __popc(s.R[i]);
+        paw += (uint64_t)tu * (uint64_t)deg[u];
+        __syncthreads();
+    }
+    tri = block_sum_u64(tri, s.red);
+    k4 = block_sum_u64(k4, s.red);
+    paw = block_sum_u64(paw, s.red);
+    if (threadIdx.x == 0) {
+        if (tri) atomicAdd((unsigned long long*)&acc[ACC_T], (unsigned long long)tri);
+        if (k4) atomicAdd((unsigned long long*)&acc[ACC_K4], (unsigned long long)k4);
+        if (paw) atomicAdd((unsigned long long*)&acc[ACC_PAWSUM], (unsigned long long)paw);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fallback for out-degree > kCtaMax: per out-arc (u, v) the frontier S_uv = N+(u) n N+(v) is
+// materialised (compaction) in a per-warp global buffer, then reused for the 4-clique extension.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int64_t lb_global(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t y) {
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict__ offp,
+                                                      const int32_t* __restrict__ colsp,
+                                                      const int32_t* __restrict__ deg,
+                                                      const int32_t* __restrict__ q, int64_t n,
+                                                      const unsigned long long* __restrict__ cnt,
+                                                      int32_t* __restrict__ scratch, int64_t scratch_per_warp,
+                                                      uint32_t* __restrict__ te, uint64_t* __restrict__ acc) {
+    __shared__ uint64_t red[32];
+    const int w = threadIdx.x >> 5, l = lane_id();
+    const int nw = blockDim.x >> 5;
+    int32_t* S = scratch + ((int64_t)blockIdx.x * nw + w) * scratch_per_warp;
+    const int64_t nq = (int64_t)cnt[1];
+    uint64_t tri = 0, k4 = 0, paw = 0;
+    for (int64_t k = blockIdx.x; k < nq; k += gridDim.x) {
+        const int32_t u = q[n - 1 - k];
+        const int64_t ub = offp[u], ue = offp[u + 1];
+        if (tri_class((int)(ue - ub)) != 3) continue;
+        const uint64_t du = (uint64_t)deg[u];
+        for (int64_t a = ub + w; a < ue; a += nw) {  // warp per out-arc (u, v)
+            const int32_t v = colsp[a];
+            const int64_t b = offp[v], e = offp[v + 1];
+            const uint64_t dv = (uint64_t)deg[v];
+            int64_t ns = 0;
+            uint32_t own_uv = 0;
+            for (int64_t p0 = b; p0 < e; p0 += 32) {
+                const int64_t p = p0 + l;
+                bool hit = false;
+                int32_t y = kInf;
+                int64_t pu = 0;
+                if (p < e) {
+                    y = colsp[p];
+                    pu = lb_global(colsp, ub, ue, y);
+                    hit = pu < ue && colsp[pu] == y;
+                }
+                const uint32_t hm = __ballot_sync(kFull, hit);
+                if (hit) {
+                    atomicAdd(&te[p], 1u);   // (v, y)
+                    atomicAdd(&te[pu], 1u);  // (u, y)
+                    S[ns + __popc(hm & lanemask_lt())] = y;
+                    paw += du + dv + (uint64_t)deg[y];
+                }
+                ns += __popc(hm);
+                own_uv += __popc(hm);
+            }
+            if (l == 0 && own_uv) atomicAdd(&te[a], own_uv);
+            tri += (l == 0) ? (uint64_t)own_uv : 0;
+            __syncwarp();
+            // 4-cliques through (u, v): pairs w < x of S_uv with x in N+(w)
+            for (int64_t s1 = 0; s1 < ns; ++s1) {
+                const int32_t wv = S[s1];
+                const int64_t wb = offp[wv], we = offp[wv + 1];
+                for (int64_t s2 = s1 + 1 + l; s2 < ns; s2 += 32) {
+                    const int32_t xv = S[s2];
+                    const int64_t px = lb_global(colsp, wb, we, xv);
+                    k4 += (px < we && colsp[px] == xv) ? 1 : 0;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    tri = block_sum_u64(tri, red);
+    k4 = block_sum_u64(k4, red);
+    paw = block_sum_u64(paw, red);
+    if (threadIdx.x == 0) {
+        if (tri) atomicAdd((unsigned long long*)&acc[ACC_T], (unsigned long long)tri);
+        if (k4) atomicAdd((unsigned long long*)&acc[ACC_K4], (unsigned long long)k4);
+        if (paw) atomicAdd((unsigned long long*)&acc[ACC_PAWSUM], (unsigned long long)paw);
+    }
+}
+
+template <int DMAX, int THREADS>
+harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slot, int blocks_per_sm,
+                       cudaStream_t s) {
+    const size_t smem = sizeof(CtaSmem<DMAX, THREADS>);
+    HARP_CK(cudaFuncSetAttribute(k_tri_cta<DMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    k_tri_cta<DMAX, THREADS><<<152 * blocks_per_sm, THREADS, smem, s>>>(
+        ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, (const unsigned long long*)&ws.acc[Q_TRI_WARP],
+        (unsigned long long*)&ws.acc[ticket_slot], ws.te, ws.acc);
+    HARP_LAUNCHED();
+    return HARP_OK;
+}
+
+}  // namespace
+
+// acc[Q_TRI_WARP], acc[Q_TRI_CTA] hold the queue lengths, acc[T_TRI_*] the CTA tickets (all cleared
+// with the accumulators before the count).
+harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s) {
+    (void)plan;
+    const int64_t n = g->n;
+    if (n == 0 || g->m == 0) return HARP_OK;  // no marks: the segments read as zero
+    unsigned long long* cnt = (unsigned long long*)&ws.acc[Q_TRI_WARP];
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.q_tri, cnt);
+    HARP_LAUNCHED();
+    k_tri_warp<<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, cnt, ws.te, ws.acc);
+    HARP_LAUNCHED();
+    HARP_CK(prof_mark(s, SEG_TRI_WARP));
+    HARP_TRY((launch_cta<kCtaSmallMax, 256>(g, ws, 1, T_TRI_S, 6, s)));
+    HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
+    HARP_TRY((launch_cta<kCtaMax, 512>(g, ws, 2, T_TRI_L, 1, s)));
+    HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
+    // fallback: per-warp frontier buffers of the largest possible out-degree (bounded by sqrt(2m))
+    int64_t dmax = 1;
+    while (dmax * dmax < 2 * g->m) ++dmax;
+    if (dmax > g->max_deg) dmax = g->max_deg;
+    if (dmax > kCtaMax) {
+        const int fb_blocks = 152;
+        const int64_t per_warp = dmax + 32;
+        const size_t bytes = (size_t)fb_blocks * 8 * (size_t)per_warp * sizeof(int32_t);
+        int32_t* scratch = nullptr;
+        HARP_CK(cudaMallocAsync((void**)&scratch, bytes, s));
+        k_tri_fallback<<<fb_blocks, 256, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, n, cnt, scratch, per_warp,
+                                                 ws.te, ws.acc);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        cudaFreeAsync(scratch, s);
+        if (e != cudaSuccess) {
+            record_cuda_error(e);
+            return HARP_ECUDA;
+        }
+    }
+    HARP_CK(prof_mark(s, SEG_TRI_FALLBACK));
+    return HARP_OK;
+}
+
+}  // namespace harp

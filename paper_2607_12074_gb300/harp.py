@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libharp (include/harp.h).  Argument marshalling only: every step of the
+counting path runs in the library's CUDA kernels.  PyTorch tensors are accepted for device memory
+(their data pointers are passed through) and torch streams for ordering.
+
+The functions keep the C names (``harp_build_csr``, ``harp_count4`` ...).  There is no CPU fallback:
+if libharp.so is missing or cannot be loaded, every call raises :class:`HarpUnavailable`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libharp.so")
+
+HARP_OK, HARP_EINVAL, HARP_ENOMEM, HARP_ECUDA, HARP_EOVERFLOW = 0, 1, 2, 3, 4
+HARP_EAGAIN, HARP_ETIMEOUT, HARP_ENOTFOUND, HARP_EDEVICE = 5, 6, 7, 8
+HARP_PTR_HOST, HARP_PTR_DEVICE = 0, 1
+HARP_ABI_VERSION = 1
+HARP_BASIS_TRIANGLE_WEDGE = 0
+HARP_PROBE_HASH, HARP_PROBE_BSEARCH = 1, 2
+HARP_PLAN_NO_GRAPH = 1
+
+MOTIFS = ("star3", "path4", "paw", "cycle4", "diamond", "clique4")
+STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")
+
+
+class HarpUnavailable(RuntimeError):
+    """libharp.so is not built or cannot be loaded (no silent fallback exists)."""
+
+
+class HarpError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {detail or status}")
+
+
+class harp_plan(ctypes.Structure):
+    _fields_ = [
+        ("version", ctypes.c_uint32),
+        ("basis", ctypes.c_uint32),
+        ("tri_probe", ctypes.c_uint32),
+        ("tri_warp_max", ctypes.c_uint32),
+        ("c4_warp_max_work", ctypes.c_uint32),
+        ("c4_cta_max_work", ctypes.c_uint32),
+        ("c4_window_bytes", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("est_enum", ctypes.c_double),
+        ("est_inter", ctypes.c_double),
+        ("est_halo", ctypes.c_double),
+        ("est_reuse", ctypes.c_double),
+        ("est_yield", ctypes.c_double),
+        ("objective", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class harp_select_opts(ctypes.Structure):
+    _fields_ = [
+        ("sample_vertices", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64),
+        ("memory_budget", ctypes.c_uint64),
+        ("lambda_inter", ctypes.c_double),
+        ("lambda_halo", ctypes.c_double),
+        ("lambda_reuse", ctypes.c_double),
+        ("lambda_yield", ctypes.c_double),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libharp.so (raises HarpUnavailable if absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise HarpUnavailable(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+        try:
+            L = ctypes.CDLL(LIB_PATH)
+        except OSError as e:
+            raise HarpUnavailable(f"cannot load {LIB_PATH}: {e}") from e
+        vp, i64, u32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int
+        pu64 = ctypes.POINTER(ctypes.c_uint64)
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        L.harp_build_csr.argtypes = [i64, i64, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        L.harp_csr_free.argtypes = [vp]
+        L.harp_csr_free.restype = None
+        L.harp_csr_info.argtypes = [vp, pi64, pi64, pi64, ctypes.POINTER(ctypes.c_size_t)]
+        L.harp_csr_arrays.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.harp_select_anchors.argtypes = [vp, ctypes.POINTER(harp_select_opts), ctypes.POINTER(harp_plan)]
+        L.harp_count4.argtypes = [vp, ctypes.POINTER(harp_plan), pu64]
+        L.harp_count4_stats.argtypes = [vp, ctypes.POINTER(harp_plan), pu64, pu64]
+        L.harp_count4_async.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp]
+        L.harp_set_profiling.argtypes = [i32]
+        L.harp_last_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float), pi64]
+        L.harp_launch_count.argtypes = []
+        L.harp_launch_count.restype = i64
+        L.harp_status_str.argtypes = [i32]
+        L.harp_status_str.restype = ctypes.c_char_p
+        L.harp_last_cuda_error.argtypes = []
+        L.harp_last_cuda_error.restype = i32
+        L.harp_last_cuda_error_str.argtypes = []
+        L.harp_last_cuda_error_str.restype = ctypes.c_char_p
+        for name in ("harp_build_csr", "harp_csr_info", "harp_csr_arrays", "harp_select_anchors", "harp_count4",
+                     "harp_count4_stats", "harp_count4_async", "harp_set_profiling", "harp_last_stage_times"):
+            getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def _check(st: int, what: str):
+    if st != HARP_OK:
+        L = lib()
+        detail = L.harp_status_str(st).decode()
+        if st == HARP_ECUDA:
+            detail += f" ({L.harp_last_cuda_error_str().decode()})"
+        raise HarpError(st, what, detail)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _edge_ptrs(src, dst):
+    """Return (ptr_src, ptr_dst, m_in, flags, keepalive)."""
+    try:
+        import torch
+        if isinstance(src, torch.Tensor):
+            if not (src.is_cuda and dst.is_cuda):
+                src, dst = src.cpu().numpy(), dst.cpu().numpy()
+            else:
+                if src.dtype != torch.int32 or dst.dtype != torch.int32:
+                    raise TypeError("device edge lists must be torch.int32")
+                src, dst = src.contiguous(), dst.contiguous()
+                if src.numel() != dst.numel():
+                    raise ValueError("src and dst differ in length")
+                return src.data_ptr(), dst.data_ptr(), src.numel(), HARP_PTR_DEVICE, (src, dst)
+    except ImportError:
+        pass
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+    d = np.ascontiguousarray(np.asarray(dst, dtype=np.int32))
+    if s.shape != d.shape or s.ndim != 1:
+        raise ValueError("src and dst must be 1-D and of equal length")
+    return s.ctypes.data, d.ctypes.data, s.size, HARP_PTR_HOST, (s, d)
+
+
+class Csr:
+    """Owns a harp_csr handle (device memory); freed on close() or garbage collection."""
+
+    def __init__(self, handle: int, keepalive=None):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keepalive
+
+    def close(self):
+        if self.handle:
+            lib().harp_csr_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return harp_csr_info(self)
+
+
+def harp_build_csr(n: int, src, dst, stream=None) -> Csr:
+    """Device CSR from an undirected edge list (numpy/host arrays or torch.int32 CUDA tensors)."""
+    ps, pd, m_in, flags, keep = _edge_ptrs(src, dst)
+    out = ctypes.c_void_p()
+    st = lib().harp_build_csr(int(n), int(m_in), ps, pd, flags, _stream_handle(stream), ctypes.byref(out))
+    _check(st, "harp_build_csr")
+    return Csr(out.value, None)
+
+
+def harp_csr_info(g: Csr) -> dict:
+    n, m, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    b = ctypes.c_size_t()
+    _check(lib().harp_csr_info(g.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(md), ctypes.byref(b)),
+           "harp_csr_info")
+    return {"n": n.value, "m": m.value, "max_degree": md.value, "device_bytes": b.value}
+
+
+def harp_csr_arrays(g: Csr) -> tuple[int, int]:
+    off, cols = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().harp_csr_arrays(g.handle, ctypes.byref(off), ctypes.byref(cols)), "harp_csr_arrays")
+    return off.value, cols.value
+
+
+def harp_select_anchors(g: Csr, sample_vertices: int = 0, seed: int = 0, memory_budget: int = 0) -> harp_plan:
+    opts = harp_select_opts(sample_vertices, seed, memory_budget, 0.0, 0.0, 0.0, 0.0)
+    p = harp_plan()
+    _check(lib().harp_select_anchors(g.handle, ctypes.byref(opts), ctypes.byref(p)), "harp_select_anchors")
+    return p
+
+
+def _plan_ref(plan):
+    return ctypes.byref(plan) if plan is not None else None
+
+
+def harp_count4(g: Csr, plan: harp_plan | None = None) -> np.ndarray:
+    """The six induced counts [star3, path4, paw, cycle4, diamond, clique4] as numpy uint64."""
+    out = np.zeros(6, np.uint64)
+    _check(lib().harp_count4(g.handle, _plan_ref(plan), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+           "harp_count4")
+    return out
+
+
+def harp_count4_stats(g: Csr, plan: harp_plan | None = None) -> tuple[np.ndarray, np.ndarray]:
+    out = np.zeros(6, np.uint64)
+    st = np.zeros(8, np.uint64)
+    _check(lib().harp_count4_stats(g.handle, _plan_ref(plan), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "harp_count4_stats")
+    return out, st
+
+
+def harp_count4_async(g: Csr, d_out_ptr: int, plan: harp_plan | None = None, stream=None) -> None:
+    """Enqueue a count; d_out_ptr is a device pointer to >= 16 uint64 (e.g. a torch int64 tensor)."""
+    _check(lib().harp_count4_async(g.handle, _plan_ref(plan), ctypes.c_void_p(d_out_ptr), _stream_handle(stream)),
+           "harp_count4_async")
+
+
+def harp_set_profiling(enable: bool) -> None:
+    _check(lib().harp_set_profiling(1 if enable else 0), "harp_set_profiling")
+
+
+def harp_last_stage_times() -> tuple[list[float], int]:
+    ms = (ctypes.c_float * 9)()
+    launches = ctypes.c_int64()
+    _check(lib().harp_last_stage_times(ms, ctypes.byref(launches)), "harp_last_stage_times")
+    return list(ms), launches.value
+
+
+def harp_launch_count() -> int:
+    return int(lib().harp_launch_count())
+
+
+def count4_edges(n: int, src, dst, plan: harp_plan | None = None, stream=None) -> np.ndarray:
+    """Convenience: build the CSR from an edge list, count, free."""
+    g = harp_build_csr(n, src, dst, stream)
+    try:
+        return harp_count4(g, plan)
+    finally:
+        g.close()

@@ -1,0 +1,119 @@
+"""Host work meter: exact algorithmic work and bytes of each counting kernel for a given graph.
+
+"Algorithmic bytes" are the bytes an ideal implementation of each step must move between the SMs
+and memory (every needed list element, offset and statistic read or written once), independent of
+how many of them the L2 serves.  They are the numerators of the roofline figures; the same per-unit
+figures are stated in the design doc.  This module is plain numpy on the host and is not on the counting
+path (bench.py uses it to turn kernel times into bandwidth).
+
+Per unit (int32 ids and counters = 4 B, int64 offsets = 8 B):
+  orientation   read offsets + cols + perm gather, write relabelled cols and offsets, out-CSR copy:
+                24 (n+1) + 12 * 2m + 8 m
+  triangle      per anchor u: its list N+(u) (4 d+), per row v in N+(u): offsets (16) and the probed
+                part of N+(v) up to max N+(u) (4 each); per triangle: 3 t_e updates (8 each, RMW);
+                per out-arc: its own t_e update (8)
+  wedge (C4)    per root u and per pass over its lower neighbours (1 pass, or 1 per x-window):
+                N-(u) (4 d-) + offsets of each w (16 d-); per wedge element x: 4
+  reduction     t_e read: 4 m
+"""
+from __future__ import annotations
+
+import numpy as np
+
+WARP_MAX_TRI = 32
+CTA_SMALL_MAX = 256
+CTA_MAX = 1024
+WIN_WORDS = 51200
+
+
+def _simple_edges(n, src, dst):
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    lo = np.minimum(s, d)
+    hi = np.maximum(s, d)
+    key = np.unique(lo * n + hi)
+    return key // n, key % n
+
+
+def rank_space(n, src, dst):
+    """Degrees and the rank-ordered sorted CSR used by the kernels (rank = (degree, id))."""
+    lo, hi = _simple_edges(n, src, dst)
+    deg0 = np.bincount(lo, minlength=n) + np.bincount(hi, minlength=n)
+    order = np.lexsort((np.arange(n), deg0))
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    a, b = rank[lo], rank[hi]
+    rows = np.concatenate([a, b])
+    cols = np.concatenate([b, a])
+    o = np.lexsort((cols, rows))
+    rows, cols = rows[o], cols[o]
+    deg = deg0[order]
+    indptr = np.zeros(n + 1, np.int64)
+    np.cumsum(deg, out=indptr[1:])
+    pos = np.arange(cols.size, dtype=np.int64) - indptr[rows]
+    split = np.bincount(rows[cols < rows], minlength=n)   # |N-(u)|
+    return {"n": n, "m": int(lo.size), "deg": deg, "indptr": indptr, "rows": rows, "cols": cols, "pos": pos,
+            "split": split, "dplus": deg - split}
+
+
+def meter(n, src, dst, c4_warp_max=512, c4_cta_max=8192):
+    """Per-kernel work and algorithmic bytes (dict of dicts)."""
+    G = rank_space(n, src, dst)
+    m = G["m"]
+    deg, indptr, rows, cols, pos = G["deg"], G["indptr"], G["rows"], G["cols"], G["pos"]
+    split, dplus = G["split"], G["dplus"]
+    out = {"n": n, "m": m}
+    out["orient"] = {"bytes": 24 * (n + 1) + 12 * 2 * m + 8 * m}
+
+    # ---- triangle anchors: out-arcs (u -> v), u < v
+    up = cols > rows
+    au, av = rows[up], cols[up]                      # oriented arcs in row order
+    offp = np.zeros(n + 1, np.int64)
+    np.cumsum(dplus, out=offp[1:])
+    last = np.full(n, -1, np.int64)
+    has = dplus > 0
+    last[has] = cols[indptr[1:][has] - 1]            # max of N+(u) = last element of row u
+    # probed part of N+(v) for each out-arc (u, v): elements y of N+(v) with y <= last[u]
+    keys = au * n + av                               # sorted: out-arcs grouped by source, ascending
+    q = av * n + last[au]
+    probed = np.searchsorted(keys, q, side="right") - offp[av]
+    probed = np.maximum(probed, 0)
+    cls = np.where(dplus < 2, -1, np.where(dplus <= WARP_MAX_TRI, 0, np.where(dplus <= CTA_SMALL_MAX, 1,
+                   np.where(dplus <= CTA_MAX, 2, 3))))
+    arc_cls = cls[au]
+    # rows i < d-1 only: the last element of N+(u) starts no row
+    is_last = np.zeros(au.size, bool)
+    ends = offp[1:][has] - 1
+    is_last[ends] = True
+    row_bytes = np.where(is_last, 0, 16 + 4 * probed)
+    tri_units = {}
+    for c, name in ((0, "tri_warp"), (1, "tri_cta_small"), (2, "tri_cta_large"), (3, "tri_fallback")):
+        sel = arc_cls == c
+        tri_units[name] = {"anchors": int((cls == c).sum()), "probes": int(probed[sel & ~is_last].sum()),
+                           "bytes": int(row_bytes[sel].sum() + 4 * sel.sum() + 8 * sel.sum())}
+    out.update(tri_units)
+    out["tri_probes_total"] = int(probed[~is_last].sum())
+
+    # ---- wedge anchors: root u, w in N-(u) (arcs (u -> w), w < u), segment = pos of u in row w
+    down = cols < rows
+    ru, rw = rows[down], cols[down]
+    # pos_w(u) = position of u in row w = pos of the reverse arc (w -> u)
+    rev = np.searchsorted(rows * n + cols, rw * n + ru)
+    seg = pos[rev]
+    W = np.bincount(ru, weights=seg, minlength=n).astype(np.int64)
+    dm = split
+    tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= c4_warp_max, 0, np.where(W <= c4_cta_max, 1, 2)))
+    width = np.where(dm <= 255, 8, np.where(dm <= 65535, 16, 32))
+    span = WIN_WORDS * (32 // width)
+    nwin = np.where(tier == 2, (np.arange(n) + span - 1) // span, 1)
+    for t, name in ((0, "c4_small"), (1, "c4_mid"), (2, "c4_window")):
+        sel = tier == t
+        passes = nwin[sel]
+        out[name] = {"roots": int(sel.sum()), "wedges": int(W[sel].sum()),
+                     "items": int(passes.sum()),
+                     "bytes": int((20 * dm[sel] * passes).sum() + 4 * W[sel].sum())}
+    out["c4_wedges_total"] = int(W.sum())
+    out["reduce"] = {"bytes": 4 * m}
+    return out

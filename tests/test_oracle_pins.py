@@ -5,10 +5,10 @@ closed forms derived from the definition of an induced occurrence (Section II), 
 matrix identities (tr A^3, tr A^4), hand-derived fixtures, and brute force over all 4-subsets.
 Each check is chosen so that a dropped term, a wrong sign or a transposed operand fails one of them.
 """
-import itertools
 import json
 import math
 import os
+import sys
 
 import numpy as np
 import pytest
@@ -18,40 +18,10 @@ import oracle as O
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 C = math.comb
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
-def edges_of(pairs):
-    pairs = list(pairs)
-    return np.array([a for a, b in pairs], np.int32), np.array([b for a, b in pairs], np.int32)
-
-
-def complete(n):
-    return edges_of(itertools.combinations(range(n), 2))
-
-
-def star(k):
-    return edges_of((0, i) for i in range(1, k + 1))
-
-
-def cycle(n):
-    return edges_of((i, (i + 1) % n) for i in range(n))
-
-
-def path(n):
-    return edges_of((i, i + 1) for i in range(n - 1))
-
-
-def kbip(a, b):
-    return edges_of((i, a + j) for i in range(a) for j in range(b))
-
-
-def wheel(n):
-    rim = [(i, (i + 1) % n) for i in range(n)]
-    return edges_of(rim + [(n, i) for i in range(n)])
-
-
-def cocktail(k):
-    return edges_of((i, j) for i in range(2 * k) for j in range(i + 1, 2 * k) if j != i + k)
+from graph_families import closed_forms, complete, edges_of, star  # noqa: E402
 
 
 ALL = ("brute", "esu", "literal", "combo")
@@ -62,22 +32,7 @@ def run(method, n, s, d):
             "combo": O.count4_combo}[method](n, s, d)
 
 
-CLOSED = []
-for n in (4, 5, 6, 9, 12):
-    CLOSED.append((f"K{n}", n, complete(n), [0, 0, 0, 0, 0, C(n, 4)]))
-for k in (3, 4, 7, 11):
-    CLOSED.append((f"K1,{k}", k + 1, star(k), [C(k, 3), 0, 0, 0, 0, 0]))
-CLOSED.append(("C4", 4, cycle(4), [0, 0, 0, 1, 0, 0]))
-for n in (5, 6, 9, 17):
-    CLOSED.append((f"C{n}", n, cycle(n), [0, n, 0, 0, 0, 0]))
-for n in (4, 5, 10, 23):
-    CLOSED.append((f"P{n}", n, path(n), [0, n - 3, 0, 0, 0, 0]))
-for a, b in ((2, 2), (2, 5), (3, 4), (5, 6)):
-    CLOSED.append((f"K{a},{b}", a + b, kbip(a, b), [a * C(b, 3) + b * C(a, 3), 0, 0, C(a, 2) * C(b, 2), 0, 0]))
-for n in (5, 6, 8, 13):
-    CLOSED.append((f"W{n}", n + 1, wheel(n), [n * C(n - 3, 3) // (n - 3), n, n * (n - 4), 0, n, 0]))
-for k in (2, 3, 4, 6):
-    CLOSED.append((f"CP{k}", 2 * k, cocktail(k), [0, 0, 0, C(k, 2), 4 * k * C(k - 1, 2), 16 * C(k, 4)]))
+CLOSED = closed_forms()
 
 
 @pytest.mark.parametrize("method", ALL)
