@@ -176,6 +176,30 @@ harp_status harp_last_stage_times(float ms_out[HARP_NSEGMENTS], int64_t* launche
 int64_t harp_launch_count(void);
 
 /* ------------------------------------------------------------------------------------------------
+ * Counting without allocation.  The paper has no counterpart: this entry point exists for callers
+ * that may not allocate device memory while they run (code inside another framework's
+ * pre-reserved memory regime, services that forbid cudaMalloc/cudaFree after start-up because an
+ * allocation can synchronise the device or fragment a sized pool, threads that only own a stream).
+ *
+ * harp_count4_noalloc counts the six induced motifs of a caller-owned, device-resident CSR:
+ *   n, m       vertices and undirected simple edges; n <= 262,144 and m <= 524,288, larger sizes
+ *              return HARP_ENOMEM (they do not fit the fixed scratch)
+ *   d_offsets  device int64[n+1], d_cols device int32[2m]: a symmetric CSR with every row sorted
+ *              ascending, no self-loops, no duplicates (e.g. the arrays of harp_csr_arrays);
+ *              read only.  A malformed CSR gives undefined results.
+ *   d_out      device uint64[16]: [0..5] counts, [8..15] statistics (HARP_STAT_* order), written
+ *              when `stream` reaches the end of the work
+ *   stream     cudaStream_t; the call only enqueues work and returns
+ * Scratch lives in one file-scope static device array of 32 MiB that every GPU used by the process
+ * holds until exit.  The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream capture.  All calls
+ * share the array and clear what must start at zero themselves: calls whose work overlaps on the
+ * GPU (different streams or threads) race on it, so serialise them.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+harp_status harp_count4_noalloc(int64_t n, int64_t m, const int64_t* d_offsets, const int32_t* d_cols,
+                                uint64_t* d_out, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
  * Errors.
  * ---------------------------------------------------------------------------------------------- */
 const char* harp_status_str(harp_status s);

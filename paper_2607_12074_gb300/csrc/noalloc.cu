@@ -1,0 +1,133 @@
+// harp_count4_noalloc: the counting pipeline for small graphs with every scratch buffer carved out
+// of one file-scope static device array, so the call allocates nothing.
+//
+// Who needs it: callers that must not allocate device memory while they run - code executing
+// inside another framework's pre-reserved memory regime, long-running services that forbid
+// cudaMalloc/cudaFree after start-up (allocation can synchronise the device and fragment a
+// carefully sized pool), and host threads that only own a stream.  They pass a device-resident CSR
+// and a device output buffer; the library uses the static array below for everything else.
+//
+// The array lives in every process that loads libharp, on every GPU the process uses, until exit.
+// All calls share it: two calls whose work overlaps on a GPU (different streams, or different host
+// threads) race on it and give undefined results; serialise them (same stream, or events).
+#include <mutex>
+
+#include "harp_internal.cuh"
+
+namespace harp {
+namespace {
+
+// Size limits of the static scratch.  m <= 2^19 also keeps every out-degree <= 1024 (out-degree is
+// at most sqrt(2m)), so no execution mode that would need extra scratch is reached.
+constexpr int64_t kNoAllocMaxN = 262144;
+constexpr int64_t kNoAllocMaxM = 524288;
+constexpr size_t kNoAllocBytes = (size_t)32 << 20;  // 32 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Lay out a Workspace for (n, m) inside [base, base + cap); returns the bytes used (0 if it does
+// not fit).  Same arrays and sizes as the allocating path.
+size_t carve(unsigned char* base, size_t cap, int64_t n, int64_t m, Workspace& ws) {
+    const int64_t nn = n > 0 ? n : 1;
+    const int64_t mm = m > 0 ? m : 1;
+    const size_t hist_len = radix_hist_len(nn);
+    const size_t tmp_len = scan_tmp_needed(nn) + scan_tmp_needed((int64_t)hist_len) + 64;
+    struct Part { void** p; size_t bytes; };
+    Part parts[] = {
+        {(void**)&ws.deg, sizeof(int32_t) * nn},
+        {(void**)&ws.order, sizeof(int32_t) * nn},
+        {(void**)&ws.perm, sizeof(int32_t) * nn},
+        {(void**)&ws.dplus, sizeof(int32_t) * nn},
+        {(void**)&ws.vkeys, sizeof(uint64_t) * nn},
+        {(void**)&ws.vkeys_alt, sizeof(uint64_t) * nn},
+        {(void**)&ws.hist, sizeof(uint32_t) * hist_len},
+        {(void**)&ws.off, sizeof(int64_t) * (nn + 1)},
+        {(void**)&ws.offp, sizeof(int64_t) * (nn + 1)},
+        {(void**)&ws.cols, sizeof(int32_t) * 2 * mm},
+        {(void**)&ws.colsp, sizeof(int32_t) * 2 * mm},
+        {(void**)&ws.q_tri, sizeof(int32_t) * nn},
+        {(void**)&ws.q_mid, sizeof(int32_t) * 2 * nn},
+        {(void**)&ws.q_win, sizeof(int32_t) * 2 * nn},
+        {(void**)&ws.win_prefix, sizeof(int64_t) * (nn + 1)},
+        {(void**)&ws.scan_tmp, sizeof(int64_t) * tmp_len},
+        {(void**)&ws.acc, sizeof(uint64_t) * kOutLen},
+    };
+    size_t off = 0;
+    for (const Part& p : parts) off += up256(p.bytes);
+    if (off > cap) return 0;
+    off = 0;
+    for (const Part& p : parts) {
+        *p.p = base + off;
+        off += up256(p.bytes);
+    }
+    ws.te = reinterpret_cast<uint32_t*>(ws.colsp + mm);
+    ws.hist_len = hist_len;
+    ws.scan_tmp_len = tmp_len;
+    ws.base = base;
+    ws.bytes = off;
+    ws.n = n;
+    ws.m = m;
+    return off;
+}
+
+// Device address of the static array for the current device (looked up once per device).
+harp_status scratch_address(unsigned char** out) {
+    int dev = 0;
+    HARP_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return HARP_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            record_cuda_error(e);
+            return HARP_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    return HARP_OK;
+}
+
+}  // namespace
+}  // namespace harp
+
+using namespace harp;
+
+extern "C" harp_status harp_count4_noalloc(int64_t n, int64_t m, const int64_t* d_offsets, const int32_t* d_cols,
+                                           uint64_t* d_out, void* stream) {
+    if (n < 0 || m < 0) return HARP_EINVAL;
+    if (n > kNoAllocMaxN || m > kNoAllocMaxM) return HARP_ENOMEM;  // beyond the static scratch
+    if (!d_out || (n > 0 && !d_offsets) || (m > 0 && !d_cols)) return HARP_EINVAL;
+    unsigned char* base = nullptr;
+    HARP_TRY(scratch_address(&base));
+    harp_csr g;  // a view of the caller's CSR; owns nothing
+    HARP_CK(cudaGetDevice(&g.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    g.stream = s;
+    g.n = n;
+    g.m = m;
+    g.max_deg = n > 0 ? n - 1 : 0;  // an upper bound suffices (it only sizes the degree sort key)
+    g.off = const_cast<int64_t*>(d_offsets);
+    g.cols = const_cast<int32_t*>(d_cols);
+    Workspace ws;
+    if (carve(base, kNoAllocBytes, n, m, ws) == 0) return HARP_ENOMEM;
+    harp_plan plan;
+    normalise_plan(nullptr, &plan);
+    // every accumulator, queue counter and ticket starts at zero; the kernels clear t_e and the
+    // window counts themselves
+    HARP_CK(cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s));
+    if (n > 0) {
+        HARP_TRY(orient(&g, ws, s));
+        HARP_TRY(count_triangles_k4(&g, ws, plan, s));
+        HARP_TRY(count_wedge_c4(&g, ws, plan, s));
+    }
+    HARP_TRY(reduce_and_close(&g, ws, s));
+    HARP_CK(cudaMemcpyAsync(d_out, ws.acc, 16 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    return HARP_OK;
+}

@@ -100,6 +100,7 @@ def lib():
         L.harp_count4.argtypes = [vp, ctypes.POINTER(harp_plan), pu64]
         L.harp_count4_stats.argtypes = [vp, ctypes.POINTER(harp_plan), pu64, pu64]
         L.harp_count4_async.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp]
+        L.harp_count4_noalloc.argtypes = [i64, i64, vp, vp, vp, vp]
         L.harp_set_profiling.argtypes = [i32]
         L.harp_last_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float), pi64]
         L.harp_launch_count.argtypes = []
@@ -111,7 +112,8 @@ def lib():
         L.harp_last_cuda_error_str.argtypes = []
         L.harp_last_cuda_error_str.restype = ctypes.c_char_p
         for name in ("harp_build_csr", "harp_csr_info", "harp_csr_arrays", "harp_select_anchors", "harp_count4",
-                     "harp_count4_stats", "harp_count4_async", "harp_set_profiling", "harp_last_stage_times"):
+                     "harp_count4_stats", "harp_count4_async", "harp_count4_noalloc", "harp_set_profiling",
+                     "harp_last_stage_times"):
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -239,6 +241,17 @@ def harp_count4_async(g: Csr, d_out_ptr: int, plan: harp_plan | None = None, str
     """Enqueue a count; d_out_ptr is a device pointer to >= 16 uint64 (e.g. a torch int64 tensor)."""
     _check(lib().harp_count4_async(g.handle, _plan_ref(plan), ctypes.c_void_p(d_out_ptr), _stream_handle(stream)),
            "harp_count4_async")
+
+
+def harp_count4_noalloc(n: int, m: int, d_offsets: int, d_cols: int, d_out: int, stream=None) -> None:
+    """Count a device CSR (n <= 262,144, m <= 524,288) without any device allocation.
+
+    For callers that may not allocate device memory while they run.  d_offsets / d_cols / d_out
+    are device pointers (int64[n+1], int32[2m], uint64[16]); the work is only enqueued on `stream`.
+    Scratch is a static 32 MiB device array shared by all calls: serialise calls that could overlap.
+    """
+    _check(lib().harp_count4_noalloc(int(n), int(m), ctypes.c_void_p(d_offsets), ctypes.c_void_p(d_cols),
+                                     ctypes.c_void_p(d_out), _stream_handle(stream)), "harp_count4_noalloc")
 
 
 def harp_set_profiling(enable: bool) -> None:
