@@ -33,9 +33,7 @@ cudaError_t prof_mark(cudaStream_t s, int seg) {
     return cudaEventRecord(t_marks[seg + 1], s);
 }
 
-harp_status ws_ensure(Workspace& ws, int64_t n, int64_t m, cudaStream_t s) {
-    if (ws.base && ws.n == n && ws.m == m) return HARP_OK;
-    ws_release(ws, s);
+size_t ws_layout(Workspace& ws, unsigned char* base, int64_t n, int64_t m) {
     const int64_t nn = n > 0 ? n : 1;
     const int64_t mm = m > 0 ? m : 1;
     const size_t hist_len = radix_hist_len(nn);
@@ -46,6 +44,7 @@ harp_status ws_ensure(Workspace& ws, int64_t n, int64_t m, cudaStream_t s) {
         {(void**)&ws.order, sizeof(int32_t) * nn},
         {(void**)&ws.perm, sizeof(int32_t) * nn},
         {(void**)&ws.dplus, sizeof(int32_t) * nn},
+        {(void**)&ws.fpos, sizeof(int32_t) * nn},
         {(void**)&ws.vkeys, sizeof(uint64_t) * nn},
         {(void**)&ws.vkeys_alt, sizeof(uint64_t) * nn},
         {(void**)&ws.hist, sizeof(uint32_t) * hist_len},
@@ -61,25 +60,34 @@ harp_status ws_ensure(Workspace& ws, int64_t n, int64_t m, cudaStream_t s) {
         {(void**)&ws.acc, sizeof(uint64_t) * kOutLen},
     };
     size_t total = 0;
-    for (const Part& p : parts) total += align_up(p.bytes);
+    for (const Part& p : parts) {
+        if (base) *p.p = base + total;
+        total += align_up(p.bytes);
+    }
+    if (base) {
+        ws.te = reinterpret_cast<uint32_t*>(ws.colsp + mm);
+        ws.hist_len = hist_len;
+        ws.scan_tmp_len = tmp_len;
+        ws.base = base;
+        ws.bytes = total;
+        ws.n = n;
+        ws.m = m;
+    }
+    return total;
+}
+
+harp_status ws_ensure(Workspace& ws, int64_t n, int64_t m, cudaStream_t s) {
+    if (ws.base && ws.n == n && ws.m == m) return HARP_OK;
+    ws_release(ws, s);
+    Workspace probe;
+    const size_t total = ws_layout(probe, nullptr, n, m);
     void* base = nullptr;
     cudaError_t e = cudaMallocAsync(&base, total, s);
     if (e != cudaSuccess) {
         record_cuda_error(e);
         return e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
     }
-    size_t off = 0;
-    for (const Part& p : parts) {
-        *p.p = (char*)base + off;
-        off += align_up(p.bytes);
-    }
-    ws.te = reinterpret_cast<uint32_t*>(ws.colsp + mm);
-    ws.hist_len = hist_len;
-    ws.scan_tmp_len = tmp_len;
-    ws.base = base;
-    ws.bytes = total;
-    ws.n = n;
-    ws.m = m;
+    ws_layout(ws, static_cast<unsigned char*>(base), n, m);
     return HARP_OK;
 }
 

@@ -93,6 +93,7 @@ struct Workspace {
     int64_t* off = nullptr;        // [n+1] rank-order CSR offsets
     int32_t* cols = nullptr;       // [2m]  rank-order CSR columns, rows ascending
     int32_t* dplus = nullptr;      // [n]   out-degree (neighbours with larger rank)
+    int32_t* fpos = nullptr;       // [n]   first row position holding a neighbour of degree >= 2
     int64_t* offp = nullptr;       // [n+1] out-CSR offsets
     int32_t* colsp = nullptr;      // [m]   out-CSR columns
     uint32_t* te = nullptr;        // [m]   per out-arc triangle count t_e (colsp and te are contiguous)
@@ -105,6 +106,9 @@ struct Workspace {
     uint64_t* acc = nullptr;       // [kOutLen]
 };
 
+// The workspace layout for (n, m): assigns every array of ws inside [base, base + returned bytes)
+// (with base == nullptr it only computes the size).  Shared by every path that builds a workspace.
+size_t ws_layout(Workspace& ws, unsigned char* base, int64_t n, int64_t m);
 // stream-ordered allocation helpers
 harp_status ws_ensure(Workspace& ws, int64_t n, int64_t m, cudaStream_t s);
 void ws_release(Workspace& ws, cudaStream_t s);

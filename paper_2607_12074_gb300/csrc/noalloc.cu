@@ -28,51 +28,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device
 
-size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Lay out a Workspace for (n, m) inside [base, base + cap); returns the bytes used (0 if it does
-// not fit).  Same arrays and sizes as the allocating path.
+// Lay out a Workspace for (n, m) inside [base, base + cap) with the library's one layout; returns
+// the bytes used, or 0 if it does not fit.
 size_t carve(unsigned char* base, size_t cap, int64_t n, int64_t m, Workspace& ws) {
-    const int64_t nn = n > 0 ? n : 1;
-    const int64_t mm = m > 0 ? m : 1;
-    const size_t hist_len = radix_hist_len(nn);
-    const size_t tmp_len = scan_tmp_needed(nn) + scan_tmp_needed((int64_t)hist_len) + 64;
-    struct Part { void** p; size_t bytes; };
-    Part parts[] = {
-        {(void**)&ws.deg, sizeof(int32_t) * nn},
-        {(void**)&ws.order, sizeof(int32_t) * nn},
-        {(void**)&ws.perm, sizeof(int32_t) * nn},
-        {(void**)&ws.dplus, sizeof(int32_t) * nn},
-        {(void**)&ws.vkeys, sizeof(uint64_t) * nn},
-        {(void**)&ws.vkeys_alt, sizeof(uint64_t) * nn},
-        {(void**)&ws.hist, sizeof(uint32_t) * hist_len},
-        {(void**)&ws.off, sizeof(int64_t) * (nn + 1)},
-        {(void**)&ws.offp, sizeof(int64_t) * (nn + 1)},
-        {(void**)&ws.cols, sizeof(int32_t) * 2 * mm},
-        {(void**)&ws.colsp, sizeof(int32_t) * 2 * mm},
-        {(void**)&ws.q_tri, sizeof(int32_t) * nn},
-        {(void**)&ws.q_mid, sizeof(int32_t) * 2 * nn},
-        {(void**)&ws.q_win, sizeof(int32_t) * 2 * nn},
-        {(void**)&ws.win_prefix, sizeof(int64_t) * (nn + 1)},
-        {(void**)&ws.scan_tmp, sizeof(int64_t) * tmp_len},
-        {(void**)&ws.acc, sizeof(uint64_t) * kOutLen},
-    };
-    size_t off = 0;
-    for (const Part& p : parts) off += up256(p.bytes);
-    if (off > cap) return 0;
-    off = 0;
-    for (const Part& p : parts) {
-        *p.p = base + off;
-        off += up256(p.bytes);
-    }
-    ws.te = reinterpret_cast<uint32_t*>(ws.colsp + mm);
-    ws.hist_len = hist_len;
-    ws.scan_tmp_len = tmp_len;
-    ws.base = base;
-    ws.bytes = off;
-    ws.n = n;
-    ws.m = m;
-    return off;
+    Workspace probe;
+    const size_t need = ws_layout(probe, nullptr, n, m);
+    if (need > cap) return 0;
+    return ws_layout(ws, base, n, m);
 }
 
 // Device address of the static array for the current device (looked up once per device).

@@ -79,14 +79,17 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restric
                                                         const int32_t* __restrict__ deg,
                                                         const int64_t* __restrict__ off, int64_t n,
                                                         int32_t* __restrict__ cols,
-                                                        int32_t* __restrict__ dplus) {
-    __shared__ int64_t range[2];
+                                                        int32_t* __restrict__ dplus,
+                                                        int32_t* __restrict__ fpos) {
+    __shared__ int64_t range[3];
     if (threadIdx.x == 0) {
         range[0] = first_above(deg, n, 0);
         range[1] = first_above(deg, n, kTierA);
+        range[2] = first_above(deg, n, 1);  // n1: first rank of degree >= 2
     }
     __syncthreads();
     const int64_t lo = range[0], hi = range[1];
+    const int32_t n1 = (int32_t)range[2];
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -106,12 +109,18 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restric
         }
         if (l < d) cols[off[i] + l] = v;
         uint32_t above = __ballot_sync(kFull, l < d && v > (int32_t)i);
-        if (l == 0) dplus[i] = __popc(above);
+        uint32_t leaves = __ballot_sync(kFull, l < d && v < n1);
+        if (l == 0) {
+            dplus[i] = __popc(above);
+            fpos[i] = __popc(leaves);
+        }
     }
     // rows with d == 0 (a prefix of the rank order)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lo;
-         i += (int64_t)gridDim.x * blockDim.x)
+         i += (int64_t)gridDim.x * blockDim.x) {
         dplus[i] = 0;
+        fpos[i] = 0;
+    }
 }
 
 // Tier B: 32 < d <= 4096, one block per row, bitonic sort in shared memory.
@@ -122,23 +131,29 @@ __global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restri
                                                          const int32_t* __restrict__ deg,
                                                          const int64_t* __restrict__ off, int64_t n,
                                                          int32_t* __restrict__ cols,
-                                                         int32_t* __restrict__ dplus) {
+                                                         int32_t* __restrict__ dplus,
+                                                         int32_t* __restrict__ fpos) {
     __shared__ int32_t buf[kTierB];
-    __shared__ int64_t range[2];
-    __shared__ int cnt_below;
+    __shared__ int64_t range[3];
+    __shared__ int cnt_below, cnt_leaf;
     if (threadIdx.x == 0) {
         range[0] = first_above(deg, n, kTierA);
         range[1] = first_above(deg, n, kTierB);
+        range[2] = first_above(deg, n, 1);
     }
     __syncthreads();
     const int64_t lo = range[0], hi = range[1];
+    const int32_t n1 = (int32_t)range[2];
     for (int64_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
         const int d = deg[i];
         int P = 64;
         while (P < d) P <<= 1;
         const int64_t src = goff[order[i]];
         for (int k = threadIdx.x; k < P; k += blockDim.x) buf[k] = (k < d) ? perm[gcols[src + k]] : 0x7fffffff;
-        if (threadIdx.x == 0) cnt_below = 0;
+        if (threadIdx.x == 0) {
+            cnt_below = 0;
+            cnt_leaf = 0;
+        }
         __syncthreads();
         for (int k = 2; k <= P; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -155,16 +170,22 @@ __global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restri
                 __syncthreads();
             }
         }
-        int below = 0;
+        int below = 0, leaf = 0;
         for (int k = threadIdx.x; k < d; k += blockDim.x) {
             int32_t x = buf[k];
             cols[off[i] + k] = x;
             below += x < (int32_t)i;
+            leaf += x < n1;
         }
         below = warp_sum(below);
+        leaf = warp_sum(leaf);
         if (lane_id() == 0 && below) atomicAdd(&cnt_below, below);
+        if (lane_id() == 0 && leaf) atomicAdd(&cnt_leaf, leaf);
         __syncthreads();
-        if (threadIdx.x == 0) dplus[i] = d - cnt_below;
+        if (threadIdx.x == 0) {
+            dplus[i] = d - cnt_below;
+            fpos[i] = cnt_leaf;
+        }
         __syncthreads();
     }
 }
@@ -183,17 +204,20 @@ __global__ void __launch_bounds__(kHubThreads) k_sort_rows_hub(const int64_t* __
                                                                const int64_t* __restrict__ off, int64_t n,
                                                                int nbits, int32_t* __restrict__ cols,
                                                                int32_t* __restrict__ tmp,
-                                                               int32_t* __restrict__ dplus) {
+                                                               int32_t* __restrict__ dplus,
+                                                               int32_t* __restrict__ fpos) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[kHubWarps][256];
-    __shared__ int64_t range[2];
-    __shared__ int cnt_below;
+    __shared__ int64_t range[3];
+    __shared__ int cnt_below, cnt_leaf;
     if (threadIdx.x == 0) {
         range[0] = first_above(deg, n, kTierB);
         range[1] = n;
+        range[2] = first_above(deg, n, 1);
     }
     __syncthreads();
     const int64_t lo = range[0], hi = range[1];
+    const int32_t n1 = (int32_t)range[2];
     const int npass = (nbits + 7) / 8;
     const int w = threadIdx.x >> 5, l = lane_id();
     const uint32_t lt = lanemask_lt();
@@ -257,15 +281,27 @@ __global__ void __launch_bounds__(kHubThreads) k_sort_rows_hub(const int64_t* __
             }
             __syncthreads();
         }
-        // out-degree: elements above i in the sorted row
-        if (threadIdx.x == 0) cnt_below = 0;
+        // out-degree: elements above i in the sorted row; fpos: elements of degree <= 1
+        if (threadIdx.x == 0) {
+            cnt_below = 0;
+            cnt_leaf = 0;
+        }
         __syncthreads();
-        int below = 0;
-        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) below += cols[dst0 + k] < (int32_t)i;
+        int below = 0, leaf = 0;
+        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
+            const int32_t x = cols[dst0 + k];
+            below += x < (int32_t)i;
+            leaf += x < n1;
+        }
         below = warp_sum(below);
+        leaf = warp_sum(leaf);
         if (l == 0 && below) atomicAdd(&cnt_below, below);
+        if (l == 0 && leaf) atomicAdd(&cnt_leaf, leaf);
         __syncthreads();
-        if (threadIdx.x == 0) dplus[i] = (int32_t)(d - cnt_below);
+        if (threadIdx.x == 0) {
+            dplus[i] = (int32_t)(d - cnt_below);
+            fpos[i] = cnt_leaf;
+        }
         __syncthreads();
     }
 }
@@ -316,17 +352,18 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     HARP_TRY(exclusive_scan_i32_to_i64(ws.deg, ws.off, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {
         k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
-                                                                ws.off, n, ws.cols, ws.dplus);
+                                                                ws.off, n, ws.cols, ws.dplus, ws.fpos);
         HARP_LAUNCHED();
         k_sort_rows_block<<<152 * 4, 512, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n,
-                                                   ws.cols, ws.dplus);
+                                                   ws.cols, ws.dplus, ws.fpos);
         HARP_LAUNCHED();
         // the out-CSR columns + t_e region (2m int32) is free until k_out_csr: hub sort ping-pong
         k_sort_rows_hub<<<152, kHubThreads, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n, b,
-                                                     ws.cols, ws.colsp, ws.dplus);
+                                                     ws.cols, ws.colsp, ws.dplus, ws.fpos);
         HARP_LAUNCHED();
     } else {
         HARP_CK(cudaMemsetAsync(ws.dplus, 0, (size_t)n * sizeof(int32_t), s));
+        HARP_CK(cudaMemsetAsync(ws.fpos, 0, (size_t)n * sizeof(int32_t), s));
     }
     HARP_TRY(exclusive_scan_i32_to_i64(ws.dplus, ws.offp, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {

@@ -13,7 +13,7 @@ Per unit (int32 ids and counters = 4 B, int64 offsets = 8 B):
                 part of N+(v) up to max N+(u) (4 each); per triangle: 3 t_e updates (8 each, RMW);
                 per out-arc: its own t_e update (8)
   wedge (C4)    per root u and per pass over its lower neighbours (1 pass, or 1 per x-window):
-                N-(u) (4 d-) + offsets of each w (16 d-); per wedge element x: 4
+                N-(u) (4 d-) + offsets of each w (16 d-); per wedge element x of degree >= 2: 4
   reduction     t_e read: 4 m
 """
 from __future__ import annotations
@@ -96,18 +96,30 @@ def meter(n, src, dst, c4_warp_max=512, c4_cta_max=8192):
     out.update(tri_units)
     out["tri_probes_total"] = int(probed[~is_last].sum())
 
-    # ---- wedge anchors: root u, w in N-(u) (arcs (u -> w), w < u), segment = pos of u in row w
+    # ---- wedge anchors: root u, w in N-(u) (arcs (u -> w), w < u).  Leaves (degree 1) never close a
+    # 4-cycle, so a segment runs from fpos[w] (first neighbour of degree >= 2) to pos_w(u).
     down = cols < rows
     ru, rw = rows[down], cols[down]
-    # pos_w(u) = position of u in row w = pos of the reverse arc (w -> u)
     rev = np.searchsorted(rows * n + cols, rw * n + ru)
-    seg = pos[rev]
+    n1 = int(np.searchsorted(deg, 2))                 # first rank of degree >= 2
+    r256 = int(np.searchsorted(deg, 256))
+    r64k = int(np.searchsorted(deg, 65536))
+    fpos = np.bincount(rows[cols < n1], minlength=n)  # neighbours of degree <= 1 lead every row
+    seg = np.maximum(pos[rev] - fpos[rw], 0)
     W = np.bincount(ru, weights=seg, minlength=n).astype(np.int64)
     dm = split
     tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= c4_warp_max, 0, np.where(W <= c4_cta_max, 1, 2)))
-    width = np.where(dm <= 255, 8, np.where(dm <= 65535, 16, 32))
-    span = WIN_WORDS * (32 // width)
-    nwin = np.where(tier == 2, (np.arange(n) + span - 1) // span, 1)
+    u_ids = np.arange(n, dtype=np.int64)
+    by_dm = np.where(dm <= 255, 8, np.where(dm <= 65535, 16, 32))
+    nwin = np.zeros(n, np.int64)
+    bounds = [n1, max(r256, n1), max(r64k, n1)]
+    for band, width_x in enumerate((8, 16, 32)):
+        lo = np.minimum(bounds[band], u_ids)
+        hi = np.minimum(bounds[band + 1], u_ids) if band < 2 else u_ids
+        hi = np.maximum(hi, lo)
+        span = WIN_WORDS * (32 // np.minimum(by_dm, width_x))
+        nwin += (hi - lo + span - 1) // span
+    nwin = np.where(tier == 2, nwin, 1)
     for t, name in ((0, "c4_small"), (1, "c4_mid"), (2, "c4_window")):
         sel = tier == t
         passes = nwin[sel]
