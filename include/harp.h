@@ -176,6 +176,35 @@ harp_status harp_last_stage_times(float ms_out[HARP_NSEGMENTS], int64_t* launche
 int64_t harp_launch_count(void);
 
 /* ------------------------------------------------------------------------------------------------
+ * Batched counting (thousands of graphs of uneven size).  The members' CSRs are packed into one
+ * device arena (their disjoint union); every anchor's statistics go to its own member, so the whole
+ * batch runs as one sequence of persistent kernels over global heavy-first work queues.  The
+ * sequence is captured once into a CUDA graph and replayed by every harp_batch_count.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct harp_batch harp_batch;
+
+/* Pack G handles (all on the current device) into a batch.  The members are copied; they may be
+ * freed afterwards.  HARP_EOVERFLOW if the union exceeds 2^31-1 vertices or 2^32-1 arcs. */
+harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_batch** out);
+
+/* Count every member; counts_out[G][6] (host) and optionally stats_out[G][8] (host, HARP_STAT_*
+ * order).  The first call (and any call with a different plan) captures the CUDA graph; later calls
+ * replay it on `stream` and return after the results are on the host.  plan->flags may carry
+ * HARP_PLAN_NO_GRAPH to launch kernels one by one instead. */
+harp_status harp_batch_count(harp_batch* b, const harp_plan* plan, uint64_t (*counts_out)[6],
+                             uint64_t (*stats_out)[8], void* stream);
+
+/* Number of members, union sizes and device bytes held by a batch.  Any output may be NULL. */
+harp_status harp_batch_info(const harp_batch* b, int64_t* graphs, int64_t* n_total, int64_t* m_total,
+                            size_t* device_bytes);
+
+void harp_batch_free(harp_batch* b);
+
+/* One-shot convenience: create, count once (kernels launched directly), free. */
+harp_status harp_count4_batch(const harp_csr* const* graphs, int64_t G, const harp_plan* plan,
+                              uint64_t (*counts_out)[6], void* stream);
+
+/* ------------------------------------------------------------------------------------------------
  * Counting without allocation.  The paper has no counterpart: this entry point exists for callers
  * that may not allocate device memory while they run (code inside another framework's
  * pre-reserved memory regime, services that forbid cudaMalloc/cudaFree after start-up because an

@@ -29,6 +29,8 @@ void note_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed)
 
 cudaError_t prof_mark(cudaStream_t s, int seg) {
     if (!g_profiling.load(std::memory_order_relaxed) || !t_marks[0]) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return cudaSuccess;
     t_marked[seg + 1] = true;
     return cudaEventRecord(t_marks[seg + 1], s);
 }

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __res
                                                             int32_t* __restrict__ q_mid,
                                                             int32_t* __restrict__ q_win,
                                                             int32_t* __restrict__ wcount,
-                                                            uint64_t* __restrict__ acc) {
+                                                            uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t* my_keys = reinterpret_cast<int32_t*>(smem_raw) + (threadIdx.x >> 5) * kSmallSlots;
     uint32_t* my_cnt = reinterpret_cast<uint32_t*>(smem_raw + kSmallWarps * kSmallSlots * sizeof(int32_t)) +
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __res
             my_cnt[i] = 0;
         }
         __syncwarp();
+        uint64_t a_c4 = 0;
         for (int64_t a0 = 0; a0 < dm; a0 += 32) {
             const int64_t a = a0 + l;
             int64_t base = 0;
@@ -235,7 +236,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __res
                 base = off[wv] + f;
                 len = p > f ? (int)(p - f) : 0;
             }
-            warp_flat(cols, base, len, [&](int32_t x) { c4 += hash_add(my_keys, my_cnt, P - 1, x); });
+            warp_flat(cols, base, len, [&](int32_t x) { a_c4 += hash_add(my_keys, my_cnt, P - 1, x); });
+        }
+        if (sink.batch()) {
+            a_c4 = warp_sum(a_c4);
+            if (l == 0) sink_add(sink, u, G_C4, a_c4);
+        } else {
+            c4 += a_c4;
         }
         __syncwarp();
     }
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(kMidThreads) k_c4_mid(const int64_t* __restric
                                                         const int32_t* __restrict__ dplus,
                                                         const int32_t* __restrict__ fpos,
                                                         const int32_t* __restrict__ q_mid, int64_t n,
-                                                        uint64_t* __restrict__ acc) {
+                                                        uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem_raw + kMidSlots * sizeof(int32_t));
@@ -283,6 +290,7 @@ __global__ void __launch_bounds__(kMidThreads) k_c4_mid(const int64_t* __restric
             cnt[i] = 0;
         }
         __syncthreads();
+        uint64_t a_c4 = 0;
         for (int64_t a0 = (int64_t)w * 32; a0 < dm; a0 += (int64_t)NW * 32) {
             const int64_t a = a0 + lane_id();
             int64_t base = 0;
@@ -294,9 +302,15 @@ __global__ void __launch_bounds__(kMidThreads) k_c4_mid(const int64_t* __restric
                 base = off[wv] + f;
                 len = p > f ? (int)(p - f) : 0;
             }
-            warp_segments(cols, base, len, [&](int32_t x) { c4 += hash_add(keys, cnt, P - 1, x); });
+            warp_segments(cols, base, len, [&](int32_t x) { a_c4 += hash_add(keys, cnt, P - 1, x); });
         }
         __syncthreads();
+        if (sink.batch()) {
+            const uint64_t t = block_sum_u64(a_c4, red);
+            if (threadIdx.x == 0) sink_add(sink, u, G_C4, t);
+        } else {
+            c4 += a_c4;
+        }
     }
     c4 = block_sum_u64(c4, red);
     if (threadIdx.x == 0 && c4) atomicAdd((unsigned long long*)&acc[ACC_C4], (unsigned long long)c4);
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_c4_window(const int64_t* __r
                                                            const int32_t* __restrict__ fpos, int64_t n,
                                                            const int32_t* __restrict__ q_win,
                                                            const int64_t* __restrict__ win_prefix,
-                                                           uint64_t* __restrict__ acc) {
+                                                           uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t* cw = reinterpret_cast<uint32_t*>(smem_raw);
     __shared__ int64_t s_item;
@@ -416,16 +430,23 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_c4_window(const int64_t* __r
         const int64_t ub = off[u];
         const bool first = xlo == B.n1;
         const bool last = xhi == (int64_t)u;
+        uint64_t a_c4 = 0;
         if (width == 8)
             window_pass<8>(off, cols, offp, colsp, deg, dplus, fpos, u, ub, dm, (int32_t)xlo, (int32_t)xhi, first,
-                           last, cw, &s_group, c4);
+                           last, cw, &s_group, a_c4);
         else if (width == 16)
             window_pass<16>(off, cols, offp, colsp, deg, dplus, fpos, u, ub, dm, (int32_t)xlo, (int32_t)xhi, first,
-                            last, cw, &s_group, c4);
+                            last, cw, &s_group, a_c4);
         else
             window_pass<32>(off, cols, offp, colsp, deg, dplus, fpos, u, ub, dm, (int32_t)xlo, (int32_t)xhi, first,
-                            last, cw, &s_group, c4);
+                            last, cw, &s_group, a_c4);
         __syncthreads();
+        if (sink.batch()) {
+            const uint64_t t = block_sum_u64(a_c4, red);
+            if (threadIdx.x == 0) sink_add(sink, u, G_C4, t);
+        } else {
+            c4 += a_c4;
+        }
     }
     c4 = block_sum_u64(c4, red);
     if (threadIdx.x == 0 && c4) atomicAdd((unsigned long long*)&acc[ACC_C4], (unsigned long long)c4);
@@ -443,25 +464,26 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     if (cta_max < warp_max) cta_max = warp_max;
 
     int32_t* wcount = ws.q_win + n;
+    const Sink sink{ws.acc, ws.gid, ws.accG};
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
     k_c4_small<<<152 * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus,
                                                           ws.fpos, n, warp_max, cta_max, ws.q_mid, ws.q_win, wcount,
-                                                          ws.acc);
+                                                          ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_SMALL));
     const size_t mid_smem = (size_t)kMidSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_smem));
     k_c4_mid<<<152, kMidThreads, mid_smem, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, ws.fpos,
-                                                ws.q_mid, n, ws.acc);
+                                                ws.q_mid, n, ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_MID));
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
     const size_t win_smem = (size_t)kWinWords * sizeof(uint32_t);
     HARP_CK(cudaFuncSetAttribute(k_c4_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
     k_c4_window<<<152, kWinThreads, win_smem, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, ws.fpos,
-                                                   n, ws.q_win, ws.win_prefix, ws.acc);
+                                                   n, ws.q_win, ws.win_prefix, ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_WINDOW));
     return HARP_OK;

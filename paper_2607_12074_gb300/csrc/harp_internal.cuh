@@ -76,6 +76,10 @@ enum : int {
     kOutLen = 40
 };
 
+// Per-graph accumulator slots (batch mode), kGStride per graph.
+constexpr int kGStride = 8;
+enum : int { G_T = 0, G_K4, G_C4, G_S, G_PW, G_PAWSUM, G_D };
+
 // ---------------------------------------------------------------------------------------------
 // Workspace for one counting pass, sized for (n, m) and cached in the graph handle.
 // ---------------------------------------------------------------------------------------------
@@ -104,6 +108,10 @@ struct Workspace {
     int64_t* scan_tmp = nullptr;   // scan partials
     size_t scan_tmp_len = 0;
     uint64_t* acc = nullptr;       // [kOutLen]
+    // batch mode only (the union of many graphs); nullptr for a single graph
+    const int32_t* gid_in = nullptr;  // [n] graph of each input (union) vertex
+    int32_t* gid = nullptr;           // [n] graph of each rank-order vertex
+    uint64_t* accG = nullptr;         // [G * kGStride] per-graph accumulators
 };
 
 // The workspace layout for (n, m): assigns every array of ws inside [base, base + returned bytes)
@@ -159,6 +167,8 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
 
 // reduce.cu: sum_e C(t_e,2), closure (step a7); writes acc[OUT_COUNTS..], acc[OUT_STATS..]
 harp_status reduce_and_close(const harp_csr* g, Workspace& ws, cudaStream_t s);
+// batch mode: per-graph sum_e C(t_e,2) and closure; d_out holds 16 uint64 per graph
+harp_status reduce_and_close_batch(const harp_csr* g, Workspace& ws, int64_t G, uint64_t* d_out, cudaStream_t s);
 
 // planner.cpp
 void default_plan(harp_plan* p);
@@ -195,6 +205,21 @@ __device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t* smem32) 
     }
     __syncthreads();
     return r;
+}
+
+// Where anchor statistics go.  Single graph: thread-local sums, one block reduction and one atomic
+// per block at the end (acc[ACC_*]).  Batch (the disjoint union of many graphs): every anchor's sum
+// goes to its own graph's slot accG[gid[anchor] * kGStride + G_*] as soon as the anchor is done.
+struct Sink {
+    uint64_t* acc;
+    const int32_t* gid;
+    uint64_t* accG;
+    __device__ __forceinline__ bool batch() const { return gid != nullptr; }
+};
+
+__device__ __forceinline__ void sink_add(const Sink& s, int32_t anchor, int gslot, uint64_t v) {
+    if (v) atomicAdd((unsigned long long*)&s.accG[(int64_t)s.gid[anchor] * kGStride + gslot],
+                     (unsigned long long)v);
 }
 
 // lower_bound in a sorted int32 array a[0..len): first index with a[i] >= key

@@ -34,13 +34,19 @@ unsigned grid_for(int64_t work, int threads, int64_t cap = 152 * 64) {
 }
 
 __global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b,
-                              uint64_t* __restrict__ keys, uint64_t* __restrict__ acc) {
+                              uint64_t* __restrict__ keys, uint64_t* __restrict__ acc,
+                              const int32_t* __restrict__ gid_in, uint64_t* __restrict__ accG) {
     uint64_t s3 = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         uint64_t d = (uint64_t)(off[v + 1] - off[v]);
         keys[v] = (d << b) | (uint64_t)v;
-        s3 += choose3_u64(d);
+        const uint64_t c3 = choose3_u64(d);
+        if (gid_in) {
+            if (c3) atomicAdd((unsigned long long*)&accG[(int64_t)gid_in[v] * kGStride + G_S], (unsigned long long)c3);
+        } else {
+            s3 += c3;
+        }
     }
     __shared__ uint64_t red[32];
     uint64_t t = block_sum_u64(s3, red);
@@ -48,7 +54,8 @@ __global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b,
 }
 
 __global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t n, int b, int32_t* __restrict__ order,
-                          int32_t* __restrict__ perm, int32_t* __restrict__ deg) {
+                          int32_t* __restrict__ perm, int32_t* __restrict__ deg,
+                          const int32_t* __restrict__ gid_in, int32_t* __restrict__ gid) {
     const uint64_t mask = ((uint64_t)1 << b) - 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -57,6 +64,7 @@ __global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t n, int b, i
         order[i] = old;
         perm[old] = (int32_t)i;
         deg[i] = (int32_t)(k >> b);
+        if (gid_in) gid[i] = gid_in[old];
     }
 }
 
@@ -312,7 +320,7 @@ __global__ void __launch_bounds__(256) k_out_csr(const int64_t* __restrict__ off
                                                  const int32_t* __restrict__ dplus,
                                                  const int32_t* __restrict__ deg,
                                                  const int64_t* __restrict__ offp, int64_t n,
-                                                 int32_t* __restrict__ colsp, uint64_t* __restrict__ acc) {
+                                                 int32_t* __restrict__ colsp, Sink sink) {
     __shared__ uint64_t red[32];
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -324,14 +332,21 @@ __global__ void __launch_bounds__(256) k_out_csr(const int64_t* __restrict__ off
         const int64_t srcb = off[i + 1] - dp;
         const int64_t dstb = offp[i];
         const uint64_t di1 = (uint64_t)deg[i] - 1;
+        uint64_t row_pw = 0;
         for (int64_t k = l; k < dp; k += 32) {
             const int32_t v = cols[srcb + k];
             colsp[dstb + k] = v;
-            pw += di1 * ((uint64_t)deg[v] - 1);
+            row_pw += di1 * ((uint64_t)deg[v] - 1);
+        }
+        if (sink.batch()) {
+            row_pw = warp_sum(row_pw);
+            if (l == 0) sink_add(sink, (int32_t)i, G_PW, row_pw);
+        } else {
+            pw += row_pw;
         }
     }
     pw = block_sum_u64(pw, red);
-    if (threadIdx.x == 0 && pw) atomicAdd((unsigned long long*)&acc[ACC_PW], (unsigned long long)pw);
+    if (threadIdx.x == 0 && pw) atomicAdd((unsigned long long*)&sink.acc[ACC_PW], (unsigned long long)pw);
 }
 
 }  // namespace
@@ -342,12 +357,12 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     const int b = bits_for(n);
     const int bd = bits_for(g->max_deg);
 
-    k_vertex_keys<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, b, ws.vkeys, ws.acc);
+    k_vertex_keys<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, b, ws.vkeys, ws.acc, ws.gid_in, ws.accG);
     HARP_LAUNCHED();
     uint64_t* k0 = ws.vkeys;
     uint64_t* k1 = ws.vkeys_alt;
     HARP_TRY(radix_sort_u64(&k0, &k1, n, 0, b + bd, ws.hist, ws.scan_tmp, ws.scan_tmp_len, s));
-    k_relabel<<<grid_for(n, 256), 256, 0, s>>>(k0, n, b, ws.order, ws.perm, ws.deg);
+    k_relabel<<<grid_for(n, 256), 256, 0, s>>>(k0, n, b, ws.order, ws.perm, ws.deg, ws.gid_in, ws.gid);
     HARP_LAUNCHED();
     HARP_TRY(exclusive_scan_i32_to_i64(ws.deg, ws.off, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {
@@ -367,8 +382,9 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     }
     HARP_TRY(exclusive_scan_i32_to_i64(ws.dplus, ws.offp, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {
+        const Sink sink{ws.acc, ws.gid, ws.accG};
         k_out_csr<<<grid_for(n * 32, 256), 256, 0, s>>>(ws.off, ws.cols, ws.dplus, ws.deg, ws.offp, n, ws.colsp,
-                                                         ws.acc);
+                                                         sink);
         HARP_LAUNCHED();
         HARP_CK(cudaMemsetAsync(ws.te, 0, (size_t)m * sizeof(uint32_t), s));
     }

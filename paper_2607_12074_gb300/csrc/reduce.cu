@@ -62,7 +62,72 @@ __global__ void __launch_bounds__(256) k_reduce_close(const uint32_t* __restrict
     acc[OUT_STATS + HARP_STAT_EDGES] = (uint64_t)m;
 }
 
+// Batch mode: sum_e C(t_e, 2) per graph (warp per row of the out-CSR; gid[u] is the row's graph).
+__global__ void __launch_bounds__(256) k_reduce_rows_batch(const int64_t* __restrict__ offp,
+                                                           const uint32_t* __restrict__ te, int64_t n, Sink sink) {
+    const int l = lane_id();
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wid; u < n; u += nw) {
+        const int64_t b = offp[u], e = offp[u + 1];
+        if (b == e) continue;
+        uint64_t d = 0;
+        for (int64_t a = b + l; a < e; a += 32) d += choose2_u64((uint64_t)te[a]);
+        d = warp_sum(d);
+        if (l == 0) sink_add(sink, (int32_t)u, G_D, d);
+    }
+}
+
+// Batch mode: the closure of every graph (one thread per graph); out holds 16 uint64 per graph.
+__global__ void k_close_batch(const uint64_t* __restrict__ accG, int64_t G, uint64_t* __restrict__ out) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t* a = accG + g * kGStride;
+        const uint64_t T = a[G_T], K4 = a[G_K4], C4n = a[G_C4], S = a[G_S];
+        const uint64_t P = a[G_PW] - 3 * T;
+        const uint64_t pawn = a[G_PAWSUM] - 6 * T;
+        const uint64_t D = a[G_D];
+        const uint64_t diamond = D - 6 * K4;
+        const uint64_t c4 = C4n - diamond - 3 * K4;
+        const uint64_t paw = pawn - 4 * diamond - 12 * K4;
+        const uint64_t path = P - 2 * paw - 4 * c4 - 6 * diamond - 12 * K4;
+        const uint64_t star = S - paw - 2 * diamond - 4 * K4;
+        uint64_t* o = out + g * 16;
+        o[HARP_STAR3] = star;
+        o[HARP_PATH4] = path;
+        o[HARP_PAW] = paw;
+        o[HARP_CYCLE4] = c4;
+        o[HARP_DIAMOND] = diamond;
+        o[HARP_CLIQUE4] = K4;
+        o[6] = 0;
+        o[7] = 0;
+        o[8 + HARP_STAT_TRIANGLES] = T;
+        o[8 + HARP_STAT_K4] = K4;
+        o[8 + HARP_STAT_C4] = C4n;
+        o[8 + HARP_STAT_STARS] = S;
+        o[8 + HARP_STAT_PATHS] = P;
+        o[8 + HARP_STAT_PAWS] = pawn;
+        o[8 + HARP_STAT_DIAMONDS] = D;
+        o[8 + HARP_STAT_EDGES] = 0;  // filled by the host, which knows every member's m
+    }
+}
+
 }  // namespace
+
+harp_status reduce_and_close_batch(const harp_csr* g, Workspace& ws, int64_t G, uint64_t* d_out, cudaStream_t s) {
+    const Sink sink{ws.acc, ws.gid, ws.accG};
+    int64_t blocks = (g->n * 32 + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (g->m > 0) {
+        k_reduce_rows_batch<<<(unsigned)blocks, 256, 0, s>>>(ws.offp, ws.te, g->n, sink);
+        HARP_LAUNCHED();
+    }
+    int64_t cb = (G + 255) / 256;
+    if (cb < 1) cb = 1;
+    k_close_batch<<<(unsigned)cb, 256, 0, s>>>(ws.accG, G, d_out);
+    HARP_LAUNCHED();
+    return HARP_OK;
+}
 
 harp_status reduce_and_close(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     int64_t blocks = (g->m + 255) / 256;

@@ -68,6 +68,18 @@ __device__ __forceinline__ int lb_smem(const int32_t* a, int P, int32_t y) {
     return j;
 }
 
+// single-graph mode: one block reduction and one atomic per statistic at the end of the kernel
+__device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint64_t k4, uint64_t paw, uint64_t* red) {
+    tri = block_sum_u64(tri, red);
+    k4 = block_sum_u64(k4, red);
+    paw = block_sum_u64(paw, red);
+    if (threadIdx.x == 0 && !sink.batch()) {
+        if (tri) atomicAdd((unsigned long long*)&sink.acc[ACC_T], (unsigned long long)tri);
+        if (k4) atomicAdd((unsigned long long*)&sink.acc[ACC_K4], (unsigned long long)k4);
+        if (paw) atomicAdd((unsigned long long*)&sink.acc[ACC_PAWSUM], (unsigned long long)paw);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Warp-local mode.
 // ---------------------------------------------------------------------------------------------
@@ -79,8 +91,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
                                                            const int32_t* __restrict__ deg,
                                                            const int32_t* __restrict__ q,
                                                            const unsigned long long* __restrict__ cnt,
-                                                           uint32_t* __restrict__ te,
-                                                           uint64_t* __restrict__ acc) {
+                                                           uint32_t* __restrict__ te, Sink sink) {
     __shared__ int32_t sL[kWarpsPerBlock][32];
     __shared__ uint32_t sRow[kWarpsPerBlock][32];
     __shared__ uint64_t red[32];
@@ -125,25 +136,31 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
         const uint32_t myrow = sRow[w][l];
         const uint32_t own = (l < d) ? (uint32_t)__popc(myrow) + col : 0u;
         if (own) atomicAdd(&te[ub + l], own);
-        tri += (uint64_t)__popc(myrow);
+        const uint64_t a_tri = (uint64_t)__popc(myrow);
+        uint64_t a_k4 = 0;
         uint32_t bits = myrow;
         while (bits) {
             const int j = __ffs(bits) - 1;
             bits &= bits - 1;
-            k4 += (uint64_t)__popc(myrow & sRow[w][j]);
+            a_k4 += (uint64_t)__popc(myrow & sRow[w][j]);
         }
         const uint64_t dx = (l < d) ? (uint64_t)deg[x] : 0;
-        paw += (uint64_t)own * dx + (uint64_t)__popc(myrow) * (uint64_t)deg[u];
+        const uint64_t a_paw = (uint64_t)own * dx + a_tri * (uint64_t)deg[u];
+        if (sink.batch()) {
+            const uint64_t t1 = warp_sum(a_tri), t2 = warp_sum(a_k4), t3 = warp_sum(a_paw);
+            if (l == 0) {
+                sink_add(sink, u, G_T, t1);
+                sink_add(sink, u, G_K4, t2);
+                sink_add(sink, u, G_PAWSUM, t3);
+            }
+        } else {
+            tri += a_tri;
+            k4 += a_k4;
+            paw += a_paw;
+        }
         __syncwarp();
     }
-    tri = block_sum_u64(tri, red);
-    k4 = block_sum_u64(k4, red);
-    paw = block_sum_u64(paw, red);
-    if (threadIdx.x == 0) {
-        if (tri) atomicAdd((unsigned long long*)&acc[ACC_T], (unsigned long long)tri);
-        if (k4) atomicAdd((unsigned long long*)&acc[ACC_K4], (unsigned long long)k4);
-        if (paw) atomicAdd((unsigned long long*)&acc[ACC_PAWSUM], (unsigned long long)paw);
-    }
+    flush_block(sink, tri, k4, paw, red);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__
                                                      const int32_t* __restrict__ q, int64_t n, int cls,
                                                      const unsigned long long* __restrict__ cnt,
                                                      unsigned long long* __restrict__ ticket,
-                                                     uint32_t* __restrict__ te, uint64_t* __restrict__ acc) {
+                                                     uint32_t* __restrict__ te, Sink sink) {
     using S = CtaSmem<DMAX, THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S& s = *reinterpret_cast<S*>(smem_raw);
@@ -219,18 +236,19 @@ __global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__
         }
         __syncthreads();
         // 4-cliques: warp per row i, lane per candidate bit j of the current word
+        uint64_t a_tri = 0, a_k4 = 0, a_paw = 0;
         for (int i = w; i < d - 1; i += NW) {
             const uint32_t* Ri = &s.R[i * WS];
             for (int ww = (i + 1) >> 5; ww < W; ++ww) {
                 const uint32_t word = Ri[ww];
                 if (!word) continue;
-                tri += (l == 0) ? (uint64_t)__popc(word) : 0;
+                a_tri += (l == 0) ? (uint64_t)__popc(word) : 0;
                 if ((word >> l) & 1u) {
                     const int j = (ww << 5) + l;
                     const uint32_t* Rj = &s.R[j * WS];
                     uint32_t c = 0;
                     for (int x = ww; x < W; ++x) c += __popc(Ri[x] & Rj[x]);
-                    k4 += c;
+                    a_k4 += c;
                 }
             }
         }
@@ -238,24 +256,31 @@ __global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__
             const uint32_t o = s.own[i];
             if (o) {
                 atomicAdd(&te[ub + i], o);
-                paw += (uint64_t)o * (uint64_t)deg[s.L[i]];
+                a_paw += (uint64_t)o * (uint64_t)deg[s.L[i]];
             }
         }
         __syncthreads();
         // T_u * d_u for the paw sum (T_u = sum of popc over rows; recomputed cheaply)
         uint32_t tu = 0;
         for (int i = threadIdx.x; i < d * WS; i += THREADS) tu += __popc(s.R[i]);
-        paw += (uint64_t)tu * (uint64_t)deg[u];
+        a_paw += (uint64_t)tu * (uint64_t)deg[u];
         __syncthreads();
+        if (sink.batch()) {
+            const uint64_t t1 = block_sum_u64(a_tri, s.red);
+            const uint64_t t2 = block_sum_u64(a_k4, s.red);
+            const uint64_t t3 = block_sum_u64(a_paw, s.red);
+            if (threadIdx.x == 0) {
+                sink_add(sink, u, G_T, t1);
+                sink_add(sink, u, G_K4, t2);
+                sink_add(sink, u, G_PAWSUM, t3);
+            }
+        } else {
+            tri += a_tri;
+            k4 += a_k4;
+            paw += a_paw;
+        }
     }
-    tri = block_sum_u64(tri, s.red);
-    k4 = block_sum_u64(k4, s.red);
-    paw = block_sum_u64(paw, s.red);
-    if (threadIdx.x == 0) {
-        if (tri) atomicAdd((unsigned long long*)&acc[ACC_T], (unsigned long long)tri);
-        if (k4) atomicAdd((unsigned long long*)&acc[ACC_K4], (unsigned long long)k4);
-        if (paw) atomicAdd((unsigned long long*)&acc[ACC_PAWSUM], (unsigned long long)paw);
-    }
+    flush_block(sink, tri, k4, paw, s.red);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -277,7 +302,7 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
                                                       const int32_t* __restrict__ q, int64_t n,
                                                       const unsigned long long* __restrict__ cnt,
                                                       int32_t* __restrict__ scratch, int64_t scratch_per_warp,
-                                                      uint32_t* __restrict__ te, uint64_t* __restrict__ acc) {
+                                                      uint32_t* __restrict__ te, Sink sink) {
     __shared__ uint64_t red[32];
     const int w = threadIdx.x >> 5, l = lane_id();
     const int nw = blockDim.x >> 5;
@@ -289,6 +314,7 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
         const int64_t ub = offp[u], ue = offp[u + 1];
         if (tri_class((int)(ue - ub)) != 3) continue;
         const uint64_t du = (uint64_t)deg[u];
+        const uint64_t tri0 = tri, k40 = k4, paw0 = paw;
         for (int64_t a = ub + w; a < ue; a += nw) {  // warp per out-arc (u, v)
             const int32_t v = colsp[a];
             const int64_t b = offp[v], e = offp[v + 1];
@@ -330,15 +356,21 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
             }
             __syncwarp();
         }
+        if (sink.batch()) {  // this anchor's part goes to its graph; the running sums stay unchanged
+            const uint64_t t1 = block_sum_u64(tri - tri0, red);
+            const uint64_t t2 = block_sum_u64(k4 - k40, red);
+            const uint64_t t3 = block_sum_u64(paw - paw0, red);
+            if (threadIdx.x == 0) {
+                sink_add(sink, u, G_T, t1);
+                sink_add(sink, u, G_K4, t2);
+                sink_add(sink, u, G_PAWSUM, t3);
+            }
+            tri = tri0;
+            k4 = k40;
+            paw = paw0;
+        }
     }
-    tri = block_sum_u64(tri, red);
-    k4 = block_sum_u64(k4, red);
-    paw = block_sum_u64(paw, red);
-    if (threadIdx.x == 0) {
-        if (tri) atomicAdd((unsigned long long*)&acc[ACC_T], (unsigned long long)tri);
-        if (k4) atomicAdd((unsigned long long*)&acc[ACC_K4], (unsigned long long)k4);
-        if (paw) atomicAdd((unsigned long long*)&acc[ACC_PAWSUM], (unsigned long long)paw);
-    }
+    flush_block(sink, tri, k4, paw, red);
 }
 
 template <int DMAX, int THREADS>
@@ -349,7 +381,7 @@ harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slo
                                  (int)smem));
     k_tri_cta<DMAX, THREADS><<<152 * blocks_per_sm, THREADS, smem, s>>>(
         ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, (const unsigned long long*)&ws.acc[Q_TRI_WARP],
-        (unsigned long long*)&ws.acc[ticket_slot], ws.te, ws.acc);
+        (unsigned long long*)&ws.acc[ticket_slot], ws.te, Sink{ws.acc, ws.gid, ws.accG});
     HARP_LAUNCHED();
     return HARP_OK;
 }
@@ -367,7 +399,8 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.q_tri, cnt);
     HARP_LAUNCHED();
-    k_tri_warp<<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, cnt, ws.te, ws.acc);
+    const Sink sink{ws.acc, ws.gid, ws.accG};
+    k_tri_warp<<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, cnt, ws.te, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_TRI_WARP));
     HARP_TRY((launch_cta<kCtaSmallMax, 256>(g, ws, 1, T_TRI_S, 6, s)));
@@ -385,7 +418,7 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
         int32_t* scratch = nullptr;
         HARP_CK(cudaMallocAsync((void**)&scratch, bytes, s));
         k_tri_fallback<<<fb_blocks, 256, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, n, cnt, scratch, per_warp,
-                                                 ws.te, ws.acc);
+                                                 ws.te, sink);
         note_launch();
         cudaError_t e = cudaGetLastError();
         cudaFreeAsync(scratch, s);

@@ -101,6 +101,14 @@ def lib():
         L.harp_count4_stats.argtypes = [vp, ctypes.POINTER(harp_plan), pu64, pu64]
         L.harp_count4_async.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp]
         L.harp_count4_noalloc.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.harp_batch_create.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp)]
+        L.harp_batch_count.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp, vp]
+        L.harp_batch_info.argtypes = [vp, pi64, pi64, pi64, ctypes.POINTER(ctypes.c_size_t)]
+        L.harp_batch_free.argtypes = [vp]
+        L.harp_batch_free.restype = None
+        L.harp_count4_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(harp_plan), vp, vp]
+        for name in ("harp_batch_create", "harp_batch_count", "harp_batch_info", "harp_count4_batch"):
+            getattr(L, name).restype = i32
         L.harp_set_profiling.argtypes = [i32]
         L.harp_last_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float), pi64]
         L.harp_launch_count.argtypes = []
@@ -252,6 +260,56 @@ def harp_count4_noalloc(n: int, m: int, d_offsets: int, d_cols: int, d_out: int,
     """
     _check(lib().harp_count4_noalloc(int(n), int(m), ctypes.c_void_p(d_offsets), ctypes.c_void_p(d_cols),
                                      ctypes.c_void_p(d_out), _stream_handle(stream)), "harp_count4_noalloc")
+
+
+class Batch:
+    """Owns a harp_batch (the packed union of many handles and its captured CUDA graph)."""
+
+    def __init__(self, handle: int, G: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.G = G
+
+    def close(self):
+        if self.handle:
+            lib().harp_batch_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def harp_batch_create(graphs) -> Batch:
+    arr = (ctypes.c_void_p * max(1, len(graphs)))(*[g.handle.value for g in graphs])
+    out = ctypes.c_void_p()
+    _check(lib().harp_batch_create(arr, len(graphs), ctypes.byref(out)), "harp_batch_create")
+    return Batch(out.value, len(graphs))
+
+
+def harp_batch_count(b: Batch, plan: harp_plan | None = None, stream=None, stats: bool = False):
+    counts = np.zeros((max(1, b.G), 6), np.uint64)
+    st = np.zeros((max(1, b.G), 8), np.uint64)
+    _check(lib().harp_batch_count(b.handle, _plan_ref(plan), counts.ctypes.data, st.ctypes.data if stats else None,
+                                  _stream_handle(stream)), "harp_batch_count")
+    return (counts[:b.G], st[:b.G]) if stats else counts[:b.G]
+
+
+def harp_batch_info(b: Batch) -> dict:
+    g, n, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    by = ctypes.c_size_t()
+    _check(lib().harp_batch_info(b.handle, ctypes.byref(g), ctypes.byref(n), ctypes.byref(m), ctypes.byref(by)),
+           "harp_batch_info")
+    return {"graphs": g.value, "n": n.value, "m": m.value, "device_bytes": by.value}
+
+
+def harp_count4_batch(graphs, plan: harp_plan | None = None, stream=None) -> np.ndarray:
+    arr = (ctypes.c_void_p * max(1, len(graphs)))(*[g.handle.value for g in graphs])
+    counts = np.zeros((max(1, len(graphs)), 6), np.uint64)
+    _check(lib().harp_count4_batch(arr, len(graphs), _plan_ref(plan), counts.ctypes.data, _stream_handle(stream)),
+           "harp_count4_batch")
+    return counts[:len(graphs)]
 
 
 def harp_set_profiling(enable: bool) -> None:
