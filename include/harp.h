@@ -219,7 +219,7 @@ harp_status harp_count4_batch(const harp_csr* const* graphs, int64_t G, const ha
  *   d_out      device uint64[16]: [0..5] counts, [8..15] statistics (HARP_STAT_* order), written
  *              when `stream` reaches the end of the work
  *   stream     cudaStream_t; the call only enqueues work and returns
- * Scratch lives in one file-scope static device array of 32 MiB that every GPU used by the process
+ * Scratch lives in one file-scope static device array of 64 MiB that every GPU used by the process
  * holds until exit.  The first call on a device looks up that array's device address (once per
  * device, with the device current); make that first call before any stream capture.  All calls
  * share the array and clear what must start at zero themselves: calls whose work overlaps on the

@@ -47,6 +47,9 @@ size_t ws_layout(Workspace& ws, unsigned char* base, int64_t n, int64_t m) {
         {(void**)&ws.perm, sizeof(int32_t) * nn},
         {(void**)&ws.dplus, sizeof(int32_t) * nn},
         {(void**)&ws.fpos, sizeof(int32_t) * nn},
+        {(void**)&ws.rev, sizeof(int32_t) * 2 * mm},
+        {(void**)&ws.bpos, sizeof(int32_t) * kGridCap * nn},
+        {(void**)&ws.ginfo, sizeof(int64_t) * kGInfo},
         {(void**)&ws.vkeys, sizeof(uint64_t) * nn},
         {(void**)&ws.vkeys_alt, sizeof(uint64_t) * nn},
         {(void**)&ws.hist, sizeof(uint32_t) * hist_len},

@@ -54,6 +54,8 @@ struct harp_batch {
     int32_t* d_gid_in = nullptr;      // [N]
     int32_t* d_gid = nullptr;         // [N]
     uint64_t* d_accG = nullptr;       // [G * kGStride]
+    int64_t* d_gbase = nullptr;       // [G + 1] first union vertex of each member
+    int64_t* d_ginfo = nullptr;       // [G * kGInfo]
     uint64_t* d_out = nullptr;        // [G * 16]
     uint64_t* h_out = nullptr;        // pinned [G * 16]
     cudaGraphExec_t exec = nullptr;
@@ -75,6 +77,8 @@ harp_status batch_release(harp_batch* b) {
     if (b->d_gid_in) cudaFreeAsync(b->d_gid_in, s);
     if (b->d_gid) cudaFreeAsync(b->d_gid, s);
     if (b->d_accG) cudaFreeAsync(b->d_accG, s);
+    if (b->d_gbase) cudaFreeAsync(b->d_gbase, s);
+    if (b->d_ginfo) cudaFreeAsync(b->d_ginfo, s);
     if (b->d_out) cudaFreeAsync(b->d_out, s);
     if (s) {
         cudaStreamSynchronize(s);
@@ -129,14 +133,17 @@ harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_bat
     cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
     cudaStream_t s = b->capture_stream;
     std::vector<MemberDesc> desc((size_t)G);
+    std::vector<int64_t> gbase((size_t)G + 1);
     int64_t vb = 0, ab = 0;
     for (int64_t g = 0; g < G; ++g) {
         const harp_csr* c = graphs[g];
         desc[(size_t)g] = MemberDesc{c->off, c->cols, c->n, vb, ab};
+        gbase[(size_t)g] = vb;
         b->m_of[(size_t)g] = c->m;
         vb += c->n;
         ab += 2 * c->m;
     }
+    gbase[(size_t)G] = vb;
     const size_t gg = (size_t)(G > 0 ? G : 1);
     b->u.device = dev;
     b->u.stream = s;
@@ -150,6 +157,10 @@ harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_bat
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_gid, sizeof(int32_t) * (size_t)(N > 0 ? N : 1), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_accG, sizeof(uint64_t) * kGStride * gg, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_out, sizeof(uint64_t) * 16 * gg, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_gbase, sizeof(int64_t) * (gg + 1), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_ginfo, sizeof(int64_t) * kGInfo * gg, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_gbase, gbase.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_out, sizeof(uint64_t) * 16 * gg);
     if (e == cudaSuccess && G > 0)
         e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(MemberDesc) * (size_t)G, cudaMemcpyHostToDevice, s);
@@ -183,6 +194,9 @@ harp_status harp_batch_count(harp_batch* b, const harp_plan* user_plan, uint64_t
     b->u.ws.gid_in = b->d_gid_in;
     b->u.ws.gid = b->d_gid;
     b->u.ws.accG = b->d_accG;
+    b->u.ws.G = b->G;
+    b->u.ws.gbase = b->d_gbase;
+    b->u.ws.ginfo = b->d_ginfo;
     const bool use_graph = !(plan.flags & HARP_PLAN_NO_GRAPH);
     if (use_graph && (!b->exec || !same_plan(plan, b->plan_captured))) {
         if (b->exec) {

@@ -8,41 +8,47 @@
 // value, which sums to the same total without a second pass.
 //
 // Two bounds shape the work: cnt(x) <= d(x) (every wedge into x uses a distinct neighbour of x) and
-// cnt(x) <= d-(u).  Hence
-//   * x of degree 1 never complete a cycle: the x-range is [n1, u) with n1 the first rank of
-//     degree >= 2 (rank order puts isolated vertices and leaves first), and every row's segment
-//     starts at fpos[w] (the first neighbour of degree >= 2, found once when the row was sorted);
-//   * a dense counter for x fits 8 bits if d(x) <= 255 or d-(u) <= 255, 16 bits below 65536.  Rank
-//     order makes degree monotone in x, so the x-range splits into at most three bands
-//     [n1, r256), [r256, r64k), [r64k, u) whose counters are 8, 16 and 32 bits wide (narrower when
-//     d-(u) allows), and most of rank space is covered by 8-bit windows.
+// cnt(x) <= d-(u).  Rank order sorts each graph's vertices by degree, so inside a graph's rank range
+//   * x of degree 1 never complete a cycle: x runs over [n1, u) with n1 the graph's first rank of
+//     degree >= 2, and every row's segment starts at fpos[w] (its first neighbour of degree >= 2);
+//   * a dense counter for x fits 8 bits while d(x) <= 255 and 16 bits while d(x) <= 65535, so the
+//     x-range splits into the bands [n1, r256), [r256, r64k), [r64k, end) with 8-, 16- and 32-bit
+//     counters.  The bands cut into windows of 100 KiB of counters form a fixed grid per graph, so the
+//     row position of every grid boundary is computed once per row (bpos) instead of being searched
+//     for every (root, lower neighbour, window).
+// pos_w(u) itself is computed once per lower arc (rev) by a fully parallel pass.
 //
 // The frontier (the set of x) is not an induced class: whether u ~ x or w1 ~ w2 holds decides
 // whether the cycle is induced, a diamond or part of a 4-clique; the closure resolves that mix
 // (Section III-C explains why a frontier alone must not be reused as an induced state).
 //
-// Work per root W(u) = sum_{w in N-(u)} (pos_w(u) - fpos[w]) decides the execution mode:
-//   W <= warp_max           one warp, hash table in shared memory (warp-local mode)
-//   W <= cta_max            one block, hash table in shared memory (CTA mode)
-//   larger                  one block per (root, x-window): dense packed counters in shared memory
+// Work per root W(u) = sum_{w in N-(u)} (pos_w(u) - fpos[w]) picks the execution mode:
+//   W <= warp_max   one warp, hash table in shared memory (warp-local mode)
+//   larger          one block per (root, grid window): dense packed counters in shared memory
+//                   (CTA mode); lower neighbours are handed to warps in groups of 32, heaviest first,
+//                   and segments of 2048+ elements are split across all warps of the block.
 #include "harp_internal.cuh"
 
 namespace harp {
 namespace {
 
 constexpr int32_t kEmpty = -1;
-constexpr int kWinThreads = 1024;
-constexpr int kWinWords = 51200;             // 200 KiB of packed counters per window
-constexpr int kMidThreads = 512;
-constexpr int kMidSlots = 16384;             // 128 KiB hash table
+constexpr int kWinThreads = 512;
+constexpr int kWinWords = 25600;             // 100 KiB of packed counters per window
 constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
-constexpr int kSmallSlots = 1024;            // per-warp hash table
-constexpr int kLong = 32;                    // segments at least this long are read warp-coalesced
+constexpr int kSmallSlots = 1024;            // per-warp hash table (W <= 512)
+constexpr int kLong = 32;                    // segments this long are read warp-coalesced
+constexpr int kSplit = 2048;                 // segments this long are split across the block
+constexpr int kSplitQ = 128;                 // split-queue capacity per window item
+constexpr int kChunk = 1024;                 // elements per split chunk
 
-// first rank whose degree is > t (deg is non-decreasing in rank order)
-__device__ __forceinline__ int64_t rank_above(const int32_t* __restrict__ deg, int64_t n, int32_t t) {
-    int64_t lo = 0, hi = n;
+// ---------------------------------------------------------------------------------------------
+// Per-graph band and grid geometry (ginfo: kGInfo int64 per graph).
+// ---------------------------------------------------------------------------------------------
+enum : int { GI_LO = 0, GI_HI, GI_N1, GI_B1, GI_B2, GI_NWIN };
+
+__device__ __forceinline__ int64_t first_above_in(const int32_t* __restrict__ deg, int64_t lo, int64_t hi, int32_t t) {
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         if (deg[mid] <= t) lo = mid + 1;
@@ -51,56 +57,122 @@ __device__ __forceinline__ int64_t rank_above(const int32_t* __restrict__ deg, i
     return lo;
 }
 
-struct Bands {
-    int64_t n1, r256, r64k;  // first rank of degree >= 2, >= 256, >= 65536
+__device__ __forceinline__ int64_t span_of(int width) { return (int64_t)kWinWords * (32 / width); }
+
+struct Band {
+    int64_t start, end;
+    int width;
 };
 
-__device__ __forceinline__ Bands load_bands(const int32_t* __restrict__ deg, int64_t n) {
-    Bands b;
-    b.n1 = rank_above(deg, n, 1);
-    b.r256 = rank_above(deg, n, 255);
-    b.r64k = rank_above(deg, n, 65535);
-    return b;
+__device__ __forceinline__ Band band_of(const int64_t* gi, int b) {
+    Band r;
+    r.start = b == 0 ? gi[GI_N1] : (b == 1 ? gi[GI_B1] : gi[GI_B2]);
+    r.end = b == 0 ? gi[GI_B1] : (b == 1 ? gi[GI_B2] : gi[GI_HI]);
+    r.width = b == 0 ? 8 : (b == 1 ? 16 : 32);
+    return r;
 }
 
-__device__ __forceinline__ int width_for(int band, int64_t dm) {
-    const int by_dm = dm <= 255 ? 8 : (dm <= 65535 ? 16 : 32);
-    const int by_x = band == 0 ? 8 : (band == 1 ? 16 : 32);
-    return by_dm < by_x ? by_dm : by_x;
-}
-
-__device__ __forceinline__ int64_t span_for(int width) { return (int64_t)kWinWords * (32 / width); }
-
-// The x-range [n1, u) of root u as bands; returns band b's [lo, hi) (empty if lo >= hi).
-__device__ __forceinline__ void band_range(const Bands& B, int band, int64_t u, int64_t& lo, int64_t& hi) {
-    const int64_t a[4] = {B.n1, B.r256 > B.n1 ? B.r256 : B.n1, B.r64k > B.n1 ? B.r64k : B.n1, u};
-    lo = a[band] < u ? a[band] : u;
-    hi = a[band + 1] < u ? a[band + 1] : u;
-    if (band == 2) hi = u;
-    if (hi < lo) hi = lo;
-}
-
-__device__ __forceinline__ int64_t window_count(const Bands& B, int64_t u, int64_t dm) {
-    int64_t total = 0;
-    for (int band = 0; band < 3; ++band) {
-        int64_t lo, hi;
-        band_range(B, band, u, lo, hi);
-        if (hi > lo) {
-            const int64_t span = span_for(width_for(band, dm));
-            total += (hi - lo + span - 1) / span;
+// window j of the graph's grid: [xlo, xhi) and counter width; false if j is past the grid
+__device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_t& xlo, int64_t& xhi, int& width) {
+    for (int b = 0; b < 3; ++b) {
+        const Band B = band_of(gi, b);
+        if (B.end <= B.start) continue;
+        const int64_t S = span_of(B.width);
+        const int64_t nb = (B.end - B.start + S - 1) / S;
+        if (j < nb) {
+            xlo = B.start + j * S;
+            xhi = xlo + S < B.end ? xlo + S : B.end;
+            width = B.width;
+            return true;
         }
+        j -= nb;
+    }
+    return false;
+}
+
+// number of grid windows that intersect [n1, u)
+__device__ __forceinline__ int64_t windows_below(const int64_t* gi, int64_t u) {
+    int64_t total = 0;
+    for (int b = 0; b < 3; ++b) {
+        const Band B = band_of(gi, b);
+        const int64_t e = B.end < u ? B.end : u;
+        if (e <= B.start) continue;
+        const int64_t S = span_of(B.width);
+        total += (e - B.start + S - 1) / S;
     }
     return total;
 }
 
-// position of u in w's row, for w < u: u lies in the out-list N+(w)
-__device__ __forceinline__ int64_t pos_of_root(const int64_t* __restrict__ offp, const int32_t* __restrict__ colsp,
-                                               const int32_t* __restrict__ deg, const int32_t* __restrict__ dplus,
-                                               int32_t w, int32_t u) {
-    const int64_t pb = offp[w];
-    return (int64_t)(deg[w] - dplus[w]) + lower_bound_i32(colsp + pb, offp[w + 1] - pb, u);
+__global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int64_t* __restrict__ gbase,
+                           int64_t G, int64_t* __restrict__ ginfo) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = gbase ? gbase[g] : 0, hi = gbase ? gbase[g + 1] : n;
+        const int64_t n1 = first_above_in(deg, lo, hi, 1);
+        const int64_t r256 = first_above_in(deg, lo, hi, 255);
+        const int64_t r64k = first_above_in(deg, lo, hi, 65535);
+        int64_t* gi = ginfo + g * kGInfo;
+        gi[GI_LO] = lo;
+        gi[GI_HI] = hi;
+        gi[GI_N1] = n1;
+        gi[GI_B1] = r256 > n1 ? r256 : n1;
+        gi[GI_B2] = r64k > n1 ? r64k : n1;
+        gi[GI_NWIN] = windows_below(gi, hi);
+    }
 }
 
+// rev[a] = pos_w(u) for every lower arc (u -> w) at row position a of u (warp per root)
+__global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                                                const int64_t* __restrict__ offp, const int32_t* __restrict__ colsp,
+                                                const int32_t* __restrict__ deg, const int32_t* __restrict__ dplus,
+                                                int64_t n, int32_t* __restrict__ rev) {
+    const int l = lane_id();
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wid; u < n; u += nw) {
+        const int64_t dm = (int64_t)deg[u] - dplus[u];
+        if (dm < 2) continue;
+        const int64_t ub = off[u];
+        for (int64_t a = l; a < dm; a += 32) {
+            const int32_t w = cols[ub + a];
+            const int64_t pb = offp[w];
+            rev[ub + a] = (deg[w] - dplus[w]) + (int32_t)lower_bound_i32(colsp + pb, offp[w + 1] - pb, (int32_t)u);
+        }
+    }
+}
+
+// fpos[w] = row position of w's first neighbour of degree >= 2 (the graph's n1 boundary), and
+// bpos[w * kGridCap + k] = row position of the k-th boundary of w's grid (k <= nwin), if it fits
+__global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                          const int32_t* __restrict__ gid, const int64_t* __restrict__ ginfo, int64_t n,
+                          int32_t* __restrict__ fpos, int32_t* __restrict__ bpos) {
+    const int64_t total = n * kGridCap;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = t / kGridCap;
+        const int k = (int)(t % kGridCap);
+        const int64_t* gi = ginfo + (gid ? (int64_t)gid[w] : 0) * kGInfo;
+        const int64_t nwin = gi[GI_NWIN];
+        if (k == 0) {
+            const int64_t wb = off[w];
+            const int32_t f = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)gi[GI_N1]);
+            fpos[w] = f;
+            if (nwin + 1 <= kGridCap) bpos[t] = f;
+            continue;
+        }
+        if (nwin + 1 > kGridCap || k > nwin) continue;
+        int64_t bound = gi[GI_HI];
+        if (k < nwin) {
+            int64_t xhi;
+            int width;
+            grid_window(gi, k, bound, xhi, width);
+        }
+        const int64_t wb = off[w];
+        bpos[t] = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)bound);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Segment traversal helpers.
+// ---------------------------------------------------------------------------------------------
 // Warp-cooperative traversal of 32 segments (lane l owns cols[base_l .. base_l + len_l)):
 // flattened so that every lane takes one element per round.
 template <typename F>
@@ -159,64 +231,74 @@ __device__ __forceinline__ uint32_t hash_add(int32_t* keys, uint32_t* cnt, uint3
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pass 1: every root (warp per root): W(u); small roots counted here, others queued.
+// Classification: every root (warp per root, descending rank so heavy roots are queued first).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                                                     const int32_t* __restrict__ deg,
+                                                     const int32_t* __restrict__ dplus,
+                                                     const int32_t* __restrict__ fpos,
+                                                     const int32_t* __restrict__ rev,
+                                                     const int32_t* __restrict__ gid,
+                                                     const int64_t* __restrict__ ginfo, int64_t n, uint32_t warp_max,
+                                                     int32_t* __restrict__ q_small, int32_t* __restrict__ q_win,
+                                                     int32_t* __restrict__ wcount, uint64_t* __restrict__ acc) {
+    const int l = lane_id();
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long* qcnt_small = (unsigned long long*)&acc[Q_C4_MID];
+    unsigned long long* qcnt_win = (unsigned long long*)&acc[Q_C4_WIN];
+    for (int64_t k = wid; k < n; k += nw) {
+        const int32_t u = (int32_t)(n - 1 - k);
+        const int64_t dm = (int64_t)deg[u] - dplus[u];
+        if (dm < 2) continue;
+        const int64_t ub = off[u];
+        uint64_t W = 0;
+        for (int64_t a = l; a < dm; a += 32) {
+            const int32_t f = fpos[cols[ub + a]];
+            const int32_t p = rev[ub + a];
+            W += p > f ? (uint64_t)(p - f) : 0;
+        }
+        W = warp_sum(W);
+        if (W == 0 || l != 0) continue;
+        if (W <= warp_max) {
+            const unsigned long long slot = atomicAdd(qcnt_small, 1ull);
+            q_small[slot] = u;
+            q_small[n + slot] = (int32_t)W;
+        } else {
+            const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
+            const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
+            q_win[slot] = u;
+            wcount[slot] = (int32_t)windows_below(gi, u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Warp-local mode: one warp per queued small root, hash table in shared memory.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ cols,
-                                                            const int64_t* __restrict__ offp,
-                                                            const int32_t* __restrict__ colsp,
                                                             const int32_t* __restrict__ deg,
                                                             const int32_t* __restrict__ dplus,
-                                                            const int32_t* __restrict__ fpos, int64_t n,
-                                                            uint32_t warp_max, uint32_t cta_max,
-                                                            int32_t* __restrict__ q_mid,
-                                                            int32_t* __restrict__ q_win,
-                                                            int32_t* __restrict__ wcount,
+                                                            const int32_t* __restrict__ fpos,
+                                                            const int32_t* __restrict__ rev,
+                                                            const int32_t* __restrict__ q_small, int64_t n,
                                                             uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t* my_keys = reinterpret_cast<int32_t*>(smem_raw) + (threadIdx.x >> 5) * kSmallSlots;
     uint32_t* my_cnt = reinterpret_cast<uint32_t*>(smem_raw + kSmallWarps * kSmallSlots * sizeof(int32_t)) +
                        (threadIdx.x >> 5) * kSmallSlots;
     __shared__ uint64_t red[32];
-    __shared__ Bands sB;
-    if (threadIdx.x == 0) sB = load_bands(deg, n);
-    __syncthreads();
-    const Bands B = sB;
-    const int w = threadIdx.x >> 5, l = lane_id();
-    const int64_t wid = (int64_t)blockIdx.x * kSmallWarps + w;
-    const int64_t nw = (int64_t)gridDim.x * kSmallWarps;
-    unsigned long long* qcnt_mid = (unsigned long long*)&acc[Q_C4_MID];
-    unsigned long long* qcnt_win = (unsigned long long*)&acc[Q_C4_WIN];
+    const int l = lane_id();
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nq = (int64_t)acc[Q_C4_MID];
     uint64_t c4 = 0;
-    for (int64_t k = wid; k < n - B.n1; k += nw) {
-        const int32_t u = (int32_t)(n - 1 - k);  // descending rank: heavy roots queued first
+    for (int64_t k = wid; k < nq; k += nw) {
+        const int32_t u = q_small[k];
+        const uint32_t W = (uint32_t)q_small[n + k];
         const int64_t dm = (int64_t)deg[u] - dplus[u];
-        if (dm < 2) continue;
         const int64_t ub = off[u];
-        // W(u) = sum over w in N-(u) of the segment lengths pos_w(u) - fpos[w]
-        uint64_t W = 0;
-        for (int64_t a = l; a < dm; a += 32) {
-            const int32_t wv = cols[ub + a];
-            const int64_t p = pos_of_root(offp, colsp, deg, dplus, wv, u);
-            const int64_t f = fpos[wv];
-            W += p > f ? (uint64_t)(p - f) : 0;
-        }
-        W = warp_sum(W);
-        if (W == 0) continue;
-        if (W > warp_max) {
-            if (l == 0) {
-                if (W <= cta_max) {
-                    const unsigned long long slot = atomicAdd(qcnt_mid, 1ull);
-                    q_mid[slot] = u;
-                    q_mid[n + slot] = (int32_t)W;  // second half: work, sizes the CTA table
-                } else {
-                    const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
-                    q_win[slot] = u;
-                    wcount[slot] = (int32_t)window_count(B, u, dm);
-                }
-            }
-            continue;
-        }
         uint32_t P = 32;
         while (P < 2 * W) P <<= 1;
         for (uint32_t i = l; i < P; i += 32) {
@@ -231,10 +313,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __res
             int len = 0;
             if (a < dm) {
                 const int32_t wv = cols[ub + a];
-                const int64_t p = pos_of_root(offp, colsp, deg, dplus, wv, u);
-                const int64_t f = fpos[wv];
+                const int32_t f = fpos[wv];
+                const int32_t p = rev[ub + a];
                 base = off[wv] + f;
-                len = p > f ? (int)(p - f) : 0;
+                len = p > f ? p - f : 0;
             }
             warp_flat(cols, base, len, [&](int32_t x) { a_c4 += hash_add(my_keys, my_cnt, P - 1, x); });
         }
@@ -251,74 +333,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __res
 }
 
 // ---------------------------------------------------------------------------------------------
-// CTA mode: one block per queued root, shared-memory hash table.
-// ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kMidThreads) k_c4_mid(const int64_t* __restrict__ off,
-                                                        const int32_t* __restrict__ cols,
-                                                        const int64_t* __restrict__ offp,
-                                                        const int32_t* __restrict__ colsp,
-                                                        const int32_t* __restrict__ deg,
-                                                        const int32_t* __restrict__ dplus,
-                                                        const int32_t* __restrict__ fpos,
-                                                        const int32_t* __restrict__ q_mid, int64_t n,
-                                                        uint64_t* __restrict__ acc, Sink sink) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem_raw + kMidSlots * sizeof(int32_t));
-    __shared__ int64_t s_item;
-    __shared__ uint64_t red[32];
-    const int w = threadIdx.x >> 5;
-    constexpr int NW = kMidThreads / 32;
-    const int64_t nq = (int64_t)acc[Q_C4_MID];
-    unsigned long long* ticket = (unsigned long long*)&acc[T_C4_MID];
-    uint64_t c4 = 0;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ticket, 1ull);
-        __syncthreads();
-        const int64_t k = s_item;
-        __syncthreads();
-        if (k >= nq) break;
-        const int32_t u = q_mid[k];
-        const int64_t dm = (int64_t)deg[u] - dplus[u];
-        const int64_t ub = off[u];
-        // table size: next power of two >= 2 W (distinct x <= W), at most kMidSlots
-        const uint32_t W = (uint32_t)q_mid[n + k];
-        uint32_t P = 64;
-        while (P < 2 * W && P < (uint32_t)kMidSlots) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += kMidThreads) {
-            keys[i] = kEmpty;
-            cnt[i] = 0;
-        }
-        __syncthreads();
-        uint64_t a_c4 = 0;
-        for (int64_t a0 = (int64_t)w * 32; a0 < dm; a0 += (int64_t)NW * 32) {
-            const int64_t a = a0 + lane_id();
-            int64_t base = 0;
-            int len = 0;
-            if (a < dm) {
-                const int32_t wv = cols[ub + a];
-                const int64_t p = pos_of_root(offp, colsp, deg, dplus, wv, u);
-                const int64_t f = fpos[wv];
-                base = off[wv] + f;
-                len = p > f ? (int)(p - f) : 0;
-            }
-            warp_segments(cols, base, len, [&](int32_t x) { a_c4 += hash_add(keys, cnt, P - 1, x); });
-        }
-        __syncthreads();
-        if (sink.batch()) {
-            const uint64_t t = block_sum_u64(a_c4, red);
-            if (threadIdx.x == 0) sink_add(sink, u, G_C4, t);
-        } else {
-            c4 += a_c4;
-        }
-    }
-    c4 = block_sum_u64(c4, red);
-    if (threadIdx.x == 0 && c4) atomicAdd((unsigned long long*)&acc[ACC_C4], (unsigned long long)c4);
-}
-
-// ---------------------------------------------------------------------------------------------
-// Windowed CTA mode: one block per (root, window of x); dense packed counters in shared memory.
-// Groups of 32 lower neighbours are handed to warps dynamically, heaviest (highest-degree) first.
+// Windowed CTA mode: one block per (root, grid window); dense packed counters in shared memory.
 // ---------------------------------------------------------------------------------------------
 template <int WIDTH>
 __device__ __forceinline__ uint32_t counter_add(uint32_t* cw, uint32_t r) {
@@ -333,18 +348,27 @@ __device__ __forceinline__ uint32_t counter_add(uint32_t* cw, uint32_t r) {
     }
 }
 
+struct WinShared {
+    int group;                 // next group of 32 lower neighbours
+    int nsplit;                // entries pushed to the split queue
+    int chunk;                 // next split chunk
+    int64_t split_base[kSplitQ];
+    int32_t split_len[kSplitQ];
+    int32_t split_pre[kSplitQ + 1];
+};
+
 template <int WIDTH>
 __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
-                                            const int64_t* __restrict__ offp, const int32_t* __restrict__ colsp,
-                                            const int32_t* __restrict__ deg, const int32_t* __restrict__ dplus,
-                                            const int32_t* __restrict__ fpos, int32_t u, int64_t ub, int64_t dm,
-                                            int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
-                                            int* s_group, uint64_t& c4) {
+                                            const int32_t* __restrict__ fpos, const int32_t* __restrict__ rev,
+                                            const int32_t* __restrict__ bpos, bool table, int64_t j, int64_t ub,
+                                            int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
+                                            WinShared& sh, uint64_t& c4) {
     const int l = lane_id();
+    auto add = [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); };
     const int ngroups = (int)((dm + 31) >> 5);
     for (;;) {
         int g = 0;
-        if (l == 0) g = atomicAdd(s_group, 1);
+        if (l == 0) g = atomicAdd(&sh.group, 1);
         g = __shfl_sync(kFull, g, 0);
         if (g >= ngroups) break;
         const int64_t a = (int64_t)(ngroups - 1 - g) * 32 + l;  // heaviest groups first
@@ -353,36 +377,70 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
         if (a < dm) {
             const int32_t wv = cols[ub + a];
             const int64_t wb = off[wv];
-            const int64_t rowlen = off[wv + 1] - wb;
-            const int64_t p0 = first ? (int64_t)fpos[wv] : lower_bound_i32(cols + wb, rowlen, xlo);
-            const int64_t p1 = last ? pos_of_root(offp, colsp, deg, dplus, wv, u)
-                                    : lower_bound_i32(cols + wb, rowlen, xhi);
+            int64_t p0, p1;
+            if (first) p0 = fpos[wv];
+            else if (table) p0 = bpos[(int64_t)wv * kGridCap + j];
+            else p0 = lower_bound_i32(cols + wb, off[wv + 1] - wb, xlo);
+            if (last) p1 = rev[ub + a];
+            else if (table) p1 = bpos[(int64_t)wv * kGridCap + j + 1];
+            else p1 = lower_bound_i32(cols + wb, off[wv + 1] - wb, xhi);
             base = wb + p0;
             len = p1 > p0 ? (int)(p1 - p0) : 0;
         }
-        warp_segments(cols, base, len, [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); });
+        if (len >= kSplit) {  // hand very long segments to the whole block
+            const int slot = atomicAdd(&sh.nsplit, 1);
+            if (slot < kSplitQ) {
+                sh.split_base[slot] = base;
+                sh.split_len[slot] = len;
+                len = 0;
+            }
+        }
+        warp_segments(cols, base, len, add);
     }
 }
 
-__global__ void __launch_bounds__(kWinThreads, 1) k_c4_window(const int64_t* __restrict__ off,
-                                                           const int32_t* __restrict__ cols,
-                                                           const int64_t* __restrict__ offp,
-                                                           const int32_t* __restrict__ colsp,
-                                                           const int32_t* __restrict__ deg,
-                                                           const int32_t* __restrict__ dplus,
-                                                           const int32_t* __restrict__ fpos, int64_t n,
-                                                           const int32_t* __restrict__ q_win,
-                                                           const int64_t* __restrict__ win_prefix,
-                                                           uint64_t* __restrict__ acc, Sink sink) {
+template <int WIDTH>
+__device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int32_t xlo, uint32_t* cw, WinShared& sh,
+                                           uint64_t& c4) {
+    const int l = lane_id();
+    const int ns = sh.nsplit < kSplitQ ? sh.nsplit : kSplitQ;
+    const int total = sh.split_pre[ns];
+    for (;;) {
+        int t = 0;
+        if (l == 0) t = atomicAdd(&sh.chunk, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= total) break;
+        int e = 0;  // entry owning chunk t: last e with split_pre[e] <= t
+        int hi = ns;
+        while (hi - e > 1) {
+            const int mid = (e + hi) >> 1;
+            if (sh.split_pre[mid] <= t) e = mid;
+            else hi = mid;
+        }
+        const int64_t b = sh.split_base[e] + (int64_t)(t - sh.split_pre[e]) * kChunk;
+        const int64_t end = sh.split_base[e] + sh.split_len[e];
+        const int64_t stop = b + kChunk < end ? b + kChunk : end;
+        for (int64_t p = b + l; p < stop; p += 32) c4 += counter_add<WIDTH>(cw, (uint32_t)(__ldg(cols + p) - xlo));
+    }
+}
+
+__global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __restrict__ off,
+                                                              const int32_t* __restrict__ cols,
+                                                              const int32_t* __restrict__ deg,
+                                                              const int32_t* __restrict__ dplus,
+                                                              const int32_t* __restrict__ fpos,
+                                                              const int32_t* __restrict__ rev,
+                                                              const int32_t* __restrict__ bpos,
+                                                              const int32_t* __restrict__ gid,
+                                                              const int64_t* __restrict__ ginfo,
+                                                              const int32_t* __restrict__ q_win,
+                                                              const int64_t* __restrict__ win_prefix,
+                                                              uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t* cw = reinterpret_cast<uint32_t*>(smem_raw);
     __shared__ int64_t s_item;
-    __shared__ int s_group;
+    __shared__ WinShared sh;
     __shared__ uint64_t red[32];
-    __shared__ Bands sB;
-    if (threadIdx.x == 0) sB = load_bands(deg, n);
-    __syncthreads();
-    const Bands B = sB;
     const int64_t nroots = (int64_t)acc[Q_C4_WIN];
     const int64_t total = win_prefix[nroots];
     unsigned long long* ticket = (unsigned long long*)&acc[T_C4_WIN];
@@ -390,66 +448,79 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_c4_window(const int64_t* __r
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = (int64_t)atomicAdd(ticket, 1ull);
-            s_group = 0;
+            sh.group = 0;
+            sh.nsplit = 0;
+            sh.chunk = 0;
         }
         __syncthreads();
         const int64_t t = s_item;
         if (t >= total) break;
-        // root index: last k with win_prefix[k] <= t
-        int64_t lo = 0, hi = nroots;
+        int64_t lo = 0, hi = nroots;  // root index: last k with win_prefix[k] <= t
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (win_prefix[mid] <= t) lo = mid;
             else hi = mid;
         }
         const int32_t u = q_win[lo];
-        const int64_t dm = (int64_t)deg[u] - dplus[u];
-        // window j of the root, located in its bands
-        int64_t j = t - win_prefix[lo];
-        int width = 32;
+        const int64_t j = t - win_prefix[lo];
+        const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
         int64_t xlo = 0, xhi = 0;
-        for (int band = 0; band < 3; ++band) {
-            int64_t blo, bhi;
-            band_range(B, band, u, blo, bhi);
-            if (bhi <= blo) continue;
-            const int wd = width_for(band, dm);
-            const int64_t span = span_for(wd);
-            const int64_t nb = (bhi - blo + span - 1) / span;
-            if (j < nb) {
-                width = wd;
-                xlo = blo + j * span;
-                xhi = xlo + span < bhi ? xlo + span : bhi;
-                break;
-            }
-            j -= nb;
-        }
+        int width = 32;
+        grid_window(gi, j, xlo, xhi, width);
+        const bool last = xhi >= (int64_t)u;
+        if (last) xhi = u;
+        const bool first = j == 0;
+        const bool table = gi[GI_NWIN] + 1 <= kGridCap;
+        const int64_t dm = (int64_t)deg[u] - dplus[u];
+        const int64_t ub = off[u];
         const int per = 32 / width;
         const int words = (int)((xhi - xlo + per - 1) / per);
         for (int i = threadIdx.x; i < words; i += kWinThreads) cw[i] = 0;
         __syncthreads();
-        const int64_t ub = off[u];
-        const bool first = xlo == B.n1;
-        const bool last = xhi == (int64_t)u;
         uint64_t a_c4 = 0;
         if (width == 8)
-            window_pass<8>(off, cols, offp, colsp, deg, dplus, fpos, u, ub, dm, (int32_t)xlo, (int32_t)xhi, first,
-                           last, cw, &s_group, a_c4);
+            window_pass<8>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+                           sh, a_c4);
         else if (width == 16)
-            window_pass<16>(off, cols, offp, colsp, deg, dplus, fpos, u, ub, dm, (int32_t)xlo, (int32_t)xhi, first,
-                            last, cw, &s_group, a_c4);
+            window_pass<16>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+                            sh, a_c4);
         else
-            window_pass<32>(off, cols, offp, colsp, deg, dplus, fpos, u, ub, dm, (int32_t)xlo, (int32_t)xhi, first,
-                            last, cw, &s_group, a_c4);
+            window_pass<32>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+                            sh, a_c4);
         __syncthreads();
+        if (sh.nsplit > 0) {
+            if (threadIdx.x == 0) {
+                const int ns = sh.nsplit < kSplitQ ? sh.nsplit : kSplitQ;
+                int run = 0;
+                for (int e = 0; e < ns; ++e) {
+                    sh.split_pre[e] = run;
+                    run += (sh.split_len[e] + kChunk - 1) / kChunk;
+                }
+                sh.split_pre[ns] = run;
+            }
+            __syncthreads();
+            if (width == 8) split_pass<8>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else if (width == 16) split_pass<16>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else split_pass<32>(cols, (int32_t)xlo, cw, sh, a_c4);
+            __syncthreads();
+        }
         if (sink.batch()) {
-            const uint64_t t = block_sum_u64(a_c4, red);
-            if (threadIdx.x == 0) sink_add(sink, u, G_C4, t);
+            const uint64_t s = block_sum_u64(a_c4, red);
+            if (threadIdx.x == 0) sink_add(sink, u, G_C4, s);
         } else {
             c4 += a_c4;
         }
+        __syncthreads();  // every thread is done with this item's shared state before thread 0 resets it
     }
     c4 = block_sum_u64(c4, red);
     if (threadIdx.x == 0 && c4) atomicAdd((unsigned long long*)&acc[ACC_C4], (unsigned long long)c4);
+}
+
+unsigned grid_cap(int64_t work, int threads, int64_t cap) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
 }
 
 }  // namespace
@@ -459,31 +530,34 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     if (n == 0 || g->m == 0) return HARP_OK;
     uint32_t warp_max = plan.c4_warp_max_work ? plan.c4_warp_max_work : 512;
     if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
-    uint32_t cta_max = plan.c4_cta_max_work ? plan.c4_cta_max_work : kMidSlots / 2;
-    if (cta_max > kMidSlots / 2) cta_max = kMidSlots / 2;
-    if (cta_max < warp_max) cta_max = warp_max;
-
-    int32_t* wcount = ws.q_win + n;
+    const int64_t G = ws.G > 0 ? ws.G : 1;
     const Sink sink{ws.acc, ws.gid, ws.accG};
+    int32_t* wcount = ws.q_win + n;
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
+    k_c4_ginfo<<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.ginfo);
+    HARP_LAUNCHED();
+    k_c4_rev<<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n,
+                                                              ws.rev);
+    HARP_LAUNCHED();
+    k_c4_bpos<<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n, ws.fpos,
+                                                                      ws.bpos);
+    HARP_LAUNCHED();
+    k_c4_classify<<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev,
+                                                                   ws.gid, ws.ginfo, n, warp_max, ws.q_mid, ws.q_win,
+                                                                   wcount, ws.acc);
+    HARP_LAUNCHED();
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
-    k_c4_small<<<152 * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus,
-                                                          ws.fpos, n, warp_max, cta_max, ws.q_mid, ws.q_win, wcount,
-                                                          ws.acc, sink);
+    k_c4_small<<<152 * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.q_mid,
+                                                          n, ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_SMALL));
-    const size_t mid_smem = (size_t)kMidSlots * (sizeof(int32_t) + sizeof(uint32_t));
-    HARP_CK(cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_smem));
-    k_c4_mid<<<152, kMidThreads, mid_smem, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, ws.fpos,
-                                                ws.q_mid, n, ws.acc, sink);
-    HARP_LAUNCHED();
-    HARP_CK(prof_mark(s, SEG_C4_MID));
+    HARP_CK(prof_mark(s, SEG_C4_MID));  // the CTA-hash mode is folded into the windowed mode
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
     const size_t win_smem = (size_t)kWinWords * sizeof(uint32_t);
     HARP_CK(cudaFuncSetAttribute(k_c4_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
-    k_c4_window<<<152, kWinThreads, win_smem, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, ws.fpos,
-                                                   n, ws.q_win, ws.win_prefix, ws.acc, sink);
+    k_c4_window<<<152 * 2, kWinThreads, win_smem, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.bpos,
+                                                       ws.gid, ws.ginfo, ws.q_win, ws.win_prefix, ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_WINDOW));
     return HARP_OK;

@@ -73,11 +73,14 @@ enum : int {
     T_C4_MID = 33,
     T_C4_WIN = 34,
     W_TOTAL = 35,          // total window items of the windowed wedge kernel
+    Q_SORT_CTA = 36,       // rows for the CTA row sort (36) and the hub row sort (37)
     kOutLen = 40
 };
 
 // Per-graph accumulator slots (batch mode), kGStride per graph.
 constexpr int kGStride = 8;
+constexpr int kGInfo = 8;      // int64 per graph of wedge-window geometry
+constexpr int kGridCap = 16;   // grid boundaries kept per row
 enum : int { G_T = 0, G_K4, G_C4, G_S, G_PW, G_PAWSUM, G_D };
 
 // ---------------------------------------------------------------------------------------------
@@ -98,6 +101,9 @@ struct Workspace {
     int32_t* cols = nullptr;       // [2m]  rank-order CSR columns, rows ascending
     int32_t* dplus = nullptr;      // [n]   out-degree (neighbours with larger rank)
     int32_t* fpos = nullptr;       // [n]   first row position holding a neighbour of degree >= 2
+    int32_t* rev = nullptr;        // [2m]  pos_w(u) for every lower arc (u -> w), at u's row position
+    int32_t* bpos = nullptr;       // [n * kGridCap] row positions of the wedge-window grid boundaries
+    int64_t* ginfo = nullptr;      // [G * kGInfo] per-graph bands of the wedge-window grid
     int64_t* offp = nullptr;       // [n+1] out-CSR offsets
     int32_t* colsp = nullptr;      // [m]   out-CSR columns
     uint32_t* te = nullptr;        // [m]   per out-arc triangle count t_e (colsp and te are contiguous)
@@ -109,6 +115,8 @@ struct Workspace {
     size_t scan_tmp_len = 0;
     uint64_t* acc = nullptr;       // [kOutLen]
     // batch mode only (the union of many graphs); nullptr for a single graph
+    int64_t G = 1;                    // graphs
+    const int64_t* gbase = nullptr;   // [G+1] first vertex of each graph (ranks and input ids alike)
     const int32_t* gid_in = nullptr;  // [n] graph of each input (union) vertex
     int32_t* gid = nullptr;           // [n] graph of each rank-order vertex
     uint64_t* accG = nullptr;         // [G * kGStride] per-graph accumulators

@@ -21,7 +21,7 @@ namespace {
 // at most sqrt(2m)), so no execution mode that would need extra scratch is reached.
 constexpr int64_t kNoAllocMaxN = 262144;
 constexpr int64_t kNoAllocMaxM = 524288;
-constexpr size_t kNoAllocBytes = (size_t)32 << 20;  // 32 MiB
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

@@ -9,9 +9,9 @@
 // Output (workspace): deg, order (new -> old), perm (old -> new), off/cols (relabelled CSR with
 // every row sorted), dplus, offp/colsp (out-CSR: only N+), te zeroed, S = sum_v C(d_v, 3).
 //
-// Rows are sorted by three kernels chosen by degree (rank order makes the tiers contiguous id
-// ranges): a warp bitonic network for d <= 32, a shared-memory bitonic sort for d <= 4096, and a
-// per-row LSD radix sort through global memory for hubs.
+// Rows are sorted by three kernels chosen by degree: a warp bitonic network for d <= 32 (every row
+// is visited), a shared-memory bitonic sort for d <= 4096 and a per-row LSD radix sort through global
+// memory for hubs (both from queues filled by the relabel pass).
 #include "harp_internal.cuh"
 
 namespace harp {
@@ -33,14 +33,15 @@ unsigned grid_for(int64_t work, int threads, int64_t cap = 152 * 64) {
     return (unsigned)b;
 }
 
-__global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b,
+__global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b, int bd,
                               uint64_t* __restrict__ keys, uint64_t* __restrict__ acc,
                               const int32_t* __restrict__ gid_in, uint64_t* __restrict__ accG) {
     uint64_t s3 = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         uint64_t d = (uint64_t)(off[v + 1] - off[v]);
-        keys[v] = (d << b) | (uint64_t)v;
+        const uint64_t g = gid_in ? (uint64_t)gid_in[v] : 0;
+        keys[v] = (g << (bd + b)) | (d << b) | (uint64_t)v;
         const uint64_t c3 = choose3_u64(d);
         if (gid_in) {
             if (c3) atomicAdd((unsigned long long*)&accG[(int64_t)gid_in[v] * kGStride + G_S], (unsigned long long)c3);
@@ -53,30 +54,44 @@ __global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b,
     if (threadIdx.x == 0 && t) atomicAdd((unsigned long long*)&acc[ACC_S], (unsigned long long)t);
 }
 
-__global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t n, int b, int32_t* __restrict__ order,
+// New ids = sorted key order.  Rows that need the CTA or hub sort are queued (q: CTA rows from the
+// front, hub rows from the back); the warp sort takes every other row directly.
+__global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t n, int b, int bd, int32_t* __restrict__ order,
                           int32_t* __restrict__ perm, int32_t* __restrict__ deg,
-                          const int32_t* __restrict__ gid_in, int32_t* __restrict__ gid) {
+                          const int32_t* __restrict__ gid_in, int32_t* __restrict__ gid,
+                          int32_t* __restrict__ q, unsigned long long* __restrict__ qcnt) {
     const uint64_t mask = ((uint64_t)1 << b) - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        int32_t old = (int32_t)(k & mask);
-        order[i] = old;
-        perm[old] = (int32_t)i;
-        deg[i] = (int32_t)(k >> b);
-        if (gid_in) gid[i] = gid_in[old];
+    const uint64_t dmask = ((uint64_t)1 << bd) - 1;
+    const int l = lane_id();
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - l; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + l;
+        int cls = -1;
+        if (i < n) {
+            const uint64_t k = keys[i];
+            const int32_t old = (int32_t)(k & mask);
+            const int32_t d = (int32_t)((k >> b) & dmask);
+            order[i] = old;
+            perm[old] = (int32_t)i;
+            deg[i] = d;
+            if (gid_in) gid[i] = gid_in[old];
+            cls = d > kTierB ? 1 : (d > kTierA ? 0 : -1);
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t m = __ballot_sync(kFull, cls == c);
+            if (!m) continue;
+            unsigned long long start = 0;
+            const int leader = __ffs(m) - 1;
+            if (l == leader) start = atomicAdd(&qcnt[c], (unsigned long long)__popc(m));
+            start = __shfl_sync(kFull, start, leader);
+            if (cls == c) {
+                const unsigned long long k = start + __popc(m & lanemask_lt());
+                if (c == 0) q[k] = (int32_t)i;
+                else q[n - 1 - (int64_t)k] = (int32_t)i;
+            }
+        }
     }
-}
-
-// first index in [0, n) with deg[i] > t (deg is non-decreasing in rank order)
-__device__ __forceinline__ int64_t first_above(const int32_t* __restrict__ deg, int64_t n, int32_t t) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (deg[mid] <= t) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
 }
 
 // Tier A: rows with 1 <= d <= 32, one warp per row, bitonic network in registers.
@@ -87,22 +102,17 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restric
                                                         const int32_t* __restrict__ deg,
                                                         const int64_t* __restrict__ off, int64_t n,
                                                         int32_t* __restrict__ cols,
-                                                        int32_t* __restrict__ dplus,
-                                                        int32_t* __restrict__ fpos) {
-    __shared__ int64_t range[3];
-    if (threadIdx.x == 0) {
-        range[0] = first_above(deg, n, 0);
-        range[1] = first_above(deg, n, kTierA);
-        range[2] = first_above(deg, n, 1);  // n1: first rank of degree >= 2
-    }
-    __syncthreads();
-    const int64_t lo = range[0], hi = range[1];
-    const int32_t n1 = (int32_t)range[2];
+                                                        int32_t* __restrict__ dplus) {
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = lo + wid; i < hi; i += nw) {
+    for (int64_t i = wid; i < n; i += nw) {
         const int d = deg[i];
+        if (d > kTierA) continue;  // CTA and hub rows are sorted by the queued kernels
+        if (d == 0) {
+            if (l == 0) dplus[i] = 0;
+            continue;
+        }
         const int64_t src = goff[order[i]];
         int32_t v = (l < d) ? perm[gcols[src + l]] : 0x7fffffff;
 #pragma unroll
@@ -117,17 +127,7 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restric
         }
         if (l < d) cols[off[i] + l] = v;
         uint32_t above = __ballot_sync(kFull, l < d && v > (int32_t)i);
-        uint32_t leaves = __ballot_sync(kFull, l < d && v < n1);
-        if (l == 0) {
-            dplus[i] = __popc(above);
-            fpos[i] = __popc(leaves);
-        }
-    }
-    // rows with d == 0 (a prefix of the rank order)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lo;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        dplus[i] = 0;
-        fpos[i] = 0;
+        if (l == 0) dplus[i] = __popc(above);
     }
 }
 
@@ -140,28 +140,19 @@ __global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restri
                                                          const int64_t* __restrict__ off, int64_t n,
                                                          int32_t* __restrict__ cols,
                                                          int32_t* __restrict__ dplus,
-                                                         int32_t* __restrict__ fpos) {
+                                                         const int32_t* __restrict__ q,
+                                                         const unsigned long long* __restrict__ qcnt) {
     __shared__ int32_t buf[kTierB];
-    __shared__ int64_t range[3];
-    __shared__ int cnt_below, cnt_leaf;
-    if (threadIdx.x == 0) {
-        range[0] = first_above(deg, n, kTierA);
-        range[1] = first_above(deg, n, kTierB);
-        range[2] = first_above(deg, n, 1);
-    }
-    __syncthreads();
-    const int64_t lo = range[0], hi = range[1];
-    const int32_t n1 = (int32_t)range[2];
-    for (int64_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
+    __shared__ int cnt_below;
+    const int64_t nq = (int64_t)qcnt[0];
+    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int64_t i = q[qi];
         const int d = deg[i];
         int P = 64;
         while (P < d) P <<= 1;
         const int64_t src = goff[order[i]];
         for (int k = threadIdx.x; k < P; k += blockDim.x) buf[k] = (k < d) ? perm[gcols[src + k]] : 0x7fffffff;
-        if (threadIdx.x == 0) {
-            cnt_below = 0;
-            cnt_leaf = 0;
-        }
+        if (threadIdx.x == 0) cnt_below = 0;
         __syncthreads();
         for (int k = 2; k <= P; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -178,22 +169,16 @@ __global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restri
                 __syncthreads();
             }
         }
-        int below = 0, leaf = 0;
+        int below = 0;
         for (int k = threadIdx.x; k < d; k += blockDim.x) {
             int32_t x = buf[k];
             cols[off[i] + k] = x;
             below += x < (int32_t)i;
-            leaf += x < n1;
         }
         below = warp_sum(below);
-        leaf = warp_sum(leaf);
         if (lane_id() == 0 && below) atomicAdd(&cnt_below, below);
-        if (lane_id() == 0 && leaf) atomicAdd(&cnt_leaf, leaf);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            dplus[i] = d - cnt_below;
-            fpos[i] = cnt_leaf;
-        }
+        if (threadIdx.x == 0) dplus[i] = d - cnt_below;
         __syncthreads();
     }
 }
@@ -213,23 +198,17 @@ __global__ void __launch_bounds__(kHubThreads) k_sort_rows_hub(const int64_t* __
                                                                int nbits, int32_t* __restrict__ cols,
                                                                int32_t* __restrict__ tmp,
                                                                int32_t* __restrict__ dplus,
-                                                               int32_t* __restrict__ fpos) {
+                                                               const int32_t* __restrict__ q,
+                                                               const unsigned long long* __restrict__ qcnt) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[kHubWarps][256];
-    __shared__ int64_t range[3];
-    __shared__ int cnt_below, cnt_leaf;
-    if (threadIdx.x == 0) {
-        range[0] = first_above(deg, n, kTierB);
-        range[1] = n;
-        range[2] = first_above(deg, n, 1);
-    }
-    __syncthreads();
-    const int64_t lo = range[0], hi = range[1];
-    const int32_t n1 = (int32_t)range[2];
+    __shared__ int cnt_below;
     const int npass = (nbits + 7) / 8;
     const int w = threadIdx.x >> 5, l = lane_id();
     const uint32_t lt = lanemask_lt();
-    for (int64_t i = lo + blockIdx.x; i < hi; i += gridDim.x) {
+    const int64_t nq = (int64_t)qcnt[1];
+    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int64_t i = q[n - 1 - qi];
         const int64_t d = deg[i];
         const int64_t src = goff[order[i]];
         const int64_t dst0 = off[i];
@@ -289,27 +268,15 @@ __global__ void __launch_bounds__(kHubThreads) k_sort_rows_hub(const int64_t* __
             }
             __syncthreads();
         }
-        // out-degree: elements above i in the sorted row; fpos: elements of degree <= 1
-        if (threadIdx.x == 0) {
-            cnt_below = 0;
-            cnt_leaf = 0;
-        }
+        // out-degree: elements above i in the sorted row
+        if (threadIdx.x == 0) cnt_below = 0;
         __syncthreads();
-        int below = 0, leaf = 0;
-        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
-            const int32_t x = cols[dst0 + k];
-            below += x < (int32_t)i;
-            leaf += x < n1;
-        }
+        int below = 0;
+        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) below += cols[dst0 + k] < (int32_t)i;
         below = warp_sum(below);
-        leaf = warp_sum(leaf);
         if (l == 0 && below) atomicAdd(&cnt_below, below);
-        if (l == 0 && leaf) atomicAdd(&cnt_leaf, leaf);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            dplus[i] = (int32_t)(d - cnt_below);
-            fpos[i] = cnt_leaf;
-        }
+        if (threadIdx.x == 0) dplus[i] = (int32_t)(d - cnt_below);
         __syncthreads();
     }
 }
@@ -356,29 +323,34 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     if (n == 0) return HARP_OK;
     const int b = bits_for(n);
     const int bd = bits_for(g->max_deg);
+    const int bg = ws.gid_in && ws.G > 1 ? bits_for(ws.G - 1) : 0;
+    if (b + bd + bg > 64) return HARP_EOVERFLOW;
 
-    k_vertex_keys<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, b, ws.vkeys, ws.acc, ws.gid_in, ws.accG);
+    // rank = (graph, degree, id): each graph's vertices form one contiguous rank range, sorted by
+    // degree (a single graph is graph 0)
+    k_vertex_keys<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, b, bd, ws.vkeys, ws.acc, ws.gid_in, ws.accG);
     HARP_LAUNCHED();
     uint64_t* k0 = ws.vkeys;
     uint64_t* k1 = ws.vkeys_alt;
-    HARP_TRY(radix_sort_u64(&k0, &k1, n, 0, b + bd, ws.hist, ws.scan_tmp, ws.scan_tmp_len, s));
-    k_relabel<<<grid_for(n, 256), 256, 0, s>>>(k0, n, b, ws.order, ws.perm, ws.deg, ws.gid_in, ws.gid);
+    HARP_TRY(radix_sort_u64(&k0, &k1, n, 0, b + bd + bg, ws.hist, ws.scan_tmp, ws.scan_tmp_len, s));
+    unsigned long long* qsort = (unsigned long long*)&ws.acc[Q_SORT_CTA];
+    k_relabel<<<grid_for(n, 256), 256, 0, s>>>(k0, n, b, bd, ws.order, ws.perm, ws.deg, ws.gid_in, ws.gid, ws.q_tri,
+                                               qsort);
     HARP_LAUNCHED();
     HARP_TRY(exclusive_scan_i32_to_i64(ws.deg, ws.off, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {
         k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
-                                                                ws.off, n, ws.cols, ws.dplus, ws.fpos);
+                                                                ws.off, n, ws.cols, ws.dplus);
         HARP_LAUNCHED();
         k_sort_rows_block<<<152 * 4, 512, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n,
-                                                   ws.cols, ws.dplus, ws.fpos);
+                                                   ws.cols, ws.dplus, ws.q_tri, qsort);
         HARP_LAUNCHED();
         // the out-CSR columns + t_e region (2m int32) is free until k_out_csr: hub sort ping-pong
         k_sort_rows_hub<<<152, kHubThreads, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n, b,
-                                                     ws.cols, ws.colsp, ws.dplus, ws.fpos);
+                                                     ws.cols, ws.colsp, ws.dplus, ws.q_tri, qsort);
         HARP_LAUNCHED();
     } else {
         HARP_CK(cudaMemsetAsync(ws.dplus, 0, (size_t)n * sizeof(int32_t), s));
-        HARP_CK(cudaMemsetAsync(ws.fpos, 0, (size_t)n * sizeof(int32_t), s));
     }
     HARP_TRY(exclusive_scan_i32_to_i64(ws.dplus, ws.offp, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {

@@ -256,7 +256,7 @@ def harp_count4_noalloc(n: int, m: int, d_offsets: int, d_cols: int, d_out: int,
 
     For callers that may not allocate device memory while they run.  d_offsets / d_cols / d_out
     are device pointers (int64[n+1], int32[2m], uint64[16]); the work is only enqueued on `stream`.
-    Scratch is a static 32 MiB device array shared by all calls: serialise calls that could overlap.
+    Scratch is a static 64 MiB device array shared by all calls: serialise calls that could overlap.
     """
     _check(lib().harp_count4_noalloc(int(n), int(m), ctypes.c_void_p(d_offsets), ctypes.c_void_p(d_cols),
                                      ctypes.c_void_p(d_out), _stream_handle(stream)), "harp_count4_noalloc")
