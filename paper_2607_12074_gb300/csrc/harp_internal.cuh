@@ -74,6 +74,7 @@ enum : int {
     T_C4_WIN = 34,
     W_TOTAL = 35,          // total window items of the windowed wedge kernel
     Q_SORT_CTA = 36,       // rows for the CTA row sort (36) and the hub row sort (37)
+    T_TRI_M = 38,          // ticket of the 512-wide CTA triangle kernel
     kOutLen = 40
 };
 

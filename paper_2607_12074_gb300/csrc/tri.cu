@@ -14,24 +14,29 @@
 //                  per set bit (global atomic at the position where the intersection found it)
 //   * 4-cliques:   K4_u = sum over set bits (i, j) of popc(row_i & row_j)   (the X_3 extension)
 //   * paw sums:    sum over triangles of (d_a + d_b + d_c)
+// The intersection walks N+(L[i]) from L[i+1] (found by a warp-parallel 32-ary search when the list
+// is long) up to the largest element of L, and looks each element up in a shared-memory hash of L
+// that returns its index j.
 // Warp-local mode: d <= 32, rows are single words, one warp per anchor.
-// CTA mode: 32 < d <= kCtaMax, rows live in shared memory, one block per anchor.
-// Fallback (d > kCtaMax, hubs of very large graphs): per out-arc ordered intersections through
-// global memory with binary-searched membership; 4-cliques by binary search in N+(w).
+// CTA mode: 32 < d <= 1024 in three sizes (256 / 512 / 1024), rows in shared memory, one block per
+// anchor.  Fallback (d > 1024, hubs of very large graphs): per out-arc ordered intersections
+// through global memory with binary-searched membership; 4-cliques by binary search in N+(w).
 #include "harp_internal.cuh"
 
 namespace harp {
 namespace {
 
-constexpr int kCtaSmallMax = 256;
+constexpr int kCta1 = 256;
+constexpr int kCta2 = 512;
 constexpr int kCtaMax = 1024;
 constexpr int kInf = 0x7fffffff;
+constexpr int32_t kNoKey = -1;
 
 // Anchor queues in ws.q_tri (n entries): warp-mode anchors (2 <= d <= 32) from the front,
 // CTA-mode and fallback anchors (d > 32) from the back.  Vertices are scanned in descending rank,
 // so high-degree anchors tend to be queued (and taken) first.
 __device__ __forceinline__ int tri_class(int d) {
-    return d < 2 ? -1 : (d <= 32 ? 0 : (d <= kCtaSmallMax ? 1 : (d <= kCtaMax ? 2 : 3)));
+    return d < 2 ? -1 : (d <= 32 ? 0 : (d <= kCta1 ? 1 : (d <= kCta2 ? 2 : (d <= kCtaMax ? 3 : 4))));
 }
 
 __global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int32_t* __restrict__ q,
@@ -60,12 +65,50 @@ __global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int
     }
 }
 
-// smem lower_bound over a padded sorted array a[0..P) (P a power of two)
-__device__ __forceinline__ int lb_smem(const int32_t* a, int P, int32_t y) {
-    int j = 0;
-    for (int s = P >> 1; s >= 1; s >>= 1)
-        if (a[j + s - 1] < y) j += s;
-    return j;
+// Shared-memory hash of the anchor list: key = vertex, value = its index in L.  2^bits slots.
+template <typename V>
+__device__ __forceinline__ void hash_put(int32_t* hk, V* hv, int bits, int32_t key, int idx) {
+    const uint32_t mask = (1u << bits) - 1;
+    uint32_t h = hash32((uint32_t)key) >> (32 - bits);
+    for (;;) {
+        if (atomicCAS(&hk[h], kNoKey, key) == kNoKey) {
+            hv[h] = (V)idx;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ int hash_get(const int32_t* hk, const V* hv, int bits, int32_t key) {
+    const uint32_t mask = (1u << bits) - 1;
+    uint32_t h = hash32((uint32_t)key) >> (32 - bits);
+    for (;;) {
+        const int32_t k = hk[h];
+        if (k == key) return (int)hv[h];
+        if (k == kNoKey) return -1;
+        h = (h + 1) & mask;
+    }
+}
+
+// First position p in [lo, hi) with a[p] >= t, found by the whole warp (32-ary search).
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t t) {
+    const int l = lane_id();
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = lo + (int64_t)(l + 1) * step - 1;
+        const bool pred = idx >= hi || a[idx] >= t;
+        const uint32_t m = __ballot_sync(kFull, pred);
+        if (!m) return hi;  // every probed element (the last one included) is below t
+        const int k = __ffs(m) - 1;
+        const int64_t nlo = lo + (int64_t)k * step;
+        const int64_t nhi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const bool pred = lo + l < hi && a[lo + l] >= t;
+    const uint32_t m = __ballot_sync(kFull, pred);
+    return m ? lo + __ffs(m) - 1 : hi;
 }
 
 // single-graph mode: one block reduction and one atomic per statistic at the end of the kernel
@@ -85,6 +128,7 @@ __device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint
 // ---------------------------------------------------------------------------------------------
 constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
+constexpr int kWarpHashBits = 6;  // 64 slots for <= 32 keys
 
 __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __restrict__ offp,
                                                            const int32_t* __restrict__ colsp,
@@ -94,6 +138,8 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
                                                            uint32_t* __restrict__ te, Sink sink) {
     __shared__ int32_t sL[kWarpsPerBlock][32];
     __shared__ uint32_t sRow[kWarpsPerBlock][32];
+    __shared__ int32_t sHk[kWarpsPerBlock][1 << kWarpHashBits];
+    __shared__ uint8_t sHv[kWarpsPerBlock][1 << kWarpHashBits];
     __shared__ uint64_t red[32];
     const int w = threadIdx.x >> 5, l = lane_id();
     const int64_t nq = (int64_t)cnt[0];
@@ -105,25 +151,29 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
         const int32_t x = (l < d) ? colsp[ub + l] : kInf;
         sL[w][l] = x;
         sRow[w][l] = 0;
+        sHk[w][l] = kNoKey;
+        sHk[w][l + 32] = kNoKey;
+        __syncwarp();
+        if (l < d) hash_put(sHk[w], sHv[w], kWarpHashBits, x, l);
         __syncwarp();
         const int32_t last = sL[w][d - 1];
         uint32_t col = 0;  // # rows with bit l
         for (int i = 0; i < d - 1; ++i) {
             const int32_t v = sL[w][i];
-            const int64_t b = offp[v], e = offp[v + 1];
+            const int32_t next = sL[w][i + 1];  // no element of N+(v) below L[i+1] can be in L
+            const int64_t e = offp[v + 1];
+            int64_t b = offp[v];
+            if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
             uint32_t row = 0;
             for (int64_t p0 = b; p0 < e; p0 += 32) {
                 const int64_t p = p0 + l;
                 const int32_t y = (p < e) ? colsp[p] : kInf;
-                bool hit = false;
-                int j = 0;
-                if (y <= last) {
-                    j = lb_smem(sL[w], 32, y);
-                    hit = sL[w][j] == y;
-                }
-                if (hit) {
-                    atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
-                    row |= 1u << j;
+                if (y >= next && y <= last) {
+                    const int j = hash_get(sHk[w], sHv[w], kWarpHashBits, y);
+                    if (j >= 0) {
+                        atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
+                        row |= 1u << j;
+                    }
                 }
                 // rows are sorted: stop once the chunk passed the largest candidate
                 if (__shfl_sync(kFull, y, 31) >= last) break;
@@ -166,26 +216,28 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
 // ---------------------------------------------------------------------------------------------
 // CTA mode: rows of the anchor's out-neighbourhood bitmap in shared memory.
 // ---------------------------------------------------------------------------------------------
-template <int DMAX, int THREADS>
+template <int DMAX>
 struct CtaSmem {
-    static constexpr int P = DMAX;                  // padded list length (power of two)
     static constexpr int W = DMAX / 32;             // words per row
     static constexpr int WS = W | 1;                // odd row stride: no bank conflicts
-    int32_t L[P];
+    static constexpr int HB = (DMAX <= 256) ? 9 : ((DMAX <= 512) ? 10 : 11);  // 2 * DMAX hash slots
+    int32_t L[DMAX];
     uint32_t own[DMAX];
     uint32_t R[DMAX * WS];
+    int32_t hk[1 << HB];
+    uint16_t hv[1 << HB];
     uint64_t red[32];
 };
 
 template <int DMAX, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__ offp,
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64_t* __restrict__ offp,
                                                      const int32_t* __restrict__ colsp,
                                                      const int32_t* __restrict__ deg,
                                                      const int32_t* __restrict__ q, int64_t n, int cls,
                                                      const unsigned long long* __restrict__ cnt,
                                                      unsigned long long* __restrict__ ticket,
                                                      uint32_t* __restrict__ te, Sink sink) {
-    using S = CtaSmem<DMAX, THREADS>;
+    using S = CtaSmem<DMAX>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S& s = *reinterpret_cast<S*>(smem_raw);
     __shared__ int64_t s_item;
@@ -205,24 +257,30 @@ __global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__
         if (tri_class(d) != cls) continue;
         const int W = (d + 31) >> 5;
         const int WS = W | 1;
-        int P = 32;
-        while (P < d) P <<= 1;
-        for (int i = threadIdx.x; i < P; i += THREADS) s.L[i] = (i < d) ? colsp[ub + i] : kInf;
-        for (int i = threadIdx.x; i < d; i += THREADS) s.own[i] = 0;
+        for (int i = threadIdx.x; i < d; i += THREADS) {
+            s.L[i] = colsp[ub + i];
+            s.own[i] = 0;
+        }
         for (int i = threadIdx.x; i < d * WS; i += THREADS) s.R[i] = 0;
+        for (int i = threadIdx.x; i < (1 << S::HB); i += THREADS) s.hk[i] = kNoKey;
+        __syncthreads();
+        for (int i = threadIdx.x; i < d; i += THREADS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
         __syncthreads();
         const int32_t last = s.L[d - 1];
         // rows: warp per row, ordered intersection of N+(L[i]) with L
         for (int i = w; i < d - 1; i += NW) {
             const int32_t v = s.L[i];
-            const int64_t b = offp[v], e = offp[v + 1];
+            const int32_t next = s.L[i + 1];
+            const int64_t e = offp[v + 1];
+            int64_t b = offp[v];
+            if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
             uint32_t hits = 0;
             for (int64_t p0 = b; p0 < e; p0 += 32) {
                 const int64_t p = p0 + l;
                 const int32_t y = (p < e) ? colsp[p] : kInf;
-                if (y <= last) {
-                    const int j = lb_smem(s.L, P, y);
-                    if (s.L[j] == y) {
+                if (y >= next && y <= last) {
+                    const int j = hash_get(s.hk, s.hv, S::HB, y);
+                    if (j >= 0) {
                         atomicAdd(&te[p], 1u);
                         atomicOr(&s.R[i * WS + (j >> 5)], 1u << (j & 31));
                         atomicAdd(&s.own[j], 1u);
@@ -259,11 +317,8 @@ __global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__
                 a_paw += (uint64_t)o * (uint64_t)deg[s.L[i]];
             }
         }
-        __syncthreads();
-        // T_u * d_u for the paw sum (T_u = sum of popc over rows; recomputed cheaply)
-        uint32_t tu = 0;
-        for (int i = threadIdx.x; i < d * WS; i += THREADS) tu += __popc(s.R[i]);
-        a_paw += (uint64_t)tu * (uint64_t)deg[u];
+        // the anchor's own degree term: T_u * d_u
+        a_paw += a_tri * (uint64_t)deg[u];
         __syncthreads();
         if (sink.batch()) {
             const uint64_t t1 = block_sum_u64(a_tri, s.red);
@@ -284,7 +339,7 @@ __global__ void __launch_bounds__(THREADS) k_tri_cta(const int64_t* __restrict__
 }
 
 // ---------------------------------------------------------------------------------------------
-// Fallback for out-degree > kCtaMax: per out-arc (u, v) the frontier S_uv = N+(u) n N+(v) is
+// Fallback for out-degree > kCtaMax (1024): per out-arc (u, v) the frontier S_uv = N+(u) n N+(v) is
 // materialised (compaction) in a per-warp global buffer, then reused for the 4-clique extension.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int64_t lb_global(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t y) {
@@ -312,7 +367,7 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
     for (int64_t k = blockIdx.x; k < nq; k += gridDim.x) {
         const int32_t u = q[n - 1 - k];
         const int64_t ub = offp[u], ue = offp[u + 1];
-        if (tri_class((int)(ue - ub)) != 3) continue;
+        if (tri_class((int)(ue - ub)) != 4) continue;
         const uint64_t du = (uint64_t)deg[u];
         const uint64_t tri0 = tri, k40 = k4, paw0 = paw;
         for (int64_t a = ub + w; a < ue; a += nw) {  // warp per out-arc (u, v)
@@ -376,7 +431,7 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
 template <int DMAX, int THREADS>
 harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slot, int blocks_per_sm,
                        cudaStream_t s) {
-    const size_t smem = sizeof(CtaSmem<DMAX, THREADS>);
+    const size_t smem = sizeof(CtaSmem<DMAX>);
     HARP_CK(cudaFuncSetAttribute(k_tri_cta<DMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     k_tri_cta<DMAX, THREADS><<<152 * blocks_per_sm, THREADS, smem, s>>>(
@@ -403,9 +458,10 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     k_tri_warp<<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, cnt, ws.te, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_TRI_WARP));
-    HARP_TRY((launch_cta<kCtaSmallMax, 256>(g, ws, 1, T_TRI_S, 6, s)));
+    HARP_TRY((launch_cta<kCta1, 256>(g, ws, 1, T_TRI_S, 4, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
-    HARP_TRY((launch_cta<kCtaMax, 512>(g, ws, 2, T_TRI_L, 1, s)));
+    HARP_TRY((launch_cta<kCta2, 256>(g, ws, 2, T_TRI_M, 4, s)));
+    HARP_TRY((launch_cta<kCtaMax, 512>(g, ws, 3, T_TRI_L, 1, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
     // fallback: per-warp frontier buffers of the largest possible out-degree (bounded by sqrt(2m))
     int64_t dmax = 1;

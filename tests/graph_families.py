@@ -66,7 +66,7 @@ def closed_forms(scale=1):
     for k in (2, 3, 4, 6):
         out.append((f"CP{k}", 2 * k, cocktail(k), [0, 0, 0, C(k, 2), 4 * k * C(k - 1, 2), 16 * C(k, 4)]))
     if scale > 1:
-        for n in (40, 300, 1100):        # warp, CTA and fallback triangle modes
+        for n in (40, 300, 700, 1100):   # warp, CTA (256 / 512 / 1024) and fallback triangle modes
             out.append((f"K{n}", n, complete(n), [0, 0, 0, 0, 0, C(n, 4)]))
         out.append(("K1,5000", 5001, star(5000), [C(5000, 3), 0, 0, 0, 0, 0]))   # hub row sort
         n = 5000
