@@ -169,9 +169,10 @@ harp_status count_to_host(const harp_csr* gc, const harp_plan* plan, uint64_t* c
     harp_csr* g = const_cast<harp_csr*>(gc);
     HARP_CK(cudaSetDevice(g->device));
     HARP_TRY(enqueue_count(g, plan, g->stream));
-    uint64_t host[16];
+    uint64_t host[kOutLen];
     HARP_CK(cudaMemcpyAsync(host, g->ws.acc, sizeof(host), cudaMemcpyDeviceToHost, g->stream));
     HARP_CK(cudaStreamSynchronize(g->stream));
+    if (host[ACC_ERR]) return HARP_EDEVICE;  // a kernel's self-check skipped an out-of-range access
     std::memcpy(counts_out, host + OUT_COUNTS, 6 * sizeof(uint64_t));
     if (stats_out) std::memcpy(stats_out, host + OUT_STATS, HARP_NSTATS * sizeof(uint64_t));
     return HARP_OK;

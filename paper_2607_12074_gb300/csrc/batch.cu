@@ -57,7 +57,7 @@ struct harp_batch {
     int64_t* d_gbase = nullptr;       // [G + 1] first union vertex of each member
     int64_t* d_ginfo = nullptr;       // [G * kGInfo]
     uint64_t* d_out = nullptr;        // [G * 16]
-    uint64_t* h_out = nullptr;        // pinned [G * 16]
+    uint64_t* h_out = nullptr;        // pinned [G * 16 + 1]; the last word is the device self-check flag
     cudaGraphExec_t exec = nullptr;
     harp_plan plan_captured{};
     int64_t launches_per_count = 0;
@@ -99,6 +99,7 @@ harp_status enqueue_batch(harp_batch* b, const harp_plan& plan, cudaStream_t s) 
     HARP_TRY(count_wedge_c4(&b->u, ws, plan, s));
     HARP_TRY(reduce_and_close_batch(&b->u, ws, b->G, b->d_out, s));
     HARP_CK(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(uint64_t) * 16 * (size_t)b->G, cudaMemcpyDeviceToHost, s));
+    HARP_CK(cudaMemcpyAsync(b->h_out + 16 * b->G, ws.acc + ACC_ERR, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     return HARP_OK;
 }
 
@@ -161,7 +162,7 @@ harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_bat
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_ginfo, sizeof(int64_t) * kGInfo * gg, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_gbase, gbase.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_out, sizeof(uint64_t) * 16 * gg);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_out, sizeof(uint64_t) * (16 * gg + 1));
     if (e == cudaSuccess && G > 0)
         e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(MemberDesc) * (size_t)G, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
@@ -236,6 +237,7 @@ harp_status harp_batch_count(harp_batch* b, const harp_plan* user_plan, uint64_t
         HARP_TRY(enqueue_batch(b, plan, s));
         HARP_CK(cudaStreamSynchronize(s));
     }
+    if (b->h_out[16 * b->G]) return HARP_EDEVICE;  // a kernel's self-check skipped an out-of-range access
     for (int64_t g = 0; g < b->G; ++g) {
         const uint64_t* o = b->h_out + 16 * g;
         for (int k = 0; k < 6; ++k) counts_out[g][k] = o[k];

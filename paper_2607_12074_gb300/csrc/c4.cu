@@ -120,22 +120,39 @@ __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int
     }
 }
 
-// rev[a] = pos_w(u) for every lower arc (u -> w) at row position a of u (warp per root)
+// rev[a] = pos_w(u) for every lower arc (u -> w) at row position a of u.  Each thread takes a run of
+// kRevRun consecutive arcs of the CSR (one search for the run's first row, then it walks forward), so
+// hub rows are spread over many threads.
+constexpr int kRevRun = 16;
+
 __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                                 const int64_t* __restrict__ offp, const int32_t* __restrict__ colsp,
                                                 const int32_t* __restrict__ deg, const int32_t* __restrict__ dplus,
-                                                int64_t n, int32_t* __restrict__ rev) {
-    const int l = lane_id();
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = wid; u < n; u += nw) {
-        const int64_t dm = (int64_t)deg[u] - dplus[u];
-        if (dm < 2) continue;
-        const int64_t ub = off[u];
-        for (int64_t a = l; a < dm; a += 32) {
-            const int32_t w = cols[ub + a];
+                                                int64_t n, int64_t arcs, int32_t* __restrict__ rev) {
+    const int64_t runs = (arcs + kRevRun - 1) / kRevRun;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < runs; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a0 = r * kRevRun;
+        const int64_t a1 = a0 + kRevRun < arcs ? a0 + kRevRun : arcs;
+        int64_t lo = 0, hi = n;  // row of arc a0: last u with off[u] <= a0
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (off[mid] <= a0) lo = mid;
+            else hi = mid;
+        }
+        int64_t u = lo;
+        int64_t ub = off[u], ue = off[u + 1];
+        int64_t lower_end = ub + ((int64_t)deg[u] - dplus[u]);
+        for (int64_t a = a0; a < a1; ++a) {
+            while (a >= ue) {  // next non-empty row
+                ++u;
+                ub = ue;
+                ue = off[u + 1];
+                lower_end = ub + ((int64_t)deg[u] - dplus[u]);
+            }
+            if (a >= lower_end || lower_end - ub < 2) continue;  // only lower arcs of roots with d- >= 2
+            const int32_t w = cols[a];
             const int64_t pb = offp[w];
-            rev[ub + a] = (deg[w] - dplus[w]) + (int32_t)lower_bound_i32(colsp + pb, offp[w + 1] - pb, (int32_t)u);
+            rev[a] = (deg[w] - dplus[w]) + (int32_t)lower_bound_i32(colsp + pb, offp[w + 1] - pb, (int32_t)u);
         }
     }
 }
@@ -357,14 +374,25 @@ struct WinShared {
     int32_t split_pre[kSplitQ + 1];
 };
 
+// Self-check: an element outside the window (which would index past the counters) or a segment
+// outside its row is skipped and recorded in acc[ACC_ERR]; the host then reports HARP_EDEVICE.
+__device__ __forceinline__ void flag_error(uint64_t* acc, unsigned long long bit) {
+    atomicOr((unsigned long long*)&acc[ACC_ERR], bit);
+}
+
 template <int WIDTH>
 __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                             const int32_t* __restrict__ fpos, const int32_t* __restrict__ rev,
                                             const int32_t* __restrict__ bpos, bool table, int64_t j, int64_t ub,
                                             int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
-                                            WinShared& sh, uint64_t& c4) {
+                                            WinShared& sh, uint64_t& c4, uint64_t* acc) {
     const int l = lane_id();
-    auto add = [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); };
+    const uint32_t span = (uint32_t)(xhi - xlo);
+    auto add = [&](int32_t x) {
+        const uint32_t r = (uint32_t)(x - xlo);
+        if (r < span) c4 += counter_add<WIDTH>(cw, r);
+        else flag_error(acc, 1ull);
+    };
     const int ngroups = (int)((dm + 31) >> 5);
     for (;;) {
         int g = 0;
@@ -384,6 +412,11 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
             if (last) p1 = rev[ub + a];
             else if (table) p1 = bpos[(int64_t)wv * kGridCap + j + 1];
             else p1 = lower_bound_i32(cols + wb, off[wv + 1] - wb, xhi);
+            const int64_t rowlen = off[wv + 1] - wb;
+            if (p0 < 0 || p1 > rowlen) {
+                flag_error(acc, 2ull);
+                p0 = p1 = 0;
+            }
             base = wb + p0;
             len = p1 > p0 ? (int)(p1 - p0) : 0;
         }
@@ -400,8 +433,9 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
 }
 
 template <int WIDTH>
-__device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int32_t xlo, uint32_t* cw, WinShared& sh,
-                                           uint64_t& c4) {
+__device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int32_t xlo, int32_t xhi, uint32_t* cw,
+                                           WinShared& sh, uint64_t& c4, uint64_t* acc) {
+    const uint32_t span = (uint32_t)(xhi - xlo);
     const int l = lane_id();
     const int ns = sh.nsplit < kSplitQ ? sh.nsplit : kSplitQ;
     const int total = sh.split_pre[ns];
@@ -420,7 +454,11 @@ __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int
         const int64_t b = sh.split_base[e] + (int64_t)(t - sh.split_pre[e]) * kChunk;
         const int64_t end = sh.split_base[e] + sh.split_len[e];
         const int64_t stop = b + kChunk < end ? b + kChunk : end;
-        for (int64_t p = b + l; p < stop; p += 32) c4 += counter_add<WIDTH>(cw, (uint32_t)(__ldg(cols + p) - xlo));
+        for (int64_t p = b + l; p < stop; p += 32) {
+            const uint32_t r = (uint32_t)(__ldg(cols + p) - xlo);
+            if (r < span) c4 += counter_add<WIDTH>(cw, r);
+            else flag_error(acc, 4ull);
+        }
     }
 }
 
@@ -480,13 +518,13 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __r
         uint64_t a_c4 = 0;
         if (width == 8)
             window_pass<8>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                           sh, a_c4);
+                           sh, a_c4, acc);
         else if (width == 16)
             window_pass<16>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                            sh, a_c4);
+                            sh, a_c4, acc);
         else
             window_pass<32>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                            sh, a_c4);
+                            sh, a_c4, acc);
         __syncthreads();
         if (sh.nsplit > 0) {
             if (threadIdx.x == 0) {
@@ -499,9 +537,9 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __r
                 sh.split_pre[ns] = run;
             }
             __syncthreads();
-            if (width == 8) split_pass<8>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else if (width == 16) split_pass<16>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else split_pass<32>(cols, (int32_t)xlo, cw, sh, a_c4);
+            if (width == 8) split_pass<8>(cols, (int32_t)xlo, (int32_t)xhi, cw, sh, a_c4, acc);
+            else if (width == 16) split_pass<16>(cols, (int32_t)xlo, (int32_t)xhi, cw, sh, a_c4, acc);
+            else split_pass<32>(cols, (int32_t)xlo, (int32_t)xhi, cw, sh, a_c4, acc);
             __syncthreads();
         }
         if (sink.batch()) {
@@ -536,8 +574,8 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
     k_c4_ginfo<<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.ginfo);
     HARP_LAUNCHED();
-    k_c4_rev<<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n,
-                                                              ws.rev);
+    k_c4_rev<<<grid_cap((2 * g->m + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
+        ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, 2 * g->m, ws.rev);
     HARP_LAUNCHED();
     k_c4_bpos<<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n, ws.fpos,
                                                                       ws.bpos);
