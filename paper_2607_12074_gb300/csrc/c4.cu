@@ -188,8 +188,12 @@ __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __rest
 }
 
 // ---------------------------------------------------------------------------------------------
-// Segment traversal helpers.
+// Segment traversal helpers.  Every loop issues kUnroll independent loads per lane before it uses
+// any of them: the per-element work is a load followed by a dependent shared-memory atomic, and
+// without the unrolling one load per warp in flight bounds the throughput by latency.
 // ---------------------------------------------------------------------------------------------
+constexpr int kUnroll = 4;
+
 // Warp-cooperative traversal of 32 segments (lane l owns cols[base_l .. base_l + len_l)):
 // flattened so that every lane takes one element per round.
 template <typename F>
@@ -203,31 +207,54 @@ __device__ __forceinline__ void warp_flat(const int32_t* __restrict__ cols, int6
     }
     const int excl = incl - len;
     const int total = __shfl_sync(kFull, incl, 31);
-    for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + l;
-        int o = 0;
+    for (int t0 = 0; t0 < total; t0 += 32 * kUnroll) {
+        int32_t xs[kUnroll];
 #pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            const int e = __shfl_sync(kFull, excl, o + s);
-            if (e <= t) o += s;
+        for (int r = 0; r < kUnroll; ++r) {
+            const int t = t0 + r * 32 + l;
+            int o = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int e = __shfl_sync(kFull, excl, o + s);
+                if (e <= t) o += s;
+            }
+            const int64_t ob = __shfl_sync(kFull, base, o);
+            const int oe = __shfl_sync(kFull, excl, o);
+            xs[r] = t < total ? __ldg(cols + ob + (t - oe)) : 0;
         }
-        const int64_t ob = __shfl_sync(kFull, base, o);
-        const int oe = __shfl_sync(kFull, excl, o);
-        if (t < total) f(__ldg(cols + ob + (t - oe)));
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r)
+            if (t0 + r * 32 + l < total) f(xs[r]);
+    }
+}
+
+// n consecutive elements from b, read by the whole warp (coalesced), kUnroll loads in flight per lane.
+template <typename F>
+__device__ __forceinline__ void warp_run(const int32_t* __restrict__ cols, int64_t b, int64_t n, F&& f) {
+    const int l = lane_id();
+    for (int64_t k0 = 0; k0 < n; k0 += 32 * kUnroll) {
+        int32_t xs[kUnroll];
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) {
+            const int64_t k = k0 + r * 32 + l;
+            xs[r] = k < n ? __ldg(cols + b + k) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r)
+            if (k0 + r * 32 + l < n) f(xs[r]);
     }
 }
 
 // Long segments one after the other, each read by the whole warp (coalesced); short ones flattened.
 template <typename F>
 __device__ __forceinline__ void warp_segments(const int32_t* __restrict__ cols, int64_t base, int len, F&& f) {
-    const int l = lane_id();
     uint32_t longs = __ballot_sync(kFull, len >= kLong);
     while (longs) {
         const int src = __ffs(longs) - 1;
         longs &= longs - 1;
         const int64_t b = __shfl_sync(kFull, base, src);
         const int n = __shfl_sync(kFull, len, src);
-        for (int k = l; k < n; k += 32) f(__ldg(cols + b + k));
+        warp_run(cols, b, n, f);
     }
     warp_flat(cols, base, len >= kLong ? 0 : len, f);
 }
@@ -293,7 +320,7 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
 // ---------------------------------------------------------------------------------------------
 // Warp-local mode: one warp per queued small root, hash table in shared memory.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSmallThreads) k_c4_small(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ cols,
                                                             const int32_t* __restrict__ deg,
                                                             const int32_t* __restrict__ dplus,
@@ -374,8 +401,9 @@ struct WinShared {
     int32_t split_pre[kSplitQ + 1];
 };
 
-// Self-check: an element outside the window (which would index past the counters) or a segment
-// outside its row is skipped and recorded in acc[ACC_ERR]; the host then reports HARP_EDEVICE.
+// Self-check: a segment outside its row, or one whose first or last element lies outside the window
+// (rows are sorted, so these two bound every element of the segment), is skipped and recorded in
+// acc[ACC_ERR]; the host then reports HARP_EDEVICE.
 __device__ __forceinline__ void flag_error(uint64_t* acc, unsigned long long bit) {
     atomicOr((unsigned long long*)&acc[ACC_ERR], bit);
 }
@@ -387,12 +415,7 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
                                             int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
                                             WinShared& sh, uint64_t& c4, uint64_t* acc) {
     const int l = lane_id();
-    const uint32_t span = (uint32_t)(xhi - xlo);
-    auto add = [&](int32_t x) {
-        const uint32_t r = (uint32_t)(x - xlo);
-        if (r < span) c4 += counter_add<WIDTH>(cw, r);
-        else flag_error(acc, 1ull);
-    };
+    auto add = [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); };
     const int ngroups = (int)((dm + 31) >> 5);
     for (;;) {
         int g = 0;
@@ -417,6 +440,10 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
                 flag_error(acc, 2ull);
                 p0 = p1 = 0;
             }
+            if (p1 > p0 && (cols[wb + p0] < xlo || cols[wb + p1 - 1] >= xhi)) {
+                flag_error(acc, 1ull);
+                p1 = p0;
+            }
             base = wb + p0;
             len = p1 > p0 ? (int)(p1 - p0) : 0;
         }
@@ -433,9 +460,8 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
 }
 
 template <int WIDTH>
-__device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int32_t xlo, int32_t xhi, uint32_t* cw,
-                                           WinShared& sh, uint64_t& c4, uint64_t* acc) {
-    const uint32_t span = (uint32_t)(xhi - xlo);
+__device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int32_t xlo, uint32_t* cw, WinShared& sh,
+                                           uint64_t& c4) {
     const int l = lane_id();
     const int ns = sh.nsplit < kSplitQ ? sh.nsplit : kSplitQ;
     const int total = sh.split_pre[ns];
@@ -454,11 +480,7 @@ __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int
         const int64_t b = sh.split_base[e] + (int64_t)(t - sh.split_pre[e]) * kChunk;
         const int64_t end = sh.split_base[e] + sh.split_len[e];
         const int64_t stop = b + kChunk < end ? b + kChunk : end;
-        for (int64_t p = b + l; p < stop; p += 32) {
-            const uint32_t r = (uint32_t)(__ldg(cols + p) - xlo);
-            if (r < span) c4 += counter_add<WIDTH>(cw, r);
-            else flag_error(acc, 4ull);
-        }
+        warp_run(cols, b, stop - b, [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); });
     }
 }
 
@@ -537,9 +559,9 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __r
                 sh.split_pre[ns] = run;
             }
             __syncthreads();
-            if (width == 8) split_pass<8>(cols, (int32_t)xlo, (int32_t)xhi, cw, sh, a_c4, acc);
-            else if (width == 16) split_pass<16>(cols, (int32_t)xlo, (int32_t)xhi, cw, sh, a_c4, acc);
-            else split_pass<32>(cols, (int32_t)xlo, (int32_t)xhi, cw, sh, a_c4, acc);
+            if (width == 8) split_pass<8>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else if (width == 16) split_pass<16>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else split_pass<32>(cols, (int32_t)xlo, cw, sh, a_c4);
             __syncthreads();
         }
         if (sink.batch()) {
