@@ -165,9 +165,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
             int64_t b = offp[v];
             if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
             uint32_t row = 0;
-            for (int64_t p0 = b; p0 < e; p0 += 32) {
-                const int64_t p = p0 + l;
-                const int32_t y = (p < e) ? colsp[p] : kInf;
+            auto probe = [&](int32_t y, int64_t p) {
                 if (y >= next && y <= last) {
                     const int j = hash_get(sHk[w], sHv[w], kWarpHashBits, y);
                     if (j >= 0) {
@@ -175,8 +173,15 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
                         row |= 1u << j;
                     }
                 }
-                // rows are sorted: stop once the chunk passed the largest candidate
-                if (__shfl_sync(kFull, y, 31) >= last) break;
+            };
+            for (int64_t p0 = b; p0 < e; p0 += 64) {  // two chunks' loads in flight
+                const int64_t pa = p0 + l, pb = p0 + 32 + l;
+                const int32_t ya = (pa < e) ? colsp[pa] : kInf;
+                const int32_t yb = (pb < e) ? colsp[pb] : kInf;
+                probe(ya, pa);
+                if (__shfl_sync(kFull, ya, 31) >= last) break;  // rows are sorted: past the largest candidate
+                probe(yb, pb);
+                if (__shfl_sync(kFull, yb, 31) >= last) break;
             }
             row = __reduce_or_sync(kFull, row);
             col += (row >> l) & 1u;
@@ -275,9 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
             int64_t b = offp[v];
             if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
             uint32_t hits = 0;
-            for (int64_t p0 = b; p0 < e; p0 += 32) {
-                const int64_t p = p0 + l;
-                const int32_t y = (p < e) ? colsp[p] : kInf;
+            auto probe = [&](int32_t y, int64_t p) {
                 if (y >= next && y <= last) {
                     const int j = hash_get(s.hk, s.hv, S::HB, y);
                     if (j >= 0) {
@@ -287,26 +290,52 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
                         ++hits;
                     }
                 }
-                if (__shfl_sync(kFull, y, 31) >= last) break;
+            };
+            for (int64_t p0 = b; p0 < e; p0 += 64) {  // two chunks' loads in flight
+                const int64_t pa = p0 + l, pb = p0 + 32 + l;
+                const int32_t ya = (pa < e) ? colsp[pa] : kInf;
+                const int32_t yb = (pb < e) ? colsp[pb] : kInf;
+                probe(ya, pa);
+                if (__shfl_sync(kFull, ya, 31) >= last) break;
+                probe(yb, pb);
+                if (__shfl_sync(kFull, yb, 31) >= last) break;
             }
             hits = warp_sum(hits);
             if (l == 0 && hits) atomicAdd(&s.own[i], hits);
         }
         __syncthreads();
-        // 4-cliques: warp per row i, lane per candidate bit j of the current word
+        // 4-cliques: warp per row i; the set bits j of row i are dealt to the lanes (32 per round), and
+        // each lane adds popc(row_i & row_j) over the words from j's word on.
         uint64_t a_tri = 0, a_k4 = 0, a_paw = 0;
         for (int i = w; i < d - 1; i += NW) {
             const uint32_t* Ri = &s.R[i * WS];
-            for (int ww = (i + 1) >> 5; ww < W; ++ww) {
-                const uint32_t word = Ri[ww];
-                if (!word) continue;
-                a_tri += (l == 0) ? (uint64_t)__popc(word) : 0;
-                if ((word >> l) & 1u) {
-                    const int j = (ww << 5) + l;
+            const uint32_t myw = l < W ? Ri[l] : 0u;  // W <= 32: lane l holds word l of the row
+            const int c = __popc(myw);
+            int pre = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, pre, o);
+                if (l >= o) pre += y;
+            }
+            const int B = __shfl_sync(kFull, pre, 31);  // bits in the row = triangles (u, L[i], *)
+            pre -= c;
+            a_tri += (l == 0) ? (uint64_t)B : 0;
+            for (int k0 = 0; k0 < B; k0 += 32) {
+                const int k = k0 + l;
+                int o = 0;  // word holding the k-th set bit: last lane with pre <= k
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const int e = __shfl_sync(kFull, pre, o + sft);
+                    if (e <= k) o += sft;
+                }
+                const uint32_t word = __shfl_sync(kFull, myw, o);
+                const int rank = k - __shfl_sync(kFull, pre, o);
+                if (k < B) {
+                    const int j = (o << 5) + (int)__fns(word, 0, rank + 1);
                     const uint32_t* Rj = &s.R[j * WS];
-                    uint32_t c = 0;
-                    for (int x = ww; x < W; ++x) c += __popc(Ri[x] & Rj[x]);
-                    a_k4 += c;
+                    uint32_t cnt = 0;
+                    for (int x = o; x < W; ++x) cnt += __popc(Ri[x] & Rj[x]);
+                    a_k4 += cnt;
                 }
             }
         }
