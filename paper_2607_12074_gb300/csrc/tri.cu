@@ -111,6 +111,33 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int32_t* __restrict__ 
     return m ? lo + __ffs(m) - 1 : hi;
 }
 
+// Walk the sorted list colsp[b, e) in warp-wide chunks with kProbeUnroll chunks' loads in flight,
+// calling probe(y, position) for every element, and stop after the chunk that passes `last`.
+constexpr int kProbeUnroll = 2;
+
+template <typename F>
+__device__ __forceinline__ void probe_list(const int32_t* __restrict__ colsp, int64_t b, int64_t e, int32_t last,
+                                           F&& probe) {
+    const int l = lane_id();
+    for (int64_t p0 = b; p0 < e; p0 += 32 * kProbeUnroll) {
+        int32_t ys[kProbeUnroll];
+#pragma unroll
+        for (int r = 0; r < kProbeUnroll; ++r) {
+            const int64_t p = p0 + r * 32 + l;
+            ys[r] = p < e ? colsp[p] : kInf;
+        }
+        bool done = false;
+#pragma unroll
+        for (int r = 0; r < kProbeUnroll; ++r) {
+            if (!done) {
+                probe(ys[r], p0 + r * 32 + l);
+                done = __shfl_sync(kFull, ys[r], 31) >= last;  // rows are sorted: past the largest candidate
+            }
+        }
+        if (done) break;
+    }
+}
+
 // single-graph mode: one block reduction and one atomic per statistic at the end of the kernel
 __device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint64_t k4, uint64_t paw, uint64_t* red) {
     tri = block_sum_u64(tri, red);
@@ -130,7 +157,7 @@ constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
 constexpr int kWarpHashBits = 7;  // 128 slots for <= 32 keys: load <= 1/4, ~1.4 slot reads per miss
 
-__global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __restrict__ offp,
+__global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __restrict__ offp,
                                                            const int32_t* __restrict__ colsp,
                                                            const int32_t* __restrict__ deg,
                                                            const int32_t* __restrict__ q,
@@ -174,15 +201,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_tri_warp(const int64_t* __rest
                     }
                 }
             };
-            for (int64_t p0 = b; p0 < e; p0 += 64) {  // two chunks' loads in flight
-                const int64_t pa = p0 + l, pb = p0 + 32 + l;
-                const int32_t ya = (pa < e) ? colsp[pa] : kInf;
-                const int32_t yb = (pb < e) ? colsp[pb] : kInf;
-                probe(ya, pa);
-                if (__shfl_sync(kFull, ya, 31) >= last) break;  // rows are sorted: past the largest candidate
-                probe(yb, pb);
-                if (__shfl_sync(kFull, yb, 31) >= last) break;
-            }
+            probe_list(colsp, b, e, last, probe);
             row = __reduce_or_sync(kFull, row);
             col += (row >> l) & 1u;
             if (l == i) sRow[w][i] = row;
@@ -291,15 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
                     }
                 }
             };
-            for (int64_t p0 = b; p0 < e; p0 += 64) {  // two chunks' loads in flight
-                const int64_t pa = p0 + l, pb = p0 + 32 + l;
-                const int32_t ya = (pa < e) ? colsp[pa] : kInf;
-                const int32_t yb = (pb < e) ? colsp[pb] : kInf;
-                probe(ya, pa);
-                if (__shfl_sync(kFull, ya, 31) >= last) break;
-                probe(yb, pb);
-                if (__shfl_sync(kFull, yb, 31) >= last) break;
-            }
+            probe_list(colsp, b, e, last, probe);
             hits = warp_sum(hits);
             if (l == 0 && hits) atomicAdd(&s.own[i], hits);
         }
