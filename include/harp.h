@@ -205,6 +205,83 @@ harp_status harp_count4_batch(const harp_csr* const* graphs, int64_t G, const ha
                               uint64_t (*counts_out)[6], void* stream);
 
 /* ------------------------------------------------------------------------------------------------
+ * Ownership-preserving partitioned counting (Section III-E) for graphs whose counting footprint
+ * exceeds a device-memory budget.  Rank space is cut into contiguous ranges; each range's halo (its
+ * rows and those of its lower neighbours truncated below the range's end, and the out-lists of all
+ * adjacent vertices) is copied to the device in turn, and only the anchors the range owns are
+ * enumerated: an anchor's owner is the range of the first vertex of its globally ordered tuple (the
+ * lowest vertex of a triangle / 4-clique anchor, the top vertex of a wedge anchor).  Per-edge
+ * triangle counts are summed over ranges before sum_e C(t_e, 2); the closure runs once.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct harp_partition_stats {
+    int64_t partitions;          /* ranges counted                                                */
+    int64_t m;                   /* undirected simple edges                                       */
+    int64_t halo_arcs;           /* arcs copied to the device over all ranges (rows + out-lists)  */
+    uint64_t h2d_bytes;          /* host-to-device bytes over all ranges                          */
+    uint64_t device_peak_bytes;  /* largest per-range device allocation                           */
+} harp_partition_stats;
+
+/* src, dst: HOST int32[m_in] (read only).  budget_bytes: device bytes one range may use (0 = half
+ * of the free memory).  parts: > 0 forces that many equal rank ranges (tests); 0 sizes the ranges
+ * to the budget, each the longest whose halo fits.  stats may be NULL.  Blocks until counts_out
+ * (host) is filled.
+ * Errors: HARP_EINVAL, HARP_EOVERFLOW, HARP_ENOMEM (the halo of some single vertex, or the
+ * per-vertex arrays alone, exceed the budget; on hub-dominated graphs the 2-hop halo of the top
+ * vertices approaches the whole graph), HARP_ECUDA, HARP_EDEVICE. */
+harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                                    uint64_t budget_bytes, int32_t parts, uint64_t counts_out[6],
+                                    harp_partition_stats* stats);
+
+/* ------------------------------------------------------------------------------------------------
+ * Serving with continuous batching.  Requests are admitted in arrival order while the device bytes
+ * held by admitted requests stay within the HBM budget; their edge lists are copied and their CSRs
+ * built on a copy stream while the previous batch counts on a compute stream; every built request
+ * joins the next batch (the batched pipeline, one launch per kernel).  A request larger than the
+ * budget is counted by the partitioned path under the budget.  Counts are exact and independent of
+ * the mix a request was batched with.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct harp_server harp_server;
+
+typedef struct harp_server_opts {
+    uint64_t hbm_budget_bytes;   /* device bytes for admitted requests (0 = 64 GiB)              */
+    uint32_t max_batch;          /* requests per batch (0 = 4096)                                */
+    uint32_t max_inflight;       /* admitted but unfinished requests (0 = unlimited)            */
+    uint32_t batch_window_us;    /* once a request is built, how long the executor may wait for  */
+                                 /* requests still being admitted or built to join its batch    */
+                                 /* (0 = launch at once with whatever is built)                 */
+    uint32_t reserved;           /* must be 0                                                    */
+} harp_server_opts;
+
+typedef struct harp_server_stats {
+    uint64_t completed, batches, batched_requests, partitioned, max_batch;
+    uint64_t pending, resident_bytes, peak_resident_bytes;
+    uint64_t latency_p50_us, latency_p99_us;  /* submit -> done, over the last 65,536 requests    */
+} harp_server_stats;
+
+/* Start a server on the current device (two worker threads).  opts may be NULL. */
+harp_status harp_server_create(const harp_server_opts* opts, harp_server** out);
+
+/* Enqueue a request; src/dst are HOST int32[m_in] and are copied before the call returns. */
+harp_status harp_submit(harp_server* srv, int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                        uint64_t* ticket);
+
+/* Non-blocking: *done = 0 while the request runs; *done = 1 once finished, in which case the
+ * request's status is returned, counts_out is filled on HARP_OK and the ticket is retired (a ticket
+ * belongs to one poller: the first poll or wait that sees it done retires it).
+ * HARP_ENOTFOUND for an unknown or retired ticket. */
+harp_status harp_poll(harp_server* srv, uint64_t ticket, uint64_t counts_out[6], int* done);
+
+/* Blocking form of harp_poll; timeout_ms < 0 waits without limit, HARP_ETIMEOUT when it expires
+ * (the request keeps running and can still be polled). */
+harp_status harp_wait(harp_server* srv, uint64_t ticket, uint64_t counts_out[6], double timeout_ms);
+
+harp_status harp_server_get_stats(harp_server* srv, harp_server_stats* out);
+
+/* Stop the workers (after the batch on the GPU, if any) and free everything; unfinished requests
+ * are dropped. */
+void harp_server_destroy(harp_server* srv);
+
+/* ------------------------------------------------------------------------------------------------
  * Counting without allocation.  The paper has no counterpart: this entry point exists for callers
  * that may not allocate device memory while they run (code inside another framework's
  * pre-reserved memory regime, services that forbid cudaMalloc/cudaFree after start-up because an

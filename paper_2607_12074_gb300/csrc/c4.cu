@@ -122,7 +122,7 @@ __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int
 
 // rev[a] = pos_w(u) for every lower arc (u -> w) at row position a of u.  Each thread takes a run of
 // kRevRun consecutive arcs of the CSR (one search for the run's first row, then it walks forward), so
-// hub rows are spread over many threads.
+// hub rows are spread over many threads.  arcs must equal off[n]; the walk never passes row n - 1.
 constexpr int kRevRun = 16;
 
 __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off,
         int64_t lower_end = ub + ((int64_t)deg[u] - dplus[u]);
         for (int64_t a = a0; a < a1; ++a) {
             while (a >= ue) {  // next non-empty row
+                if (u + 1 >= n) return;  // only if arcs > off[n]
                 ++u;
                 ub = ue;
                 ue = off[u + 1];
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
                                                      const int32_t* __restrict__ fpos,
                                                      const int32_t* __restrict__ rev,
                                                      const int32_t* __restrict__ gid,
-                                                     const int64_t* __restrict__ ginfo, int64_t n, uint32_t warp_max,
+                                                     const int64_t* __restrict__ ginfo, int64_t n, int64_t own_lo,
+                                                     int64_t own_hi, uint32_t warp_max,
                                                      int32_t* __restrict__ q_small, int32_t* __restrict__ q_win,
                                                      int32_t* __restrict__ wcount, uint64_t* __restrict__ acc) {
     const int l = lane_id();
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
     unsigned long long* qcnt_win = (unsigned long long*)&acc[Q_C4_WIN];
     for (int64_t k = wid; k < n; k += nw) {
         const int32_t u = (int32_t)(n - 1 - k);
+        if (u < own_lo || u >= own_hi) continue;  // the owner rule: only this range's roots
         const int64_t dm = (int64_t)deg[u] - dplus[u];
         if (dm < 2) continue;
         const int64_t ub = off[u];
@@ -596,15 +599,16 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
     k_c4_ginfo<<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.ginfo);
     HARP_LAUNCHED();
-    k_c4_rev<<<grid_cap((2 * g->m + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
-        ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, 2 * g->m, ws.rev);
+    const int64_t arcs = ws.arcs >= 0 ? ws.arcs : 2 * g->m;  // must equal off[n]
+    k_c4_rev<<<grid_cap((arcs + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
+        ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, arcs, ws.rev);
     HARP_LAUNCHED();
     k_c4_bpos<<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n, ws.fpos,
                                                                       ws.bpos);
     HARP_LAUNCHED();
     k_c4_classify<<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev,
-                                                                   ws.gid, ws.ginfo, n, warp_max, ws.q_mid, ws.q_win,
-                                                                   wcount, ws.acc);
+                                                                   ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
+                                                                   ws.q_mid, ws.q_win, wcount, ws.acc);
     HARP_LAUNCHED();
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));

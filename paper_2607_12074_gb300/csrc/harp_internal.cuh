@@ -121,6 +121,11 @@ struct Workspace {
     const int32_t* gid_in = nullptr;  // [n] graph of each input (union) vertex
     int32_t* gid = nullptr;           // [n] graph of each rank-order vertex
     uint64_t* accG = nullptr;         // [G * kGStride] per-graph accumulators
+    // partitioned mode: only anchors/roots u in [own_lo, own_hi) are enumerated (the owner rule), and
+    // the full-CSR arc count off[n] differs from 2m because halo rows are truncated (it may be 0);
+    // -1 = a whole graph, off[n] = 2m
+    int64_t own_lo = 0, own_hi = INT64_MAX;
+    int64_t arcs = -1;
 };
 
 // The workspace layout for (n, m): assigns every array of ws inside [base, base + returned bytes)

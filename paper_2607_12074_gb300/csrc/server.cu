@@ -1,0 +1,355 @@
+// Serving: continuous batching of motif-count requests on one GPU.
+//
+// Requests (host edge lists, copied at submit) wait in a FIFO.  A builder thread admits them in
+// order while the device memory held by admitted requests stays within the HBM budget and a slot is
+// free, copies each edge list to the device and builds its CSR on a copy stream.  An executor thread
+// takes every built request as the next batch and counts it with the batched pipeline (the disjoint
+// union of the batch, one launch per kernel) on a compute stream; with a batching window it first
+// waits, up to the window, while requests are still queued for admission or being built.  Requests that arrive while a batch
+// is on the GPU are admitted, copied and built meanwhile (their copies and CSR builds overlap the
+// running count) and form the next batch as soon as it finishes; results are retired per ticket.
+// A request whose own footprint exceeds the budget is counted by the halo-partitioned path with the
+// canonical anchor-owner rule (harp_count4_partitioned) under the same budget.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "harp_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum class ReqState { Pending, Built, Running, Done };
+
+struct Request {
+    uint64_t ticket = 0;
+    int64_t n = 0, m_in = 0;
+    std::vector<int32_t> src, dst;
+    ReqState state = ReqState::Pending;
+    harp_status status = HARP_OK;
+    uint64_t counts[6] = {0, 0, 0, 0, 0, 0};
+    size_t need = 0;  // device bytes this request holds from admission to completion
+    harp_csr* csr = nullptr;
+    bool partitioned = false;
+    Clock::time_point t_submit, t_done;
+};
+
+// Device bytes one request holds while resident: its CSR, its share of the batch's union copy and
+// counting workspace (estimated with the input pair count as an upper bound of the edge count).
+size_t footprint(int64_t n, int64_t m_in) {
+    harp::Workspace probe;
+    const size_t ws = harp::ws_layout(probe, nullptr, n, m_in);
+    const size_t csr = sizeof(int64_t) * (size_t)(n + 1) + sizeof(int32_t) * 2 * (size_t)m_in;
+    const size_t batch_share = csr + sizeof(int32_t) * 2 * (size_t)n + 16 * sizeof(uint64_t) * 2;
+    const size_t build_tmp = sizeof(uint64_t) * 2 * 2 * (size_t)m_in + sizeof(int64_t) * (2 * (size_t)m_in + 1) +
+                             sizeof(int32_t) * 4 * (size_t)m_in;
+    const size_t steady = csr + batch_share + ws;
+    return steady > build_tmp + csr ? steady : build_tmp + csr;
+}
+
+}  // namespace
+
+struct harp_server {
+    int device = 0;
+    harp_server_opts opts{};
+    std::mutex mu;
+    std::condition_variable cv_build;   // builder: pending work or room freed
+    std::condition_variable cv_exec;    // executor: built requests available
+    std::condition_variable cv_done;    // waiters: a request finished
+    std::deque<uint64_t> pending;       // tickets in arrival order
+    std::deque<uint64_t> built;         // tickets with a CSR, waiting for a batch
+    std::unordered_map<uint64_t, Request*> reqs;
+    uint64_t next_ticket = 1;
+    size_t resident = 0;
+    size_t peak_resident = 0;
+    int64_t inflight = 0;
+    int64_t building = 0;               // requests between admission and a built CSR
+    bool stop = false;
+    cudaStream_t copy_stream = nullptr, compute_stream = nullptr;
+    std::thread builder, executor;
+    // statistics
+    uint64_t completed = 0, batches = 0, partitioned = 0, batched_requests = 0, max_batch_seen = 0;
+    std::vector<double> latencies_ms;   // ring of the last kLatencyRing completions
+    size_t latency_next = 0;
+};
+
+namespace {
+
+constexpr size_t kLatencyRing = 65536;
+
+void finish(harp_server* s, Request* r, harp_status st) {
+    r->status = st;
+    r->state = ReqState::Done;
+    r->t_done = Clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    if (s->latencies_ms.size() < kLatencyRing) s->latencies_ms.push_back(ms);
+    else s->latencies_ms[s->latency_next] = ms;
+    s->latency_next = (s->latency_next + 1) % kLatencyRing;
+    s->completed++;
+}
+
+// The head of the queue can be admitted now (caller holds the lock): a free slot, and room in the
+// budget.  An oversize request runs alone under the whole budget; others must fit beside the
+// resident set.
+bool can_admit(const harp_server* s) {
+    if (s->pending.empty()) return false;
+    const Request* r = s->reqs.at(s->pending.front());
+    const bool slot = s->opts.max_inflight == 0 || s->inflight < (int64_t)s->opts.max_inflight;
+    const bool oversize = r->need > s->opts.hbm_budget_bytes;
+    return slot && (oversize ? s->resident == 0 : s->resident + r->need <= s->opts.hbm_budget_bytes);
+}
+
+void builder_loop(harp_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        s->cv_build.wait(lk, [&] { return s->stop || can_admit(s); });
+        if (s->stop) return;
+        Request* r = s->reqs[s->pending.front()];
+        s->pending.pop_front();
+        const bool oversize = r->need > s->opts.hbm_budget_bytes;
+        const size_t charge = oversize ? s->opts.hbm_budget_bytes : r->need;
+        s->resident += charge;
+        if (s->resident > s->peak_resident) s->peak_resident = s->resident;
+        s->inflight++;
+        harp_status st;
+        if (oversize) {
+            lk.unlock();
+            // halo-partitioned path with the owner rule, within the budget; counted right here
+            st = harp_count4_partitioned(r->n, r->m_in, r->src.data(), r->dst.data(), s->opts.hbm_budget_bytes, 0,
+                                         r->counts, nullptr);
+            lk.lock();
+            r->partitioned = true;
+            s->partitioned++;
+            s->resident -= charge;
+            s->inflight--;
+            finish(s, r, st);
+            s->cv_done.notify_all();
+            s->cv_build.notify_all();
+            continue;
+        }
+        s->building++;
+        lk.unlock();
+        st = harp_build_csr(r->n, r->m_in, r->src.data(), r->dst.data(), HARP_PTR_HOST, s->copy_stream, &r->csr);
+        lk.lock();
+        s->building--;
+        if (st != HARP_OK) {
+            s->resident -= charge;
+            s->inflight--;
+            finish(s, r, st);
+            s->cv_done.notify_all();
+            s->cv_exec.notify_one();  // a waiting batch need not wait for this one
+            continue;
+        }
+        r->state = ReqState::Built;
+        std::vector<int32_t>().swap(r->src);  // the host copy is no longer needed
+        std::vector<int32_t>().swap(r->dst);
+        s->built.push_back(r->ticket);
+        s->cv_exec.notify_one();
+    }
+}
+
+void executor_loop(harp_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        s->cv_exec.wait(lk, [&] { return s->stop || !s->built.empty(); });
+        if (s->stop) return;
+        const size_t cap = s->opts.max_batch ? s->opts.max_batch : 4096;
+        if (s->opts.batch_window_us) {
+            // gather: wait, up to the window, while more requests are on their way (being built, or
+            // admissible now); requests held back by the budget cannot join before this batch ends
+            s->cv_exec.wait_for(lk, std::chrono::microseconds(s->opts.batch_window_us), [&] {
+                return s->stop || s->built.size() >= cap || (s->building == 0 && !can_admit(s));
+            });
+            if (s->stop) return;
+        }
+        std::vector<Request*> batch;
+        while (!s->built.empty() && batch.size() < cap) {
+            Request* r = s->reqs[s->built.front()];
+            s->built.pop_front();
+            r->state = ReqState::Running;
+            batch.push_back(r);
+        }
+        lk.unlock();
+        std::vector<const harp_csr*> hs(batch.size());
+        for (size_t k = 0; k < batch.size(); ++k) hs[k] = batch[k]->csr;
+        std::vector<uint64_t> counts(6 * batch.size());
+        harp_batch* b = nullptr;
+        harp_status st = harp_batch_create(hs.data(), (int64_t)hs.size(), &b);
+        if (st == HARP_OK) {
+            harp_plan p;
+            std::memset(&p, 0, sizeof(p));
+            p.version = HARP_ABI_VERSION;
+            p.flags = HARP_PLAN_NO_GRAPH;  // every batch has a different shape
+            st = harp_batch_count(b, &p, reinterpret_cast<uint64_t(*)[6]>(counts.data()), nullptr, s->compute_stream);
+            harp_batch_free(b);
+        }
+        for (Request* r : batch) {
+            harp_csr_free(r->csr);
+            r->csr = nullptr;
+        }
+        lk.lock();
+        s->batches++;
+        s->batched_requests += batch.size();
+        if (batch.size() > s->max_batch_seen) s->max_batch_seen = batch.size();
+        for (size_t k = 0; k < batch.size(); ++k) {
+            Request* r = batch[k];
+            if (st == HARP_OK) std::memcpy(r->counts, &counts[6 * k], sizeof(r->counts));
+            s->resident -= r->need;
+            s->inflight--;
+            finish(s, r, st);
+        }
+        s->cv_done.notify_all();
+        s->cv_build.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+harp_status harp_server_create(const harp_server_opts* opts, harp_server** out) {
+    if (!out) return HARP_EINVAL;
+    harp_server* s = new (std::nothrow) harp_server();
+    if (!s) return HARP_ENOMEM;
+    if (opts && opts->reserved != 0) {
+        delete s;
+        return HARP_EINVAL;
+    }
+    if (opts) s->opts = *opts;
+    if (s->opts.hbm_budget_bytes == 0) s->opts.hbm_budget_bytes = (uint64_t)64 << 30;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return HARP_ECUDA;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        harp::record_cuda_error(e);
+        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+        delete s;
+        return HARP_ECUDA;
+    }
+    s->builder = std::thread(builder_loop, s);
+    s->executor = std::thread(executor_loop, s);
+    *out = s;
+    return HARP_OK;
+}
+
+harp_status harp_submit(harp_server* s, int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                        uint64_t* ticket) {
+    if (!s || !ticket || n < 0 || m_in < 0 || (m_in > 0 && (!src || !dst))) return HARP_EINVAL;
+    if (n > 2147483647LL || m_in > 2147483647LL) return HARP_EOVERFLOW;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return HARP_ENOMEM;
+    r->n = n;
+    r->m_in = m_in;
+    r->src.assign(src, src + m_in);
+    r->dst.assign(dst, dst + m_in);
+    r->need = footprint(n, m_in);
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+        delete r;
+        return HARP_EINVAL;
+    }
+    r->ticket = s->next_ticket++;
+    s->reqs[r->ticket] = r;
+    s->pending.push_back(r->ticket);
+    *ticket = r->ticket;
+    s->cv_build.notify_one();
+    return HARP_OK;
+}
+
+harp_status harp_poll(harp_server* s, uint64_t ticket, uint64_t counts_out[6], int* done) {
+    if (!s || !done) return HARP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return HARP_ENOTFOUND;
+    Request* r = it->second;
+    if (r->state != ReqState::Done) {
+        *done = 0;
+        return HARP_OK;
+    }
+    *done = 1;
+    const harp_status st = r->status;
+    if (st == HARP_OK && counts_out) std::memcpy(counts_out, r->counts, sizeof(r->counts));
+    s->reqs.erase(it);
+    delete r;
+    return st;
+}
+
+harp_status harp_wait(harp_server* s, uint64_t ticket, uint64_t counts_out[6], double timeout_ms) {
+    if (!s) return HARP_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return HARP_ENOTFOUND;
+    Request* r = it->second;
+    const auto pred = [&] { return r->state == ReqState::Done; };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, pred);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred)) {
+        return HARP_ETIMEOUT;
+    }
+    const harp_status st = r->status;
+    if (st == HARP_OK && counts_out) std::memcpy(counts_out, r->counts, sizeof(r->counts));
+    s->reqs.erase(ticket);
+    delete r;
+    return st;
+}
+
+harp_status harp_server_get_stats(harp_server* s, harp_server_stats* out) {
+    if (!s || !out) return HARP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->completed = s->completed;
+    out->batches = s->batches;
+    out->batched_requests = s->batched_requests;
+    out->partitioned = s->partitioned;
+    out->max_batch = s->max_batch_seen;
+    out->pending = s->pending.size() + s->built.size();
+    out->resident_bytes = s->resident;
+    out->peak_resident_bytes = s->peak_resident;
+    out->latency_p50_us = out->latency_p99_us = 0;
+    if (!s->latencies_ms.empty()) {
+        std::vector<double> v(s->latencies_ms);
+        auto q = [&](double f) {
+            const size_t k = (size_t)(f * (double)(v.size() - 1) + 0.5);
+            std::nth_element(v.begin(), v.begin() + (long)k, v.end());
+            return (uint64_t)(v[k] * 1000.0 + 0.5);
+        };
+        out->latency_p50_us = q(0.50);
+        out->latency_p99_us = q(0.99);
+    }
+    return HARP_OK;
+}
+
+void harp_server_destroy(harp_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_build.notify_all();
+    s->cv_exec.notify_all();
+    if (s->builder.joinable()) s->builder.join();
+    if (s->executor.joinable()) s->executor.join();
+    cudaSetDevice(s->device);
+    for (auto& kv : s->reqs) {
+        if (kv.second->csr) harp_csr_free(kv.second->csr);
+        delete kv.second;
+    }
+    cudaStreamDestroy(s->copy_stream);
+    cudaStreamDestroy(s->compute_stream);
+    delete s;
+}
+
+}  // extern "C"

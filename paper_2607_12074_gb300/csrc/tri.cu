@@ -39,14 +39,14 @@ __device__ __forceinline__ int tri_class(int d) {
     return d < 2 ? -1 : (d <= 32 ? 0 : (d <= kCta1 ? 1 : (d <= kCta2 ? 2 : (d <= kCtaMax ? 3 : 4))));
 }
 
-__global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int32_t* __restrict__ q,
-                               unsigned long long* __restrict__ cnt) {
+__global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int64_t own_lo, int64_t own_hi,
+                               int32_t* __restrict__ q, unsigned long long* __restrict__ cnt) {
     const int l = lane_id();
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - l; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = n - 1 - (base + l);
         int cls = -1;
-        if (u >= 0) cls = tri_class(dplus[u]);
+        if (u >= own_lo && u < own_hi && u < n) cls = tri_class(dplus[u]);
         cls = cls > 0 ? 1 : cls;  // 0: warp queue, 1: CTA queue
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -492,7 +492,7 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     unsigned long long* cnt = (unsigned long long*)&ws.acc[Q_TRI_WARP];
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.q_tri, cnt);
+    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, ws.q_tri, cnt);
     HARP_LAUNCHED();
     const Sink sink{ws.acc, ws.gid, ws.accG};
     k_tri_warp<<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, cnt, ws.te, sink);

@@ -72,6 +72,28 @@ class harp_select_opts(ctypes.Structure):
     ]
 
 
+class harp_partition_stats(ctypes.Structure):
+    _fields_ = [("partitions", ctypes.c_int64), ("m", ctypes.c_int64), ("halo_arcs", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_uint64), ("device_peak_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class harp_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("batch_window_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class harp_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("completed", "batches", "batched_requests", "partitioned",
+                                                "max_batch", "pending", "resident_bytes", "peak_resident_bytes",
+                                                "latency_p50_us", "latency_p99_us")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -108,6 +130,18 @@ def lib():
         L.harp_batch_free.restype = None
         L.harp_count4_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(harp_plan), vp, vp]
         for name in ("harp_batch_create", "harp_batch_count", "harp_batch_info", "harp_count4_batch"):
+            getattr(L, name).restype = i32
+        L.harp_count4_partitioned.argtypes = [i64, i64, vp, vp, ctypes.c_uint64, ctypes.c_int32, pu64,
+                                              ctypes.POINTER(harp_partition_stats)]
+        L.harp_server_create.argtypes = [ctypes.POINTER(harp_server_opts), ctypes.POINTER(vp)]
+        L.harp_submit.argtypes = [vp, i64, i64, vp, vp, pu64]
+        L.harp_poll.argtypes = [vp, ctypes.c_uint64, pu64, ctypes.POINTER(ctypes.c_int)]
+        L.harp_wait.argtypes = [vp, ctypes.c_uint64, pu64, ctypes.c_double]
+        L.harp_server_get_stats.argtypes = [vp, ctypes.POINTER(harp_server_stats)]
+        L.harp_server_destroy.argtypes = [vp]
+        L.harp_server_destroy.restype = None
+        for name in ("harp_count4_partitioned", "harp_server_create", "harp_submit", "harp_poll", "harp_wait",
+                     "harp_server_get_stats"):
             getattr(L, name).restype = i32
         L.harp_set_profiling.argtypes = [i32]
         L.harp_last_stage_times.argtypes = [ctypes.POINTER(ctypes.c_float), pi64]
@@ -310,6 +344,70 @@ def harp_count4_batch(graphs, plan: harp_plan | None = None, stream=None) -> np.
     _check(lib().harp_count4_batch(arr, len(graphs), _plan_ref(plan), counts.ctypes.data, _stream_handle(stream)),
            "harp_count4_batch")
     return counts[:len(graphs)]
+
+
+def harp_count4_partitioned(n: int, src, dst, budget_bytes: int = 0, parts: int = 0):
+    """Counts of a graph given as a host edge list, by owner-rule partitions under a device budget.
+
+    Returns (counts uint64[6], stats dict)."""
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+    d = np.ascontiguousarray(np.asarray(dst, dtype=np.int32))
+    out = np.zeros(6, np.uint64)
+    st = harp_partition_stats()
+    _check(lib().harp_count4_partitioned(int(n), s.size, s.ctypes.data, d.ctypes.data, int(budget_bytes), int(parts),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(st)),
+           "harp_count4_partitioned")
+    return out, st.as_dict()
+
+
+class Server:
+    """A continuous-batching counting server (harp_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0,
+                 batch_window_us: int = 0):
+        o = harp_server_opts(hbm_budget_bytes, max_batch, max_inflight, batch_window_us, 0)
+        h = ctypes.c_void_p()
+        _check(lib().harp_server_create(ctypes.byref(o), ctypes.byref(h)), "harp_server_create")
+        self.handle = h
+
+    def submit(self, n: int, src, dst) -> int:
+        s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+        d = np.ascontiguousarray(np.asarray(dst, dtype=np.int32))
+        t = ctypes.c_uint64()
+        _check(lib().harp_submit(self.handle, int(n), s.size, s.ctypes.data, d.ctypes.data, ctypes.byref(t)),
+               "harp_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running; the counts once done (raises HarpError on a failed request)."""
+        out = np.zeros(6, np.uint64)
+        done = ctypes.c_int(0)
+        st = lib().harp_poll(self.handle, ticket, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                             ctypes.byref(done))
+        _check(st, "harp_poll")
+        return out if done.value else None
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0) -> np.ndarray:
+        out = np.zeros(6, np.uint64)
+        _check(lib().harp_wait(self.handle, ticket, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                               float(timeout_ms)), "harp_wait")
+        return out
+
+    def stats(self) -> dict:
+        st = harp_server_stats()
+        _check(lib().harp_server_get_stats(self.handle, ctypes.byref(st)), "harp_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            lib().harp_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def harp_set_profiling(enable: bool) -> None:

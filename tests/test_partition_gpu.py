@@ -1,0 +1,77 @@
+"""Owner-rule partitioned counting (GPU): every partition count k gives exactly the counts of the
+unpartitioned path and of the oracle, whether the ranges are forced (k in {1, 2, 3, 7, 16}) or sized to
+a small device budget."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+from graph_families import cocktail, complete, kbip, wheel  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def harp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_12074_gb300 import _build, harp as H
+    _build.build()
+    H.lib()
+    return H
+
+
+def graphs():
+    out = [graphgen.ba_2000(), graphgen.er(3000, 40, 5), graphgen.rgg(5000, 20, 6), graphgen.rmat(14, 16, seed=2),
+           graphgen.chung_lu(20000, 2.1, 1500, 12, 7)]
+    for name, (n, e) in {"K300": (300, complete(300)), "W3000": (3001, wheel(3000)),
+                         "K120,200": (320, kbip(120, 200)), "CP80": (160, cocktail(80))}.items():
+        out.append(graphgen.Graph(n, e[0], e[1], name))
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 16])
+def test_forced_partitions_match_whole_graph(harp, k):
+    for g in graphs():
+        whole = harp.count4_edges(g.n, g.src, g.dst)
+        got, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34, parts=k)
+        assert got.tolist() == whole.tolist(), (g.name, k)
+        assert st["partitions"] == k
+
+
+@pytest.mark.parametrize("make", [lambda: graphgen.rmat(15, 16, seed=4), lambda: graphgen.rgg(40000, 16, 9),
+                                  lambda: graphgen.er(30000, 12, 3)])
+def test_budget_sized_partitions_and_oracle(harp, make):
+    g = make()
+    want = O.count4_combo(g.n, g.src, g.dst)
+    whole, st1 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34)
+    assert st1["partitions"] == 1
+    # the largest range of 16 equal ranges fits any range the greedy cut can start (its halo contains
+    # the halo of every single vertex of that range); below the whole graph's footprint it must cut
+    _, st16 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34, parts=16)
+    budget = st16["device_peak_bytes"]
+    got, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=budget)
+    if budget < st1["device_peak_bytes"]:
+        assert st["partitions"] > 1
+    assert st["device_peak_bytes"] <= budget
+    assert got.tolist() == whole.tolist() == want.tolist()
+    with pytest.raises(harp.HarpError) as ei:    # below every single-vertex halo of the top range
+        harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=st16["device_peak_bytes"] // 64)
+    assert ei.value.status == harp.HARP_ENOMEM
+
+
+def test_partitioned_errors(harp):
+    with pytest.raises(harp.HarpError) as ei:
+        harp.harp_count4_partitioned(4, [0, 9], [1, 2], budget_bytes=1 << 30)
+    assert ei.value.status == harp.HARP_EINVAL
+    g = graphgen.er(2000, 10, 1)
+    with pytest.raises(harp.HarpError) as ei:
+        harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1024)  # the per-vertex arrays alone exceed it
+    assert ei.value.status == harp.HARP_ENOMEM
