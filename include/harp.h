@@ -111,12 +111,17 @@ harp_status harp_csr_arrays(const harp_csr* g, const int64_t** offsets, const in
 #define HARP_PROBE_BSEARCH 2u  /* frontier membership by binary search in the sorted N+(u)         */
 
 #define HARP_PLAN_NO_GRAPH 1u  /* flags: launch kernels one by one instead of a captured CUDA graph */
+#define HARP_PLAN_NO_REUSE 2u  /* flags: signature reuse off: every 4-clique extension recomputes  */
+                               /* |N+(w) n S_uv| from N+(w) instead of reading the staged frontier */
+                               /* of (u, w) (Section III-C); the counts are identical              */
 
 typedef struct harp_plan {
     uint32_t version;            /* HARP_ABI_VERSION                                               */
     uint32_t basis;              /* HARP_BASIS_*                                                   */
     uint32_t tri_probe;          /* HARP_PROBE_* for the triangle / 4-clique anchor                */
     uint32_t tri_warp_max;       /* out-degree <= this (<= 32): warp-local mode; above: CTA mode   */
+    uint32_t tri_cta_max;        /* out-degree <= this (<= 1024): frontiers staged in shared memory */
+                                 /* (CTA mode); above: unstaged fallback, every extension a miss    */
     uint32_t c4_warp_max_work;   /* wedge work W(u) <= this: warp-local hash table                 */
     uint32_t c4_cta_max_work;    /* W(u) <= this: CTA hash table; above: CTA windowed counters     */
     uint32_t c4_window_bytes;    /* shared-memory bytes of one dense counter window                */
@@ -147,6 +152,11 @@ harp_status harp_select_anchors(const harp_csr* g, const harp_select_opts* opts,
 /* Count the six induced motifs of g.  plan may be NULL (library default plan).  Runs on the
  * handle's stream and returns after the counts are on the host in counts_out[6]. */
 harp_status harp_count4(const harp_csr* g, const harp_plan* plan, uint64_t counts_out[6]);
+
+/* Signature-reuse counters of the last blocking count on g (harp_count4 / harp_count4_stats):
+ * lookups = 4-clique extensions (one per triangle), hits = those answered by a staged frontier
+ * (Section III-C).  HARP_ENOTFOUND before the first blocking count. */
+harp_status harp_reuse_stats(const harp_csr* g, uint64_t* lookups, uint64_t* hits);
 
 /* As harp_count4, and also return the anchor statistics (HARP_STAT_* order) in stats_out[8]. */
 harp_status harp_count4_stats(const harp_csr* g, const harp_plan* plan, uint64_t counts_out[6],

@@ -173,6 +173,9 @@ harp_status count_to_host(const harp_csr* gc, const harp_plan* plan, uint64_t* c
     HARP_CK(cudaMemcpyAsync(host, g->ws.acc, sizeof(host), cudaMemcpyDeviceToHost, g->stream));
     HARP_CK(cudaStreamSynchronize(g->stream));
     if (host[ACC_ERR]) return HARP_EDEVICE;  // a kernel's self-check skipped an out-of-range access
+    g->sig_lookups = host[ACC_T];
+    g->sig_hits = host[ACC_SIG_HITS];
+    g->have_reuse = true;
     std::memcpy(counts_out, host + OUT_COUNTS, 6 * sizeof(uint64_t));
     if (stats_out) std::memcpy(stats_out, host + OUT_STATS, HARP_NSTATS * sizeof(uint64_t));
     return HARP_OK;
@@ -227,6 +230,14 @@ harp_status harp_build_csr(int64_t n, int64_t m_in, const int32_t* src, const in
         return st;
     }
     *out = g;
+    return HARP_OK;
+}
+
+harp_status harp_reuse_stats(const harp_csr* g, uint64_t* lookups, uint64_t* hits) {
+    if (!g) return HARP_EINVAL;
+    if (!g->have_reuse) return HARP_ENOTFOUND;
+    if (lookups) *lookups = g->sig_lookups;
+    if (hits) *hits = g->sig_hits;
     return HARP_OK;
 }
 

@@ -75,6 +75,7 @@ enum : int {
     W_TOTAL = 35,          // total window items of the windowed wedge kernel
     Q_SORT_CTA = 36,       // rows for the CTA row sort (36) and the hub row sort (37)
     T_TRI_M = 38,          // ticket of the 512-wide CTA triangle kernel
+    ACC_SIG_HITS = 39,     // 4-clique extensions answered by a staged signature frontier
     kOutLen = 40
 };
 
@@ -145,6 +146,9 @@ struct harp_csr {
     int32_t* cols = nullptr;  // [2m]
     size_t csr_bytes = 0;
     harp::Workspace ws;
+    // signature-reuse counters of the last blocking count (valid once have_reuse is set)
+    uint64_t sig_lookups = 0, sig_hits = 0;
+    bool have_reuse = false;
 };
 
 namespace harp {

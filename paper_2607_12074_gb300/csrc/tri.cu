@@ -15,12 +15,21 @@
 //   * 4-cliques:   K4_u = sum over set bits (i, j) of popc(row_i & row_j)   (the X_3 extension)
 //   * paw sums:    sum over triangles of (d_a + d_b + d_c)
 // The intersection walks N+(L[i]) from L[i+1] (found by a warp-parallel 32-ary search when the list
-// is long) up to the largest element of L, and looks each element up in a shared-memory hash of L
-// that returns its index j.
-// Warp-local mode: d <= 32, rows are single words, one warp per anchor.
-// CTA mode: 32 < d <= 1024 in three sizes (256 / 512 / 1024), rows in shared memory, one block per
-// anchor.  Fallback (d > 1024, hubs of very large graphs): per out-arc ordered intersections
-// through global memory with binary-searched membership; 4-cliques by binary search in N+(w).
+// is long) up to the largest element of L, and looks each element up in L (its index j).
+// Warp-local mode: d <= tri_warp_max (<= 32), rows are single words, one warp per anchor.
+// CTA mode: up to tri_cta_max (<= 1024) in three sizes (256 / 512 / 1024), rows in shared memory, one
+// block per anchor.  Fallback (larger d, hubs of very large graphs): per out-arc ordered
+// intersections through global memory with binary-searched membership; 4-cliques by binary search
+// in N+(w).  Membership of y in L is a hash lookup (HARP_PROBE_HASH) or a binary search of the
+// sorted L in shared memory (HARP_PROBE_BSEARCH).
+//
+// Signature reuse (Section III-C): the extension of (u, v, w) to a 4-clique needs
+// |N+(w) n S_uv|, and since S_uv is a subset of L this is popc(row_v & row_w): the staged frontier of
+// the signature (u, w) answers it.  Every triangle is one such lookup; it is a hit when the anchor's
+// rows are staged (warp and CTA modes) and a miss in the fallback, which recomputes the
+// intersection from N+(w).  With reuse switched off (HARP_PLAN_NO_REUSE) the staged modes recompute
+// too, by walking N+(w) in global memory; the counts are identical either way.  acc[ACC_SIG_HITS]
+// counts hits; the lookups are the triangles.
 #include "harp_internal.cuh"
 
 namespace harp {
@@ -32,21 +41,27 @@ constexpr int kCtaMax = 1024;
 constexpr int kInf = 0x7fffffff;
 constexpr int32_t kNoKey = -1;
 
-// Anchor queues in ws.q_tri (n entries): warp-mode anchors (2 <= d <= 32) from the front,
-// CTA-mode and fallback anchors (d > 32) from the back.  Vertices are scanned in descending rank,
-// so high-degree anchors tend to be queued (and taken) first.
-__device__ __forceinline__ int tri_class(int d) {
-    return d < 2 ? -1 : (d <= 32 ? 0 : (d <= kCta1 ? 1 : (d <= kCta2 ? 2 : (d <= kCtaMax ? 3 : 4))));
+// Anchor queues in ws.q_tri (n entries): warp-mode anchors (2 <= d <= tri_warp_max) from the front,
+// CTA-mode and fallback anchors from the back.  Vertices are scanned in descending rank, so
+// high-degree anchors tend to be queued (and taken) first.
+//
+// Tier of an anchor of out-degree d: -1 none, 0 warp, 1/2/3 CTA 256/512/1024, 4 fallback.
+// wmax <= 32 and cmax <= kCtaMax (the plan's tri_warp_max / tri_cta_max).
+__device__ __forceinline__ int tri_class(int d, int wmax, int cmax) {
+    if (d < 2) return -1;
+    if (d <= wmax) return 0;
+    if (d > cmax) return 4;
+    return d <= kCta1 ? 1 : (d <= kCta2 ? 2 : 3);
 }
 
 __global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int64_t own_lo, int64_t own_hi,
-                               int32_t* __restrict__ q, unsigned long long* __restrict__ cnt) {
+                               int wmax, int cmax, int32_t* __restrict__ q, unsigned long long* __restrict__ cnt) {
     const int l = lane_id();
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - l; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = n - 1 - (base + l);
         int cls = -1;
-        if (u >= own_lo && u < own_hi && u < n) cls = tri_class(dplus[u]);
+        if (u >= own_lo && u < own_hi && u < n) cls = tri_class(dplus[u], wmax, cmax);
         cls = cls > 0 ? 1 : cls;  // 0: warp queue, 1: CTA queue
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -89,6 +104,17 @@ __device__ __forceinline__ int hash_get(const int32_t* hk, const V* hv, int bits
         if (k == kNoKey) return -1;
         h = (h + 1) & mask;
     }
+}
+
+// Index of y in the sorted list L[0, d) (shared memory), or -1.
+__device__ __forceinline__ int find_sorted(const int32_t* L, int d, int32_t y) {
+    int lo = 0, hi = d;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (L[mid] < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < d && L[lo] == y) ? lo : -1;
 }
 
 // First position p in [lo, hi) with a[p] >= t, found by the whole warp (32-ary search).
@@ -138,15 +164,21 @@ __device__ __forceinline__ void probe_list(const int32_t* __restrict__ colsp, in
     }
 }
 
-// single-graph mode: one block reduction and one atomic per statistic at the end of the kernel
-__device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint64_t k4, uint64_t paw, uint64_t* red) {
+// single-graph mode: one block reduction and one atomic per statistic at the end of the kernel;
+// the signature hits go to acc[ACC_SIG_HITS] in both modes
+__device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint64_t k4, uint64_t paw, uint64_t hits,
+                                            uint64_t* red) {
     tri = block_sum_u64(tri, red);
     k4 = block_sum_u64(k4, red);
     paw = block_sum_u64(paw, red);
-    if (threadIdx.x == 0 && !sink.batch()) {
-        if (tri) atomicAdd((unsigned long long*)&sink.acc[ACC_T], (unsigned long long)tri);
-        if (k4) atomicAdd((unsigned long long*)&sink.acc[ACC_K4], (unsigned long long)k4);
-        if (paw) atomicAdd((unsigned long long*)&sink.acc[ACC_PAWSUM], (unsigned long long)paw);
+    hits = block_sum_u64(hits, red);
+    if (threadIdx.x == 0) {
+        if (hits) atomicAdd((unsigned long long*)&sink.acc[ACC_SIG_HITS], (unsigned long long)hits);
+        if (!sink.batch()) {
+            if (tri) atomicAdd((unsigned long long*)&sink.acc[ACC_T], (unsigned long long)tri);
+            if (k4) atomicAdd((unsigned long long*)&sink.acc[ACC_K4], (unsigned long long)k4);
+            if (paw) atomicAdd((unsigned long long*)&sink.acc[ACC_PAWSUM], (unsigned long long)paw);
+        }
     }
 }
 
@@ -157,12 +189,13 @@ constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
 constexpr int kWarpHashBits = 7;  // 128 slots for <= 32 keys: load <= 1/4, ~1.4 slot reads per miss
 
+template <bool BS>
 __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __restrict__ offp,
                                                            const int32_t* __restrict__ colsp,
                                                            const int32_t* __restrict__ deg,
                                                            const int32_t* __restrict__ q,
                                                            const unsigned long long* __restrict__ cnt,
-                                                           uint32_t* __restrict__ te, Sink sink) {
+                                                           bool reuse, uint32_t* __restrict__ te, Sink sink) {
     __shared__ int32_t sL[kWarpsPerBlock][32];
     __shared__ uint32_t sRow[kWarpsPerBlock][32];
     __shared__ int32_t sHk[kWarpsPerBlock][1 << kWarpHashBits];
@@ -170,7 +203,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
     __shared__ uint64_t red[32];
     const int w = threadIdx.x >> 5, l = lane_id();
     const int64_t nq = (int64_t)cnt[0];
-    uint64_t tri = 0, k4 = 0, paw = 0;
+    uint64_t tri = 0, k4 = 0, paw = 0, hits = 0;
     for (int64_t k = ((int64_t)blockIdx.x * kWarpsPerBlock + w); k < nq; k += (int64_t)gridDim.x * kWarpsPerBlock) {
         const int32_t u = q[k];
         const int64_t ub = offp[u];
@@ -181,9 +214,12 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
 #pragma unroll
         for (int hs = 0; hs < (1 << kWarpHashBits); hs += 32) sHk[w][l + hs] = kNoKey;
         __syncwarp();
-        if (l < d) hash_put(sHk[w], sHv[w], kWarpHashBits, x, l);
+        if (!BS && l < d) hash_put(sHk[w], sHv[w], kWarpHashBits, x, l);
         __syncwarp();
         const int32_t last = sL[w][d - 1];
+        auto lookup = [&](int32_t y) {
+            return BS ? find_sorted(sL[w], d, y) : hash_get(sHk[w], sHv[w], kWarpHashBits, y);
+        };
         uint32_t col = 0;  // # rows with bit l
         for (int i = 0; i < d - 1; ++i) {
             const int32_t v = sL[w][i];
@@ -194,7 +230,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
             uint32_t row = 0;
             auto probe = [&](int32_t y, int64_t p) {
                 if (y >= next && y <= last) {
-                    const int j = hash_get(sHk[w], sHv[w], kWarpHashBits, y);
+                    const int j = lookup(y);
                     if (j >= 0) {
                         atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
                         row |= 1u << j;
@@ -213,10 +249,25 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         const uint64_t a_tri = (uint64_t)__popc(myrow);
         uint64_t a_k4 = 0;
         uint32_t bits = myrow;
-        while (bits) {
-            const int j = __ffs(bits) - 1;
-            bits &= bits - 1;
-            a_k4 += (uint64_t)__popc(myrow & sRow[w][j]);
+        if (reuse) {
+            while (bits) {  // the staged frontier of (u, L[j]) answers the extension
+                const int j = __ffs(bits) - 1;
+                bits &= bits - 1;
+                a_k4 += (uint64_t)__popc(myrow & sRow[w][j]);
+            }
+            hits += a_tri;
+        } else {
+            while (bits) {  // recompute |N+(L[j]) n S_uv| from N+(L[j]) in global memory
+                const int j = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t wv = sL[w][j];
+                for (int64_t p = offp[wv], pe = offp[wv + 1]; p < pe; ++p) {
+                    const int32_t y = colsp[p];
+                    if (y > last) break;
+                    const int jj = lookup(y);
+                    if (jj >= 0 && ((myrow >> jj) & 1u)) ++a_k4;
+                }
+            }
         }
         const uint64_t dx = (l < d) ? (uint64_t)deg[x] : 0;
         const uint64_t a_paw = (uint64_t)own * dx + a_tri * (uint64_t)deg[u];
@@ -234,7 +285,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         }
         __syncwarp();
     }
-    flush_block(sink, tri, k4, paw, red);
+    flush_block(sink, tri, k4, paw, hits, red);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -253,11 +304,12 @@ struct CtaSmem {
     uint64_t red[32];
 };
 
-template <int DMAX, int THREADS>
+template <int DMAX, int THREADS, bool BS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64_t* __restrict__ offp,
                                                      const int32_t* __restrict__ colsp,
                                                      const int32_t* __restrict__ deg,
                                                      const int32_t* __restrict__ q, int64_t n, int cls,
+                                                     int wmax, int cmax, bool reuse,
                                                      const unsigned long long* __restrict__ cnt,
                                                      unsigned long long* __restrict__ ticket,
                                                      uint32_t* __restrict__ te, Sink sink) {
@@ -268,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
     constexpr int NW = THREADS / 32;
     const int w = threadIdx.x >> 5, l = lane_id();
     const int64_t nq = (int64_t)cnt[1];
-    uint64_t tri = 0, k4 = 0, paw = 0;
+    uint64_t tri = 0, k4 = 0, paw = 0, hits = 0;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ticket, 1ull);
         __syncthreads();
@@ -278,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
         const int32_t u = q[n - 1 - k];
         const int64_t ub = offp[u];
         const int d = (int)(offp[u + 1] - ub);
-        if (tri_class(d) != cls) continue;
+        if (tri_class(d, wmax, cmax) != cls) continue;
         const int W = (d + 31) >> 5;
         const int WS = W | 1;
         for (int i = threadIdx.x; i < d; i += THREADS) {
@@ -288,9 +340,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
         for (int i = threadIdx.x; i < d * WS; i += THREADS) s.R[i] = 0;
         for (int i = threadIdx.x; i < (1 << S::HB); i += THREADS) s.hk[i] = kNoKey;
         __syncthreads();
-        for (int i = threadIdx.x; i < d; i += THREADS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
+        if (!BS)
+            for (int i = threadIdx.x; i < d; i += THREADS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
         __syncthreads();
         const int32_t last = s.L[d - 1];
+        auto lookup = [&](int32_t y) { return BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y); };
         // rows: warp per row, ordered intersection of N+(L[i]) with L
         for (int i = w; i < d - 1; i += NW) {
             const int32_t v = s.L[i];
@@ -301,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
             uint32_t hits = 0;
             auto probe = [&](int32_t y, int64_t p) {
                 if (y >= next && y <= last) {
-                    const int j = hash_get(s.hk, s.hv, S::HB, y);
+                    const int j = lookup(y);
                     if (j >= 0) {
                         atomicAdd(&te[p], 1u);
                         atomicOr(&s.R[i * WS + (j >> 5)], 1u << (j & 31));
@@ -343,9 +397,19 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
                 const int rank = k - __shfl_sync(kFull, pre, o);
                 if (k < B) {
                     const int j = (o << 5) + (int)__fns(word, 0, rank + 1);
-                    const uint32_t* Rj = &s.R[j * WS];
                     uint32_t cnt = 0;
-                    for (int x = o; x < W; ++x) cnt += __popc(Ri[x] & Rj[x]);
+                    if (reuse) {  // the staged frontier of (u, L[j])
+                        const uint32_t* Rj = &s.R[j * WS];
+                        for (int x = o; x < W; ++x) cnt += __popc(Ri[x] & Rj[x]);
+                    } else {      // recompute from N+(L[j]) in global memory
+                        const int32_t wv = s.L[j];
+                        for (int64_t p = offp[wv], pe = offp[wv + 1]; p < pe; ++p) {
+                            const int32_t y = colsp[p];
+                            if (y > last) break;
+                            const int jj = lookup(y);
+                            if (jj >= 0 && ((Ri[jj >> 5] >> (jj & 31)) & 1u)) ++cnt;
+                        }
+                    }
                     a_k4 += cnt;
                 }
             }
@@ -359,6 +423,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
         }
         // the anchor's own degree term: T_u * d_u
         a_paw += a_tri * (uint64_t)deg[u];
+        if (reuse) hits += a_tri;
         __syncthreads();
         if (sink.batch()) {
             const uint64_t t1 = block_sum_u64(a_tri, s.red);
@@ -375,7 +440,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
             paw += a_paw;
         }
     }
-    flush_block(sink, tri, k4, paw, s.red);
+    flush_block(sink, tri, k4, paw, hits, s.red);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -394,7 +459,7 @@ __device__ __forceinline__ int64_t lb_global(const int32_t* __restrict__ a, int6
 __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict__ offp,
                                                       const int32_t* __restrict__ colsp,
                                                       const int32_t* __restrict__ deg,
-                                                      const int32_t* __restrict__ q, int64_t n,
+                                                      const int32_t* __restrict__ q, int64_t n, int wmax, int cmax,
                                                       const unsigned long long* __restrict__ cnt,
                                                       int32_t* __restrict__ scratch, int64_t scratch_per_warp,
                                                       uint32_t* __restrict__ te, Sink sink) {
@@ -407,7 +472,7 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
     for (int64_t k = blockIdx.x; k < nq; k += gridDim.x) {
         const int32_t u = q[n - 1 - k];
         const int64_t ub = offp[u], ue = offp[u + 1];
-        if (tri_class((int)(ue - ub)) != 4) continue;
+        if (tri_class((int)(ue - ub), wmax, cmax) != 4) continue;
         const uint64_t du = (uint64_t)deg[u];
         const uint64_t tri0 = tri, k40 = k4, paw0 = paw;
         for (int64_t a = ub + w; a < ue; a += nw) {  // warp per out-arc (u, v)
@@ -465,19 +530,35 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
             paw = paw0;
         }
     }
-    flush_block(sink, tri, k4, paw, red);
+    flush_block(sink, tri, k4, paw, 0, red);
 }
 
-template <int DMAX, int THREADS>
-harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slot, int blocks_per_sm,
-                       cudaStream_t s) {
+template <int DMAX, int THREADS, bool BS>
+harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slot, int blocks_per_sm, int wmax,
+                       int cmax, bool reuse, cudaStream_t s) {
     const size_t smem = sizeof(CtaSmem<DMAX>);
-    HARP_CK(cudaFuncSetAttribute(k_tri_cta<DMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HARP_CK(cudaFuncSetAttribute(k_tri_cta<DMAX, THREADS, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    k_tri_cta<DMAX, THREADS><<<152 * blocks_per_sm, THREADS, smem, s>>>(
-        ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, (const unsigned long long*)&ws.acc[Q_TRI_WARP],
-        (unsigned long long*)&ws.acc[ticket_slot], ws.te, Sink{ws.acc, ws.gid, ws.accG});
+    k_tri_cta<DMAX, THREADS, BS><<<152 * blocks_per_sm, THREADS, smem, s>>>(
+        ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, wmax, cmax, reuse,
+        (const unsigned long long*)&ws.acc[Q_TRI_WARP], (unsigned long long*)&ws.acc[ticket_slot], ws.te,
+        Sink{ws.acc, ws.gid, ws.accG});
     HARP_LAUNCHED();
+    return HARP_OK;
+}
+
+template <bool BS>
+harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, bool reuse, cudaStream_t s) {
+    const Sink sink{ws.acc, ws.gid, ws.accG};
+    k_tri_warp<BS><<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri,
+                                                   (const unsigned long long*)&ws.acc[Q_TRI_WARP], reuse, ws.te, sink);
+    HARP_LAUNCHED();
+    HARP_CK(prof_mark(s, SEG_TRI_WARP));
+    HARP_TRY((launch_cta<kCta1, 256, BS>(g, ws, 1, T_TRI_S, 4, wmax, cmax, reuse, s)));
+    HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
+    HARP_TRY((launch_cta<kCta2, 256, BS>(g, ws, 2, T_TRI_M, 4, wmax, cmax, reuse, s)));
+    HARP_TRY((launch_cta<kCtaMax, 512, BS>(g, ws, 3, T_TRI_L, 1, wmax, cmax, reuse, s)));
+    HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
     return HARP_OK;
 }
 
@@ -486,35 +567,31 @@ harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slo
 // acc[Q_TRI_WARP], acc[Q_TRI_CTA] hold the queue lengths, acc[T_TRI_*] the CTA tickets (all cleared
 // with the accumulators before the count).
 harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s) {
-    (void)plan;
     const int64_t n = g->n;
     if (n == 0 || g->m == 0) return HARP_OK;  // no marks: the segments read as zero
+    const int wmax = (int)plan.tri_warp_max;  // normalised: 1..32
+    const int cmax = (int)plan.tri_cta_max;   // normalised: 1..kCtaMax
+    const bool reuse = !(plan.flags & HARP_PLAN_NO_REUSE);
     unsigned long long* cnt = (unsigned long long*)&ws.acc[Q_TRI_WARP];
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, ws.q_tri, cnt);
+    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, wmax, cmax, ws.q_tri, cnt);
     HARP_LAUNCHED();
     const Sink sink{ws.acc, ws.gid, ws.accG};
-    k_tri_warp<<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, cnt, ws.te, sink);
-    HARP_LAUNCHED();
-    HARP_CK(prof_mark(s, SEG_TRI_WARP));
-    HARP_TRY((launch_cta<kCta1, 256>(g, ws, 1, T_TRI_S, 4, s)));
-    HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
-    HARP_TRY((launch_cta<kCta2, 256>(g, ws, 2, T_TRI_M, 4, s)));
-    HARP_TRY((launch_cta<kCtaMax, 512>(g, ws, 3, T_TRI_L, 1, s)));
-    HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
+    if (plan.tri_probe == HARP_PROBE_BSEARCH) HARP_TRY(launch_tiers<true>(g, ws, wmax, cmax, reuse, s));
+    else HARP_TRY(launch_tiers<false>(g, ws, wmax, cmax, reuse, s));
     // fallback: per-warp frontier buffers of the largest possible out-degree (bounded by sqrt(2m))
     int64_t dmax = 1;
     while (dmax * dmax < 2 * g->m) ++dmax;
     if (dmax > g->max_deg) dmax = g->max_deg;
-    if (dmax > kCtaMax) {
+    if (dmax > cmax) {
         const int fb_blocks = 152;
         const int64_t per_warp = dmax + 32;
         const size_t bytes = (size_t)fb_blocks * 8 * (size_t)per_warp * sizeof(int32_t);
         int32_t* scratch = nullptr;
         HARP_CK(cudaMallocAsync((void**)&scratch, bytes, s));
-        k_tri_fallback<<<fb_blocks, 256, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, n, cnt, scratch, per_warp,
-                                                 ws.te, sink);
+        k_tri_fallback<<<fb_blocks, 256, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, n, wmax, cmax, cnt, scratch,
+                                                 per_warp, ws.te, sink);
         note_launch();
         cudaError_t e = cudaGetLastError();
         cudaFreeAsync(scratch, s);

@@ -22,7 +22,7 @@ HARP_PTR_HOST, HARP_PTR_DEVICE = 0, 1
 HARP_ABI_VERSION = 1
 HARP_BASIS_TRIANGLE_WEDGE = 0
 HARP_PROBE_HASH, HARP_PROBE_BSEARCH = 1, 2
-HARP_PLAN_NO_GRAPH = 1
+HARP_PLAN_NO_GRAPH, HARP_PLAN_NO_REUSE = 1, 2
 
 MOTIFS = ("star3", "path4", "paw", "cycle4", "diamond", "clique4")
 STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")
@@ -44,6 +44,7 @@ class harp_plan(ctypes.Structure):
         ("basis", ctypes.c_uint32),
         ("tri_probe", ctypes.c_uint32),
         ("tri_warp_max", ctypes.c_uint32),
+        ("tri_cta_max", ctypes.c_uint32),
         ("c4_warp_max_work", ctypes.c_uint32),
         ("c4_cta_max_work", ctypes.c_uint32),
         ("c4_window_bytes", ctypes.c_uint32),
@@ -121,6 +122,8 @@ def lib():
         L.harp_select_anchors.argtypes = [vp, ctypes.POINTER(harp_select_opts), ctypes.POINTER(harp_plan)]
         L.harp_count4.argtypes = [vp, ctypes.POINTER(harp_plan), pu64]
         L.harp_count4_stats.argtypes = [vp, ctypes.POINTER(harp_plan), pu64, pu64]
+        L.harp_reuse_stats.argtypes = [vp, pu64, pu64]
+        L.harp_reuse_stats.restype = i32
         L.harp_count4_async.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp]
         L.harp_count4_noalloc.argtypes = [i64, i64, vp, vp, vp, vp]
         L.harp_batch_create.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp)]
@@ -269,6 +272,13 @@ def harp_count4(g: Csr, plan: harp_plan | None = None) -> np.ndarray:
     _check(lib().harp_count4(g.handle, _plan_ref(plan), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
            "harp_count4")
     return out
+
+
+def harp_reuse_stats(g: Csr) -> tuple[int, int]:
+    """(lookups, hits) of the signature reuse in the last blocking count on g."""
+    lk, ht = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().harp_reuse_stats(g.handle, ctypes.byref(lk), ctypes.byref(ht)), "harp_reuse_stats")
+    return lk.value, ht.value
 
 
 def harp_count4_stats(g: Csr, plan: harp_plan | None = None) -> tuple[np.ndarray, np.ndarray]:
