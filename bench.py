@@ -11,6 +11,13 @@ host edge lists: harp_build_csr (H2D + device CSR build) + harp_count4 (D2H of t
 `roofline` = the dominant kernel's algorithmic bytes (host work meter) / its CUDA-event time, against
 the measured HBM copy bandwidth.  `cpu_baseline` = the CPU oracle on a bounded R-MAT sample.
 
+`batched`: the batched workload (4,096 graphs: ER / BA / RGG, n log-uniform in [50, 20000], mean degree
+in [4, 32], seeds 0..4095) counted as one captured CUDA graph under the autotuned plan, against the plain
+path (one harp_count4 per graph) over the same graphs; counts are compared graph by graph.
+`served`: a Poisson stream of requests (edge counts log-uniform in [1e3, 1e7], ER / BA / RGG / R-MAT)
+through the continuous-batching server, against plain one-graph-per-launch processing (build + count,
+in arrival order) of the same stream: p50 / p99 latency and edges/s.
+
 --impl reference runs the CPU oracle (plain non-induced counts + containment inversion) on the host
 cores instead: each step counts an R-MAT scale-17 sample of the same family.
 """
@@ -141,6 +148,117 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(harp, graphgen, np, torch, stream, flush, steps, warmup, G=4096):
+    """Batched vs plain on the 4,096-graph workload (both exact; counts compared per graph)."""
+    t0 = time.perf_counter()
+    gs = [graphgen.batch_graph(s) for s in range(G)]
+    t_gen = time.perf_counter() - t0
+    csrs = [harp.harp_build_csr(g.n, g.src, g.dst) for g in gs]
+    m_total = sum(c.info()["m"] for c in csrs)
+    b = harp.harp_batch_create(csrs)
+    best, tune_ms = harp.harp_batch_autotune(b, reps=2)
+    for _ in range(warmup):
+        counts_b = harp.harp_batch_count(b, best, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        counts_b = harp.harp_batch_count(b, best, stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_b = sum(a.elapsed_time(z) for a, z in ev) / steps
+    # plain: one graph per launch sequence, same graphs and plan, one untimed pass then one timed pass
+    for c in csrs:
+        harp.harp_count4(c, best)
+    flush.fill_(1)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plain = [harp.harp_count4(c, best) for c in csrs]
+    z.record(stream)
+    torch.cuda.synchronize()
+    t_p = a.elapsed_time(z)
+    assert all(np.array_equal(p, q) for p, q in zip(plain, counts_b)), "batched counts differ from plain"
+    info = harp.harp_batch_info(b)
+    b.close()
+    for c in csrs:
+        c.close()
+    return {"workload": f"{G} graphs, ER/BA/RGG uniform, n log-uniform [50, 20000], mean degree U[4, 32] "
+                        f"(BA m in 2..8), seeds 0..{G - 1}", "graphs": G, "n_total": info["n"], "m_total": m_total,
+            "value": m_total / (t_b / 1000), "unit": UNIT, "ms_per_step": t_b,
+            "plain_value": m_total / (t_p / 1000), "plain_ms_per_pass": t_p, "speedup_vs_plain": t_p / t_b,
+            "plan": {"tri_warp_max": best.tri_warp_max, "tri_probe": best.tri_probe,
+                     "c4_warp_max_work": best.c4_warp_max_work},
+            "autotune_ms": tune_ms, "generate_s": t_gen, "counts_equal": True}
+
+
+def bench_served(harp, graphgen, np, rate=200.0, nreq=128, seed=11, budget=64 << 30):
+    """Poisson stream through the server vs plain one-graph-per-launch processing of the same stream."""
+    import threading
+    gs = [graphgen.serve_graph(seed * 100000 + i) for i in range(nreq)]
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    alone = [None] * nreq
+    m_of = [0] * nreq
+
+    def plain_pass():
+        lat = []
+        t0 = time.perf_counter()
+        for i, g in enumerate(gs):
+            now = time.perf_counter() - t0
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            c = harp.harp_build_csr(g.n, g.src, g.dst)
+            alone[i] = harp.harp_count4(c)
+            m_of[i] = c.info()["m"]
+            c.close()
+            lat.append(time.perf_counter() - t0 - arrivals[i])
+        return lat, time.perf_counter() - t0
+
+    plain_pass()  # untimed: first-touch of every size class
+    lat_p, span_p = plain_pass()
+    srv = harp.Server(hbm_budget_bytes=budget)
+    tickets = [None] * nreq
+    done_at = [0.0] * nreq
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, g in enumerate(gs):
+            now = time.perf_counter() - t0
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            tickets[i] = srv.submit(g.n, g.src, g.dst)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    results = [None] * nreq
+    pending = set(range(nreq))
+    while pending:
+        for i in list(pending):
+            if tickets[i] is None:
+                continue
+            r = srv.poll(tickets[i])
+            if r is not None:
+                results[i] = r
+                done_at[i] = time.perf_counter() - t0
+                pending.discard(i)
+        time.sleep(0.0002)
+    th.join()
+    span_s = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    assert all(np.array_equal(r, a) for r, a in zip(results, alone)), "served counts differ from plain"
+    lat_s = [done_at[i] - arrivals[i] for i in range(nreq)]
+    m_total = sum(m_of)
+    pct = lambda v, q: float(np.percentile(np.asarray(v) * 1000.0, q))
+    return {"workload": f"{nreq} requests, Poisson arrivals at {rate:g}/s, edge counts log-uniform [1e3, 1e7], "
+                        f"ER/BA/RGG/R-MAT uniform, HBM budget {budget >> 30} GiB", "requests": nreq,
+            "edges": m_total, "value": m_total / span_s, "unit": UNIT,
+            "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
+            "plain_value": m_total / span_p, "plain_p50_ms": pct(lat_p, 50), "plain_p99_ms": pct(lat_p, 99),
+            "batches": st["batches"], "max_batch": st["max_batch"], "partitioned": st["partitioned"],
+            "peak_resident_bytes": st["peak_resident_bytes"], "counts_equal": True}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -150,6 +268,8 @@ def main():
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of the workload (20 = the bench config)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-meter", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -233,6 +353,11 @@ def main():
         assert np.array_equal(c2, counts)
     t_e2e = sum(e2e_ms) / len(e2e_ms)
 
+    # the batched and served measurements are single-GPU workloads: skipped for replicas (N > 1)
+    batched = None if (args.no_batched or world > 1) else bench_batched(harp, graphgen, np, torch, stream, flush,
+                                                                        args.steps, args.warmup)
+    served = None if (args.no_served or world > 1) else bench_served(harp, graphgen, np)
+
     if rank != 0:
         return 0
     peak, peak_kind = load_peaks()
@@ -275,6 +400,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "segments_ms": seg_avg,
+        "batched": batched,
+        "served": served,
         "counts": [int(x) for x in counts],
         "hbm_pct_alg": (100.0 * sum(meter[k]["bytes"] for k in SEGMENTS) / (t_step / 1000) / 1e9 / peak)
         if meter else None,

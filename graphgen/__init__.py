@@ -200,3 +200,44 @@ def batch_graph(seed: int, n_lo: int = 50, n_hi: int = 20000) -> Graph:
     if s.kind == "ba":
         return ba(s.n, min(s.m, max(1, s.n - 1)), 1000003 * seed + 17)
     return rgg(s.n, s.k, 1000003 * seed + 17)
+
+
+@dataclass
+class ServeSpec:
+    seed: int
+    kind: str       # "er" | "ba" | "rgg" | "rmat"
+    m: int          # target edge count
+    n: int
+    k: float        # mean degree (er, rgg)
+    attach: int     # edges per new vertex (ba)
+    scale: int      # R-MAT scale (edge factor 16)
+
+
+def serve_spec(seed: int, m_lo: float = 1e3, m_hi: float = 1e7) -> ServeSpec:
+    """Served request ``seed``: target edge count log-uniform in [m_lo, m_hi]; generator uniform over
+    {ER, BA, RGG, R-MAT (0.57, 0.19, 0.19)}; mean degree uniform in [4, 32] (ER, RGG), BA attaches
+    m uniform in {2..8}, R-MAT uses edge factor 16 and the scale nearest the target."""
+    draw = [splitmix64_at(seed, 77, i) for i in range(4)]
+    kind = ("er", "ba", "rgg", "rmat")[draw[0] % 4]
+    u = (draw[1] >> 11) * (1.0 / 9007199254740992.0)
+    m = int(round(math.exp(math.log(m_lo) + u * (math.log(m_hi) - math.log(m_lo)))))
+    k = 4.0 + 28.0 * ((draw[2] >> 11) * (1.0 / 9007199254740992.0))
+    attach = 2 + int(draw[3] % 7)
+    if kind == "ba":
+        n = max(attach + 2, m // attach)
+    else:
+        n = max(8, int(round(2 * m / k)))
+    scale = max(4, int(round(math.log2(max(m, 16) / 16))))
+    return ServeSpec(seed, kind, m, n, k, attach, scale)
+
+
+def serve_graph(seed: int, m_lo: float = 1e3, m_hi: float = 1e7) -> Graph:
+    s = serve_spec(seed, m_lo, m_hi)
+    gseed = 7919 * seed + 3
+    if s.kind == "er":
+        return er(s.n, s.k, gseed)
+    if s.kind == "ba":
+        return ba(s.n, s.attach, gseed)
+    if s.kind == "rgg":
+        return rgg(s.n, s.k, gseed)
+    return rmat(s.scale, 16, 0.57, 0.19, 0.19, seed=gseed)

@@ -87,7 +87,8 @@ typedef struct harp_csr harp_csr;
 harp_status harp_build_csr(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
                            uint32_t flags, void* stream, harp_csr** out);
 
-/* Release a handle and all device memory it owns (stream-ordered on the handle's stream).
+/* Release a handle and all device memory it owns (stream-ordered on the handle's stream; returns
+ * without waiting for the frees).
  * NULL is accepted and ignored. */
 void harp_csr_free(harp_csr* g);
 
@@ -209,6 +210,16 @@ harp_status harp_batch_info(const harp_batch* b, int64_t* graphs, int64_t* n_tot
                             size_t* device_bytes);
 
 void harp_batch_free(harp_batch* b);
+
+/* Autotuner for a batch: counts the batch `reps` times under each candidate plan (each captured as
+ * its own CUDA graph, one untimed replay first), timed with CUDA events on the batch's stream, and
+ * writes the fastest plan to *best and candidate k's mean milliseconds to ms_out[k] (may be NULL).
+ * candidates NULL: the built-in grid of HARP_AUTOTUNE_GRID plans (tri_warp_max {16, 32} x tri_probe
+ * {hash, bsearch} x c4_warp_max_work {256, 512}); otherwise ncand >= 1 plans.  Every candidate
+ * must give identical counts and statistics: a mismatch returns HARP_EDEVICE. */
+#define HARP_AUTOTUNE_GRID 8
+harp_status harp_batch_autotune(harp_batch* b, const harp_plan* candidates, int32_t ncand, int32_t reps,
+                                harp_plan* best, float* ms_out);
 
 /* One-shot convenience: create, count once (kernels launched directly), free. */
 harp_status harp_count4_batch(const harp_csr* const* graphs, int64_t G, const harp_plan* plan,

@@ -246,10 +246,11 @@ void harp_csr_free(harp_csr* g) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
+    // stream-ordered frees: they run after the work already queued on the handle's stream, and the
+    // caller is not blocked (a server frees handles while other streams keep working)
     ws_release(g->ws, g->stream);
     if (g->off) cudaFreeAsync(g->off, g->stream);
     if (g->cols) cudaFreeAsync(g->cols, g->stream);
-    cudaStreamSynchronize(g->stream);
     cudaSetDevice(prev);
     delete g;
 }

@@ -6,6 +6,8 @@
 // orientation, anchors, reductions, per-graph closure, and the copy of the counts to pinned host
 // memory - is captured once into a CUDA graph and replayed on every count.
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -18,25 +20,73 @@ struct MemberDesc {
     const int64_t* off;
     const int32_t* cols;
     int64_t n;
-    int64_t vbase;  // first union vertex of this member
-    int64_t abase;  // first union arc of this member
+    int64_t vbase;   // first union vertex of this member
+    int64_t abase;   // first union arc of this member
+    int64_t bstart;  // first union-build block of this member
 };
 
-// one block per member (grid-stride over members): shifted offsets, graph ids, shifted columns
+// Union-build blocks per member: one per kUnionChunk vertices or arcs, whichever needs more.
+constexpr int64_t kUnionChunk = 16384;
+
+int64_t union_blocks(int64_t n, int64_t arcs) {
+    const int64_t x = n > arcs ? n : arcs;
+    const int64_t b = (x + kUnionChunk - 1) / kUnionChunk;
+    return b < 1 ? 1 : b;
+}
+
+// Block b copies chunk (b - bstart) of its member (found by binary search over bstart): shifted
+// offsets and graph ids for that chunk of vertices, shifted columns for that chunk of arcs.
 __global__ void __launch_bounds__(256) k_union_build(const MemberDesc* __restrict__ desc, int64_t G,
                                                      int64_t* __restrict__ off_u, int32_t* __restrict__ cols_u,
                                                      int32_t* __restrict__ gid_u, int64_t N, int64_t A) {
-    for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
-        const MemberDesc d = desc[g];
-        for (int64_t v = threadIdx.x; v < d.n; v += blockDim.x) {
-            off_u[d.vbase + v] = d.abase + d.off[v];
-            gid_u[d.vbase + v] = (int32_t)g;
-        }
-        const int64_t arcs = d.n > 0 ? d.off[d.n] : 0;
-        for (int64_t a = threadIdx.x; a < arcs; a += blockDim.x)
-            cols_u[d.abase + a] = (int32_t)(d.vbase + d.cols[a]);
+    int64_t lo = 0, hi = G;  // member: last g with desc[g].bstart <= blockIdx.x
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (desc[mid].bstart <= (int64_t)blockIdx.x) lo = mid;
+        else hi = mid;
     }
+    const int64_t g = lo;
+    const MemberDesc d = desc[g];
+    const int64_t c0 = ((int64_t)blockIdx.x - d.bstart) * kUnionChunk;
+    const int64_t vend = c0 + kUnionChunk < d.n ? c0 + kUnionChunk : d.n;
+    for (int64_t v = c0 + threadIdx.x; v < vend; v += blockDim.x) {
+        off_u[d.vbase + v] = d.abase + d.off[v];
+        gid_u[d.vbase + v] = (int32_t)g;
+    }
+    const int64_t arcs = d.n > 0 ? d.off[d.n] : 0;
+    const int64_t aend = c0 + kUnionChunk < arcs ? c0 + kUnionChunk : arcs;
+    for (int64_t a = c0 + threadIdx.x; a < aend; a += blockDim.x) cols_u[d.abase + a] = (int32_t)(d.vbase + d.cols[a]);
     if (blockIdx.x == 0 && threadIdx.x == 0) off_u[N] = A;
+}
+
+// Pinned host buffers for the batch outputs, kept for reuse: allocating and freeing page-locked
+// memory synchronises the whole device, which would stall unrelated streams (a server building the
+// next requests while a batch counts).
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+
+cudaError_t pinned_get(size_t bytes, void** out) {
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        auto it = g_pinned_free.lower_bound(bytes);
+        if (it != g_pinned_free.end() && it->first <= 4 * bytes + 4096) {
+            *out = it->second;
+            g_pinned_free.erase(it);
+            return cudaSuccess;
+        }
+    }
+    return cudaMallocHost(out, bytes);
+}
+
+void pinned_put(size_t bytes, void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (g_pinned_free.size() >= 64) {  // bound the cache: drop the smallest entry
+        auto it = g_pinned_free.begin();
+        cudaFreeHost(it->second);
+        g_pinned_free.erase(it);
+    }
+    g_pinned_free.emplace(bytes, p);
 }
 
 }  // namespace
@@ -58,6 +108,7 @@ struct harp_batch {
     int64_t* d_ginfo = nullptr;       // [G * kGInfo]
     uint64_t* d_out = nullptr;        // [G * 16]
     uint64_t* h_out = nullptr;        // pinned [G * 16 + 1]; the last word is the device self-check flag
+    size_t h_out_bytes = 0;           // capacity of h_out (from the pinned-buffer cache)
     cudaGraphExec_t exec = nullptr;
     harp_plan plan_captured{};
     int64_t launches_per_count = 0;
@@ -84,7 +135,7 @@ harp_status batch_release(harp_batch* b) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
-    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->h_out) pinned_put(b->h_out_bytes, b->h_out);
     delete b;
     return HARP_OK;
 }
@@ -136,14 +187,15 @@ harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_bat
     cudaStream_t s = b->capture_stream;
     std::vector<MemberDesc> desc((size_t)G);
     std::vector<int64_t> gbase((size_t)G + 1);
-    int64_t vb = 0, ab = 0;
+    int64_t vb = 0, ab = 0, blocks = 0;
     for (int64_t g = 0; g < G; ++g) {
         const harp_csr* c = graphs[g];
-        desc[(size_t)g] = MemberDesc{c->off, c->cols, c->n, vb, ab};
+        desc[(size_t)g] = MemberDesc{c->off, c->cols, c->n, vb, ab, blocks};
         gbase[(size_t)g] = vb;
         b->m_of[(size_t)g] = c->m;
         vb += c->n;
         ab += 2 * c->m;
+        blocks += union_blocks(c->n, 2 * c->m);
     }
     gbase[(size_t)G] = vb;
     const size_t gg = (size_t)(G > 0 ? G : 1);
@@ -163,12 +215,15 @@ harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_bat
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->d_ginfo, sizeof(int64_t) * kGInfo * gg, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_gbase, gbase.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_out, sizeof(uint64_t) * (16 * gg + 1));
+    if (e == cudaSuccess) {
+        b->h_out_bytes = sizeof(uint64_t) * (16 * gg + 1);
+        e = pinned_get(b->h_out_bytes, (void**)&b->h_out);
+    }
     if (e == cudaSuccess && G > 0)
         e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(MemberDesc) * (size_t)G, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        int64_t blocks = G < 152 * 16 ? G : 152 * 16;
-        if (blocks < 1) blocks = 1;
+    if (e == cudaSuccess && blocks > 2147483647LL) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && G == 0) e = cudaMemsetAsync(b->u.off, 0, sizeof(int64_t), s);  // off[0] = 0
+    if (e == cudaSuccess && G > 0) {
         k_union_build<<<(unsigned)blocks, 256, 0, s>>>(b->d_desc, G, b->u.off, b->u.cols, b->d_gid_in, N, 2 * M);
         note_launch();
         e = cudaGetLastError();
@@ -184,14 +239,13 @@ harp_status harp_batch_create(const harp_csr* const* graphs, int64_t G, harp_bat
     return HARP_OK;
 }
 
-harp_status harp_batch_count(harp_batch* b, const harp_plan* user_plan, uint64_t (*counts_out)[6],
-                             uint64_t (*stats_out)[8], void* stream) {
-    if (!b || (!counts_out && b->G > 0)) return HARP_EINVAL;
-    if (user_plan && user_plan->basis != HARP_BASIS_TRIANGLE_WEDGE) return HARP_EINVAL;
-    HARP_CK(cudaSetDevice(b->device));
-    cudaStream_t s = (cudaStream_t)stream;
-    harp_plan plan;
-    normalise_plan(user_plan, &plan);
+}  // extern "C"
+
+namespace {
+
+// Prepare b for counting under `plan`: workspace, batch pointers, and (unless the plan asks for
+// direct launches) the CUDA graph of the whole sequence, captured again only when the plan changes.
+harp_status batch_prepare(harp_batch* b, const harp_plan& plan) {
     HARP_TRY(ws_ensure(b->u.ws, b->u.n, b->u.m, b->capture_stream));
     b->u.ws.gid_in = b->d_gid_in;
     b->u.ws.gid = b->d_gid;
@@ -229,6 +283,23 @@ harp_status harp_batch_count(harp_batch* b, const harp_plan* user_plan, uint64_t
         b->launches_per_count = harp_launch_count() - l0;
         b->plan_captured = plan;
     }
+    return HARP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+harp_status harp_batch_count(harp_batch* b, const harp_plan* user_plan, uint64_t (*counts_out)[6],
+                             uint64_t (*stats_out)[8], void* stream) {
+    if (!b || (!counts_out && b->G > 0)) return HARP_EINVAL;
+    if (user_plan && user_plan->basis != HARP_BASIS_TRIANGLE_WEDGE) return HARP_EINVAL;
+    HARP_CK(cudaSetDevice(b->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    harp_plan plan;
+    normalise_plan(user_plan, &plan);
+    HARP_TRY(batch_prepare(b, plan));
+    const bool use_graph = !(plan.flags & HARP_PLAN_NO_GRAPH);
     if (use_graph) {
         HARP_CK(cudaGraphLaunch(b->exec, s));
         note_launch(b->launches_per_count);
@@ -251,6 +322,82 @@ harp_status harp_batch_count(harp_batch* b, const harp_plan* user_plan, uint64_t
 }
 
 void harp_batch_free(harp_batch* b) { batch_release(b); }
+
+harp_status harp_batch_autotune(harp_batch* b, const harp_plan* candidates, int32_t ncand, int32_t reps,
+                                harp_plan* best, float* ms_out) {
+    if (!b || !best || reps < 1) return HARP_EINVAL;
+    if (candidates && ncand < 1) return HARP_EINVAL;
+    HARP_CK(cudaSetDevice(b->device));
+    std::vector<harp_plan> cand;
+    if (candidates) {
+        for (int32_t k = 0; k < ncand; ++k) {
+            if (candidates[k].basis != HARP_BASIS_TRIANGLE_WEDGE) return HARP_EINVAL;
+            harp_plan p;
+            normalise_plan(&candidates[k], &p);
+            p.flags &= ~HARP_PLAN_NO_GRAPH;  // candidates are timed as captured graphs
+            cand.push_back(p);
+        }
+    } else {  // the built-in grid: warp/CTA split x membership probe x wedge warp/CTA split
+        for (uint32_t wm : {16u, 32u})
+            for (uint32_t pr : {(uint32_t)HARP_PROBE_HASH, (uint32_t)HARP_PROBE_BSEARCH})
+                for (uint32_t cw : {256u, 512u}) {
+                    harp_plan p;
+                    normalise_plan(nullptr, &p);
+                    p.tri_warp_max = wm;
+                    p.tri_probe = pr;
+                    p.c4_warp_max_work = cw;
+                    cand.push_back(p);
+                }
+    }
+    cudaStream_t s = b->capture_stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HARP_CK(cudaEventCreate(&e0));
+    HARP_CK(cudaEventCreate(&e1));
+    std::vector<uint64_t> first;
+    harp_status st = HARP_OK;
+    float best_ms = 0.0f;
+    size_t best_k = 0;
+    for (size_t k = 0; k < cand.size() && st == HARP_OK; ++k) {
+        st = batch_prepare(b, cand[k]);
+        if (st != HARP_OK) break;
+        // one untimed replay (first touch of the captured graph), then reps timed replays
+        cudaError_t e = cudaGraphLaunch(b->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int32_t r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            record_cuda_error(e);
+            st = HARP_ECUDA;
+            break;
+        }
+        note_launch(b->launches_per_count * (reps + 1));
+        if (b->h_out[16 * b->G]) {
+            st = HARP_EDEVICE;
+            break;
+        }
+        // every candidate must produce the same counts and statistics (a plan changes only the work)
+        std::vector<uint64_t> now(b->h_out, b->h_out + 16 * b->G);
+        if (first.empty()) first = now;
+        else if (now != first) {
+            st = HARP_EDEVICE;
+            break;
+        }
+        ms /= (float)reps;
+        if (ms_out) ms_out[k] = ms;
+        if (k == 0 || ms < best_ms) {
+            best_ms = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HARP_OK) return st;
+    *best = cand[best_k];
+    return HARP_OK;
+}
 
 harp_status harp_batch_info(const harp_batch* b, int64_t* graphs, int64_t* n_total, int64_t* m_total,
                             size_t* device_bytes) {

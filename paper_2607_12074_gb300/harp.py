@@ -132,7 +132,10 @@ def lib():
         L.harp_batch_free.argtypes = [vp]
         L.harp_batch_free.restype = None
         L.harp_count4_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(harp_plan), vp, vp]
-        for name in ("harp_batch_create", "harp_batch_count", "harp_batch_info", "harp_count4_batch"):
+        L.harp_batch_autotune.argtypes = [vp, ctypes.POINTER(harp_plan), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(harp_plan), ctypes.POINTER(ctypes.c_float)]
+        for name in ("harp_batch_create", "harp_batch_count", "harp_batch_info", "harp_count4_batch",
+                     "harp_batch_autotune"):
             getattr(L, name).restype = i32
         L.harp_count4_partitioned.argtypes = [i64, i64, vp, vp, ctypes.c_uint64, ctypes.c_int32, pu64,
                                               ctypes.POINTER(harp_partition_stats)]
@@ -346,6 +349,23 @@ def harp_batch_info(b: Batch) -> dict:
     _check(lib().harp_batch_info(b.handle, ctypes.byref(g), ctypes.byref(n), ctypes.byref(m), ctypes.byref(by)),
            "harp_batch_info")
     return {"graphs": g.value, "n": n.value, "m": m.value, "device_bytes": by.value}
+
+
+HARP_AUTOTUNE_GRID = 8
+
+
+def harp_batch_autotune(b: Batch, candidates=None, reps: int = 3):
+    """Time each candidate plan (default: the built-in grid) on the batch; returns (best plan, ms list)."""
+    if candidates:
+        arr = (harp_plan * len(candidates))(*candidates)
+        nc = len(candidates)
+    else:
+        arr, nc = None, HARP_AUTOTUNE_GRID
+    ms = (ctypes.c_float * nc)()
+    best = harp_plan()
+    _check(lib().harp_batch_autotune(b.handle, arr, nc if candidates else 0, int(reps), ctypes.byref(best), ms),
+           "harp_batch_autotune")
+    return best, [float(x) for x in ms]
 
 
 def harp_count4_batch(graphs, plan: harp_plan | None = None, stream=None) -> np.ndarray:

@@ -96,3 +96,27 @@ def test_one_shot_batch_and_member_order(harp, handles):
     got = harp.harp_count4_batch([hs[i] for i in order])
     assert got.tolist() == alone[order].tolist()
     assert harp.harp_count4_batch([]).shape == (0, 6)
+
+
+def test_autotune_grid_and_custom_candidates(harp, handles):
+    hs, alone, _ = handles
+    b = harp.harp_batch_create(hs)
+    try:
+        base = harp.harp_batch_count(b)
+        assert base.tolist() == alone.tolist()
+        best, ms = harp.harp_batch_autotune(b, reps=1)
+        assert len(ms) == harp.HARP_AUTOTUNE_GRID and all(x > 0 for x in ms)
+        assert best.tri_warp_max in (16, 32) and best.c4_warp_max_work in (256, 512)
+        assert harp.harp_batch_count(b, best).tolist() == base.tolist()
+        cands = []
+        for wm, cta in ((4, 64), (32, 1024)):
+            p = harp.harp_plan()
+            p.version = harp.HARP_ABI_VERSION
+            p.tri_warp_max, p.tri_cta_max = wm, cta
+            cands.append(p)
+        best2, ms2 = harp.harp_batch_autotune(b, cands, reps=2)
+        assert len(ms2) == 2 and all(x > 0 for x in ms2)
+        assert (best2.tri_warp_max, best2.tri_cta_max) in ((4, 64), (32, 1024))
+        assert harp.harp_batch_count(b, best2).tolist() == base.tolist()
+    finally:
+        b.close()
