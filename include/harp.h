@@ -270,7 +270,9 @@ typedef struct harp_server_opts {
     uint32_t batch_window_us;    /* once a request is built, how long the executor may wait for  */
                                  /* requests still being admitted or built to join its batch    */
                                  /* (0 = launch at once with whatever is built)                 */
-    uint32_t reserved;           /* must be 0                                                    */
+    uint32_t staging_mib;        /* page-locked host staging for submitted edge lists, MiB       */
+                                 /* (0 = 512); a request that finds no room is kept in pageable */
+                                 /* memory instead (slower host-to-device copy)                  */
 } harp_server_opts;
 
 typedef struct harp_server_stats {
@@ -279,7 +281,8 @@ typedef struct harp_server_stats {
     uint64_t latency_p50_us, latency_p99_us;  /* submit -> done, over the last 65,536 requests    */
 } harp_server_stats;
 
-/* Start a server on the current device (two worker threads).  opts may be NULL. */
+/* Start a server on the current device (two builder threads with their own copy streams, one
+ * executor thread with a compute stream).  opts may be NULL. */
 harp_status harp_server_create(const harp_server_opts* opts, harp_server** out);
 
 /* Enqueue a request; src/dst are HOST int32[m_in] and are copied before the call returns. */

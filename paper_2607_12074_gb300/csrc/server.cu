@@ -1,8 +1,9 @@
 // Serving: continuous batching of motif-count requests on one GPU.
 //
-// Requests (host edge lists, copied at submit) wait in a FIFO.  A builder thread admits them in
-// order while the device memory held by admitted requests stays within the HBM budget and a slot is
-// free, copies each edge list to the device and builds its CSR on a copy stream.  An executor thread
+// Requests (host edge lists, copied at submit into a page-locked staging arena when it has room)
+// wait in a FIFO.  Two builder threads admit them in order while the device memory held by admitted
+// requests stays within the HBM budget and a slot is free, copy each edge list to the device and
+// build its CSR, each on its own copy stream.  An executor thread
 // takes every built request as the next batch and counts it with the batched pipeline (the disjoint
 // union of the batch, one launch per kernel) on a compute stream; with a batching window it first
 // waits, up to the window, while requests are still queued for admission or being built.  Requests that arrive while a batch
@@ -15,6 +16,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -29,10 +31,57 @@ using Clock = std::chrono::steady_clock;
 
 enum class ReqState { Pending, Built, Running, Done };
 
+// First-fit allocator over one page-locked host block (caller holds the server lock).
+struct StagingArena {
+    unsigned char* base = nullptr;
+    size_t bytes = 0;
+    std::map<size_t, size_t> free_;  // offset -> size, coalesced
+
+    void init(void* p, size_t n) {
+        base = static_cast<unsigned char*>(p);
+        bytes = n;
+        free_.clear();
+        if (n) free_[0] = n;
+    }
+    void* alloc(size_t n) {
+        n = (n + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            const size_t off = it->first, rest = it->second - n;
+            free_.erase(it);
+            if (rest) free_[off + n] = rest;
+            return base + off;
+        }
+        return nullptr;
+    }
+    void release(void* p, size_t n) {
+        if (!p) return;
+        n = (n + 255) & ~(size_t)255;
+        size_t off = static_cast<unsigned char*>(p) - base;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + n == next->first) {
+            n += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                off = prev->first;
+                n += prev->second;
+                free_.erase(prev);
+            }
+        }
+        free_[off] = n;
+    }
+};
+
 struct Request {
     uint64_t ticket = 0;
     int64_t n = 0, m_in = 0;
-    std::vector<int32_t> src, dst;
+    std::vector<int32_t> src, dst;    // pageable copy (when the staging arena had no room)
+    int32_t* staged = nullptr;        // [2 * m_in] in the staging arena: src then dst
+    const int32_t* hsrc = nullptr;    // the edge list the builder reads
+    const int32_t* hdst = nullptr;
     ReqState state = ReqState::Pending;
     harp_status status = HARP_OK;
     uint64_t counts[6] = {0, 0, 0, 0, 0, 0};
@@ -73,8 +122,11 @@ struct harp_server {
     int64_t inflight = 0;
     int64_t building = 0;               // requests between admission and a built CSR
     bool stop = false;
-    cudaStream_t copy_stream = nullptr, compute_stream = nullptr;
-    std::thread builder, executor;
+    static constexpr int kBuilders = 2;
+    cudaStream_t copy_stream[kBuilders] = {nullptr, nullptr};
+    cudaStream_t compute_stream = nullptr;
+    std::thread builder[kBuilders], executor;
+    StagingArena staging;
     // statistics
     uint64_t completed = 0, batches = 0, partitioned = 0, batched_requests = 0, max_batch_seen = 0;
     std::vector<double> latencies_ms;   // ring of the last kLatencyRing completions
@@ -107,8 +159,17 @@ bool can_admit(const harp_server* s) {
     return slot && (oversize ? s->resident == 0 : s->resident + r->need <= s->opts.hbm_budget_bytes);
 }
 
-void builder_loop(harp_server* s) {
+void drop_host_copy(harp_server* s, Request* r) {  // caller holds the lock
+    if (r->staged) s->staging.release(r->staged, sizeof(int32_t) * 2 * (size_t)r->m_in);
+    r->staged = nullptr;
+    r->hsrc = r->hdst = nullptr;
+    std::vector<int32_t>().swap(r->src);
+    std::vector<int32_t>().swap(r->dst);
+}
+
+void builder_loop(harp_server* s, int which) {
     cudaSetDevice(s->device);
+    cudaStream_t stream = s->copy_stream[which];
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         s->cv_build.wait(lk, [&] { return s->stop || can_admit(s); });
@@ -124,9 +185,10 @@ void builder_loop(harp_server* s) {
         if (oversize) {
             lk.unlock();
             // halo-partitioned path with the owner rule, within the budget; counted right here
-            st = harp_count4_partitioned(r->n, r->m_in, r->src.data(), r->dst.data(), s->opts.hbm_budget_bytes, 0,
-                                         r->counts, nullptr);
+            st = harp_count4_partitioned(r->n, r->m_in, r->hsrc, r->hdst, s->opts.hbm_budget_bytes, 0, r->counts,
+                                         nullptr);
             lk.lock();
+            drop_host_copy(s, r);
             r->partitioned = true;
             s->partitioned++;
             s->resident -= charge;
@@ -138,9 +200,10 @@ void builder_loop(harp_server* s) {
         }
         s->building++;
         lk.unlock();
-        st = harp_build_csr(r->n, r->m_in, r->src.data(), r->dst.data(), HARP_PTR_HOST, s->copy_stream, &r->csr);
+        st = harp_build_csr(r->n, r->m_in, r->hsrc, r->hdst, HARP_PTR_HOST, stream, &r->csr);
         lk.lock();
         s->building--;
+        drop_host_copy(s, r);  // the build has copied and synchronised
         if (st != HARP_OK) {
             s->resident -= charge;
             s->inflight--;
@@ -150,8 +213,6 @@ void builder_loop(harp_server* s) {
             continue;
         }
         r->state = ReqState::Built;
-        std::vector<int32_t>().swap(r->src);  // the host copy is no longer needed
-        std::vector<int32_t>().swap(r->dst);
         s->built.push_back(r->ticket);
         s->cv_exec.notify_one();
     }
@@ -221,25 +282,30 @@ harp_status harp_server_create(const harp_server_opts* opts, harp_server** out) 
     if (!out) return HARP_EINVAL;
     harp_server* s = new (std::nothrow) harp_server();
     if (!s) return HARP_ENOMEM;
-    if (opts && opts->reserved != 0) {
-        delete s;
-        return HARP_EINVAL;
-    }
     if (opts) s->opts = *opts;
     if (s->opts.hbm_budget_bytes == 0) s->opts.hbm_budget_bytes = (uint64_t)64 << 30;
+    if (s->opts.staging_mib == 0) s->opts.staging_mib = 512;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return HARP_ECUDA;
     }
-    cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < harp_server::kBuilders && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&s->copy_stream[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute_stream, cudaStreamNonBlocking);
+    void* arena = nullptr;
+    const size_t arena_bytes = (size_t)s->opts.staging_mib << 20;
+    if (e == cudaSuccess) e = cudaMallocHost(&arena, arena_bytes);
     if (e != cudaSuccess) {
         harp::record_cuda_error(e);
-        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+        for (cudaStream_t c : s->copy_stream)
+            if (c) cudaStreamDestroy(c);
+        if (s->compute_stream) cudaStreamDestroy(s->compute_stream);
         delete s;
-        return HARP_ECUDA;
+        return e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
     }
-    s->builder = std::thread(builder_loop, s);
+    s->staging.init(arena, arena_bytes);
+    for (int k = 0; k < harp_server::kBuilders; ++k) s->builder[k] = std::thread(builder_loop, s, k);
     s->executor = std::thread(executor_loop, s);
     *out = s;
     return HARP_OK;
@@ -253,12 +319,31 @@ harp_status harp_submit(harp_server* s, int64_t n, int64_t m_in, const int32_t* 
     if (!r) return HARP_ENOMEM;
     r->n = n;
     r->m_in = m_in;
-    r->src.assign(src, src + m_in);
-    r->dst.assign(dst, dst + m_in);
     r->need = footprint(n, m_in);
     r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (m_in > 0) r->staged = static_cast<int32_t*>(s->staging.alloc(sizeof(int32_t) * 2 * (size_t)m_in));
+    }
+    if (r->staged) {
+        std::memcpy(r->staged, src, sizeof(int32_t) * (size_t)m_in);
+        std::memcpy(r->staged + m_in, dst, sizeof(int32_t) * (size_t)m_in);
+        r->hsrc = r->staged;
+        r->hdst = r->staged + m_in;
+    } else if (m_in > 0) {
+        try {
+            r->src.assign(src, src + m_in);
+            r->dst.assign(dst, dst + m_in);
+        } catch (...) {
+            delete r;
+            return HARP_ENOMEM;
+        }
+        r->hsrc = r->src.data();
+        r->hdst = r->dst.data();
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
+        drop_host_copy(s, r);
         delete r;
         return HARP_EINVAL;
     }
@@ -340,15 +425,20 @@ void harp_server_destroy(harp_server* s) {
     }
     s->cv_build.notify_all();
     s->cv_exec.notify_all();
-    if (s->builder.joinable()) s->builder.join();
+    for (auto& b : s->builder)
+        if (b.joinable()) b.join();
     if (s->executor.joinable()) s->executor.join();
     cudaSetDevice(s->device);
     for (auto& kv : s->reqs) {
         if (kv.second->csr) harp_csr_free(kv.second->csr);
         delete kv.second;
     }
-    cudaStreamDestroy(s->copy_stream);
+    for (cudaStream_t c : s->copy_stream) {
+        cudaStreamSynchronize(c);
+        cudaStreamDestroy(c);
+    }
     cudaStreamDestroy(s->compute_stream);
+    cudaFreeHost(s->staging.base);
     delete s;
 }
 
