@@ -13,7 +13,7 @@
 //     degree >= 2, and every row's segment starts at fpos[w] (its first neighbour of degree >= 2);
 //   * a dense counter for x fits 8 bits while d(x) <= 255 and 16 bits while d(x) <= 65535, so the
 //     x-range splits into the bands [n1, r256), [r256, r64k), [r64k, end) with 8-, 16- and 32-bit
-//     counters.  The bands cut into windows of 100 KiB of counters form a fixed grid per graph, so the
+//     counters.  The bands cut into windows of 48-100 KiB of counters form a fixed grid per graph, so the
 //     row position of every grid boundary is computed once per row (bpos) instead of being searched
 //     for every (root, lower neighbour, window).
 // pos_w(u) itself is computed once per lower arc (rev) by a fully parallel pass.
@@ -26,7 +26,8 @@
 //   W <= warp_max   one warp, hash table in shared memory (warp-local mode)
 //   larger          one block per (root, grid window): dense packed counters in shared memory
 //                   (CTA mode); lower neighbours are handed to warps in groups of 32, heaviest first,
-//                   and segments of 2048+ elements are split across all warps of the block.
+//                   and segments of 2048+ elements are split across all warps of the block.  The
+//                   window (100, 64 or 48 KiB) sets how many blocks share an SM (2, 3 or 4).
 #include "harp_internal.cuh"
 
 namespace harp {
@@ -34,7 +35,12 @@ namespace {
 
 constexpr int32_t kEmpty = -1;
 constexpr int kWinThreads = 512;
-constexpr int kWinWords = 25600;             // 100 KiB of packed counters per window
+// Window sizes by resident blocks per SM (plan.c4_window_bytes picks one): 100 KiB at 2 blocks,
+// 64 KiB at 3, 48 KiB at 4 (counters plus ~3 KiB of static and reserved shared memory per block).
+constexpr int kWinWords2 = 25600;
+constexpr int kWinWords3 = 16384;
+constexpr int kWinWords4 = 12288;
+__host__ __device__ constexpr int win_words(int minb) { return minb == 2 ? kWinWords2 : (minb == 3 ? kWinWords3 : kWinWords4); }
 constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallSlots = 1024;            // per-warp hash table (W <= 512)
@@ -46,6 +52,8 @@ constexpr int kChunk = 1024;                 // elements per split chunk
 // ---------------------------------------------------------------------------------------------
 // Per-graph band and grid geometry (ginfo: kGInfo int64 per graph).
 // ---------------------------------------------------------------------------------------------
+// The window size is a template parameter (WORDS 32-bit words of counters) of every kernel that
+// computes window geometry, so each size is its own compiled instance with constant spans.
 enum : int { GI_LO = 0, GI_HI, GI_N1, GI_B1, GI_B2, GI_NWIN };
 
 __device__ __forceinline__ int64_t first_above_in(const int32_t* __restrict__ deg, int64_t lo, int64_t hi, int32_t t) {
@@ -57,7 +65,9 @@ __device__ __forceinline__ int64_t first_above_in(const int32_t* __restrict__ de
     return lo;
 }
 
-__device__ __forceinline__ int64_t span_of(int width) { return (int64_t)kWinWords * (32 / width); }
+// x-values one window covers at a counter width: the window's words times counters per word
+template <int WORDS>
+__device__ __forceinline__ int64_t span_of(int width) { return (int64_t)WORDS * (32 / width); }
 
 struct Band {
     int64_t start, end;
@@ -73,11 +83,12 @@ __device__ __forceinline__ Band band_of(const int64_t* gi, int b) {
 }
 
 // window j of the graph's grid: [xlo, xhi) and counter width; false if j is past the grid
+template <int WORDS>
 __device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_t& xlo, int64_t& xhi, int& width) {
     for (int b = 0; b < 3; ++b) {
         const Band B = band_of(gi, b);
         if (B.end <= B.start) continue;
-        const int64_t S = span_of(B.width);
+        const int64_t S = span_of<WORDS>(B.width);
         const int64_t nb = (B.end - B.start + S - 1) / S;
         if (j < nb) {
             xlo = B.start + j * S;
@@ -91,18 +102,20 @@ __device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_
 }
 
 // number of grid windows that intersect [n1, u)
+template <int WORDS>
 __device__ __forceinline__ int64_t windows_below(const int64_t* gi, int64_t u) {
     int64_t total = 0;
     for (int b = 0; b < 3; ++b) {
         const Band B = band_of(gi, b);
         const int64_t e = B.end < u ? B.end : u;
         if (e <= B.start) continue;
-        const int64_t S = span_of(B.width);
+        const int64_t S = span_of<WORDS>(B.width);
         total += (e - B.start + S - 1) / S;
     }
     return total;
 }
 
+template <int WORDS>
 __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int64_t* __restrict__ gbase,
                            int64_t G, int64_t* __restrict__ ginfo) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
@@ -116,7 +129,7 @@ __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int
         gi[GI_N1] = n1;
         gi[GI_B1] = r256 > n1 ? r256 : n1;
         gi[GI_B2] = r64k > n1 ? r64k : n1;
-        gi[GI_NWIN] = windows_below(gi, hi);
+        gi[GI_NWIN] = windows_below<WORDS>(gi, hi);
     }
 }
 
@@ -160,6 +173,7 @@ __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off,
 
 // fpos[w] = row position of w's first neighbour of degree >= 2 (the graph's n1 boundary), and
 // bpos[w * kGridCap + k] = row position of the k-th boundary of w's grid (k <= nwin), if it fits
+template <int WORDS>
 __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                           const int32_t* __restrict__ gid, const int64_t* __restrict__ ginfo, int64_t n,
                           int32_t* __restrict__ fpos, int32_t* __restrict__ bpos) {
@@ -181,7 +195,7 @@ __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __rest
         if (k < nwin) {
             int64_t xhi;
             int width;
-            grid_window(gi, k, bound, xhi, width);
+            grid_window<WORDS>(gi, k, bound, xhi, width);
         }
         const int64_t wb = off[w];
         bpos[t] = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)bound);
@@ -278,6 +292,7 @@ __device__ __forceinline__ uint32_t hash_add(int32_t* keys, uint32_t* cnt, uint3
 // ---------------------------------------------------------------------------------------------
 // Classification: every root (warp per root, descending rank so heavy roots are queued first).
 // ---------------------------------------------------------------------------------------------
+template <int WORDS>
 __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                                      const int32_t* __restrict__ deg,
                                                      const int32_t* __restrict__ dplus,
@@ -315,7 +330,7 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
             const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
             const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
             q_win[slot] = u;
-            wcount[slot] = (int32_t)windows_below(gi, u);
+            wcount[slot] = (int32_t)windows_below<WORDS>(gi, u);
         }
     }
 }
@@ -382,7 +397,10 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
 // ---------------------------------------------------------------------------------------------
 // Windowed CTA mode: one block per (root, grid window); dense packed counters in shared memory.
 // ---------------------------------------------------------------------------------------------
-template <int WIDTH>
+// Packed counters: 8-bit counters four to a word, 16-bit two to a word.  (A byte-plane layout that
+// puts consecutive x in consecutive banks was measured no faster: the kernel is bound by load
+// latency and the end-of-item barrier, not by shared-memory bank conflicts.)
+template <int WIDTH, int WORDS>
 __device__ __forceinline__ uint32_t counter_add(uint32_t* cw, uint32_t r) {
     if (WIDTH == 8) {
         const uint32_t sh = (r & 3u) << 3;
@@ -411,14 +429,14 @@ __device__ __forceinline__ void flag_error(uint64_t* acc, unsigned long long bit
     atomicOr((unsigned long long*)&acc[ACC_ERR], bit);
 }
 
-template <int WIDTH>
+template <int WIDTH, int WORDS>
 __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                             const int32_t* __restrict__ fpos, const int32_t* __restrict__ rev,
                                             const int32_t* __restrict__ bpos, bool table, int64_t j, int64_t ub,
                                             int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
                                             WinShared& sh, uint64_t& c4, uint64_t* acc) {
     const int l = lane_id();
-    auto add = [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); };
+    auto add = [&](int32_t x) { c4 += counter_add<WIDTH, WORDS>(cw, (uint32_t)(x - xlo)); };
     const int ngroups = (int)((dm + 31) >> 5);
     for (;;) {
         int g = 0;
@@ -462,7 +480,7 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
     }
 }
 
-template <int WIDTH>
+template <int WIDTH, int WORDS>
 __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int32_t xlo, uint32_t* cw, WinShared& sh,
                                            uint64_t& c4) {
     const int l = lane_id();
@@ -483,11 +501,12 @@ __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int
         const int64_t b = sh.split_base[e] + (int64_t)(t - sh.split_pre[e]) * kChunk;
         const int64_t end = sh.split_base[e] + sh.split_len[e];
         const int64_t stop = b + kChunk < end ? b + kChunk : end;
-        warp_run(cols, b, stop - b, [&](int32_t x) { c4 += counter_add<WIDTH>(cw, (uint32_t)(x - xlo)); });
+        warp_run(cols, b, stop - b, [&](int32_t x) { c4 += counter_add<WIDTH, WORDS>(cw, (uint32_t)(x - xlo)); });
     }
 }
 
-__global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __restrict__ off,
+template <int MINB>
+__global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* __restrict__ off,
                                                               const int32_t* __restrict__ cols,
                                                               const int32_t* __restrict__ deg,
                                                               const int32_t* __restrict__ dplus,
@@ -529,26 +548,27 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __r
         const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
         int64_t xlo = 0, xhi = 0;
         int width = 32;
-        grid_window(gi, j, xlo, xhi, width);
+        grid_window<win_words(MINB)>(gi, j, xlo, xhi, width);
         const bool last = xhi >= (int64_t)u;
         if (last) xhi = u;
         const bool first = j == 0;
         const bool table = gi[GI_NWIN] + 1 <= kGridCap;
         const int64_t dm = (int64_t)deg[u] - dplus[u];
         const int64_t ub = off[u];
+        constexpr int WORDS = win_words(MINB);
         const int per = 32 / width;
         const int words = (int)((xhi - xlo + per - 1) / per);
         for (int i = threadIdx.x; i < words; i += kWinThreads) cw[i] = 0;
         __syncthreads();
         uint64_t a_c4 = 0;
         if (width == 8)
-            window_pass<8>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<8, WORDS>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                            sh, a_c4, acc);
         else if (width == 16)
-            window_pass<16>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<16, WORDS>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                             sh, a_c4, acc);
         else
-            window_pass<32>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<32, WORDS>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                             sh, a_c4, acc);
         __syncthreads();
         if (sh.nsplit > 0) {
@@ -562,9 +582,9 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_c4_window(const int64_t* __r
                 sh.split_pre[ns] = run;
             }
             __syncthreads();
-            if (width == 8) split_pass<8>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else if (width == 16) split_pass<16>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else split_pass<32>(cols, (int32_t)xlo, cw, sh, a_c4);
+            if (width == 8) split_pass<8, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else if (width == 16) split_pass<16, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else split_pass<32, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
             __syncthreads();
         }
         if (sink.batch()) {
@@ -586,29 +606,27 @@ unsigned grid_cap(int64_t work, int threads, int64_t cap) {
     return (unsigned)b;
 }
 
-}  // namespace
-
-harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s) {
+// The whole wedge pass for one window size (MINB resident window blocks per SM).
+template <int MINB>
+harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, cudaStream_t s) {
+    constexpr int WORDS = win_words(MINB);
     const int64_t n = g->n;
-    if (n == 0 || g->m == 0) return HARP_OK;
-    uint32_t warp_max = plan.c4_warp_max_work ? plan.c4_warp_max_work : 512;
-    if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
     const int64_t G = ws.G > 0 ? ws.G : 1;
     const Sink sink{ws.acc, ws.gid, ws.accG};
     int32_t* wcount = ws.q_win + n;
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
-    k_c4_ginfo<<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.ginfo);
+    k_c4_ginfo<WORDS><<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.ginfo);
     HARP_LAUNCHED();
     const int64_t arcs = ws.arcs >= 0 ? ws.arcs : 2 * g->m;  // must equal off[n]
     k_c4_rev<<<grid_cap((arcs + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
         ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, arcs, ws.rev);
     HARP_LAUNCHED();
-    k_c4_bpos<<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n, ws.fpos,
-                                                                      ws.bpos);
+    k_c4_bpos<WORDS><<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n,
+                                                                             ws.fpos, ws.bpos);
     HARP_LAUNCHED();
-    k_c4_classify<<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev,
-                                                                   ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
-                                                                   ws.q_mid, ws.q_win, wcount, ws.acc);
+    k_c4_classify<WORDS><<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(
+        ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
+        ws.q_mid, ws.q_win, wcount, ws.acc);
     HARP_LAUNCHED();
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
@@ -618,13 +636,26 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     HARP_CK(prof_mark(s, SEG_C4_SMALL));
     HARP_CK(prof_mark(s, SEG_C4_MID));  // the CTA-hash mode is folded into the windowed mode
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
-    const size_t win_smem = (size_t)kWinWords * sizeof(uint32_t);
-    HARP_CK(cudaFuncSetAttribute(k_c4_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
-    k_c4_window<<<152 * 2, kWinThreads, win_smem, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.bpos,
-                                                       ws.gid, ws.ginfo, ws.q_win, ws.win_prefix, ws.acc, sink);
+    const size_t win_smem = (size_t)WORDS * sizeof(uint32_t);
+    HARP_CK(cudaFuncSetAttribute(k_c4_window<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
+    k_c4_window<MINB><<<152 * MINB, kWinThreads, win_smem, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev,
+                                                                ws.bpos, ws.gid, ws.ginfo, ws.q_win, ws.win_prefix,
+                                                                ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_WINDOW));
     return HARP_OK;
+}
+
+}  // namespace
+
+harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s) {
+    if (g->n == 0 || g->m == 0) return HARP_OK;
+    uint32_t warp_max = plan.c4_warp_max_work ? plan.c4_warp_max_work : 512;
+    if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
+    // window size: the largest of the three that fits plan.c4_window_bytes (at least the smallest)
+    if (plan.c4_window_bytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, s);
+    if (plan.c4_window_bytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, s);
+    return wedge_pass<4>(g, ws, warp_max, s);
 }
 
 }  // namespace harp

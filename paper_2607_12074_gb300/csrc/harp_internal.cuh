@@ -76,7 +76,8 @@ enum : int {
     Q_SORT_CTA = 36,       // rows for the CTA row sort (36) and the hub row sort (37)
     T_TRI_M = 38,          // ticket of the 512-wide CTA triangle kernel
     ACC_SIG_HITS = 39,     // 4-clique extensions answered by a staged signature frontier
-    kOutLen = 40
+    Q_TRI_FB = 40,         // length of the unstaged-fallback triangle queue
+    kOutLen = 48
 };
 
 // Per-graph accumulator slots (batch mode), kGStride per graph.

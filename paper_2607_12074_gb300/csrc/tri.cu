@@ -41,9 +41,10 @@ constexpr int kCtaMax = 1024;
 constexpr int kInf = 0x7fffffff;
 constexpr int32_t kNoKey = -1;
 
-// Anchor queues in ws.q_tri (n entries): warp-mode anchors (2 <= d <= tri_warp_max) from the front,
-// CTA-mode and fallback anchors from the back.  Vertices are scanned in descending rank, so
-// high-degree anchors tend to be queued (and taken) first.
+// Anchor queues: in ws.q_tri (n entries) warp-mode anchors (2 <= d <= tri_warp_max) from the front
+// and CTA-mode anchors from the back; fallback anchors in their own queue (ws.q_mid, free until the
+// wedge pass).  Vertices are scanned in descending rank, so high-degree anchors tend to be queued
+// (and taken) first.
 //
 // Tier of an anchor of out-degree d: -1 none, 0 warp, 1/2/3 CTA 256/512/1024, 4 fallback.
 // wmax <= 32 and cmax <= kCtaMax (the plan's tri_warp_max / tri_cta_max).
@@ -55,26 +56,28 @@ __device__ __forceinline__ int tri_class(int d, int wmax, int cmax) {
 }
 
 __global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int64_t own_lo, int64_t own_hi,
-                               int wmax, int cmax, int32_t* __restrict__ q, unsigned long long* __restrict__ cnt) {
+                               int wmax, int cmax, int32_t* __restrict__ q, int32_t* __restrict__ q_fb,
+                               unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ cnt_fb) {
     const int l = lane_id();
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - l; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = n - 1 - (base + l);
         int cls = -1;
         if (u >= own_lo && u < own_hi && u < n) cls = tri_class(dplus[u], wmax, cmax);
-        cls = cls > 0 ? 1 : cls;  // 0: warp queue, 1: CTA queue
+        cls = cls == 4 ? 2 : (cls > 0 ? 1 : cls);  // 0: warp queue, 1: CTA queue, 2: fallback queue
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < 3; ++c) {
             const uint32_t mask = __ballot_sync(kFull, cls == c);
             if (!mask) continue;
             unsigned long long start = 0;
             const int leader = __ffs(mask) - 1;
-            if (l == leader) start = atomicAdd(&cnt[c], (unsigned long long)__popc(mask));
+            if (l == leader) start = atomicAdd(c < 2 ? &cnt[c] : cnt_fb, (unsigned long long)__popc(mask));
             start = __shfl_sync(kFull, start, leader);
             if (cls == c) {
                 const unsigned long long k = start + __popc(mask & lanemask_lt());
                 if (c == 0) q[k] = (int32_t)u;
-                else q[n - 1 - (int64_t)k] = (int32_t)u;
+                else if (c == 1) q[n - 1 - (int64_t)k] = (int32_t)u;
+                else q_fb[k] = (int32_t)u;
             }
         }
     }
@@ -459,20 +462,19 @@ __device__ __forceinline__ int64_t lb_global(const int32_t* __restrict__ a, int6
 __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict__ offp,
                                                       const int32_t* __restrict__ colsp,
                                                       const int32_t* __restrict__ deg,
-                                                      const int32_t* __restrict__ q, int64_t n, int wmax, int cmax,
-                                                      const unsigned long long* __restrict__ cnt,
+                                                      const int32_t* __restrict__ q_fb,
+                                                      const unsigned long long* __restrict__ cnt_fb,
                                                       int32_t* __restrict__ scratch, int64_t scratch_per_warp,
                                                       uint32_t* __restrict__ te, Sink sink) {
     __shared__ uint64_t red[32];
     const int w = threadIdx.x >> 5, l = lane_id();
     const int nw = blockDim.x >> 5;
     int32_t* S = scratch + ((int64_t)blockIdx.x * nw + w) * scratch_per_warp;
-    const int64_t nq = (int64_t)cnt[1];
+    const int64_t nq = (int64_t)*cnt_fb;
     uint64_t tri = 0, k4 = 0, paw = 0;
     for (int64_t k = blockIdx.x; k < nq; k += gridDim.x) {
-        const int32_t u = q[n - 1 - k];
+        const int32_t u = q_fb[k];
         const int64_t ub = offp[u], ue = offp[u + 1];
-        if (tri_class((int)(ue - ub), wmax, cmax) != 4) continue;
         const uint64_t du = (uint64_t)deg[u];
         const uint64_t tri0 = tri, k40 = k4, paw0 = paw;
         for (int64_t a = ub + w; a < ue; a += nw) {  // warp per out-arc (u, v)
@@ -575,7 +577,9 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     unsigned long long* cnt = (unsigned long long*)&ws.acc[Q_TRI_WARP];
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, wmax, cmax, ws.q_tri, cnt);
+    unsigned long long* cnt_fb = (unsigned long long*)&ws.acc[Q_TRI_FB];
+    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, wmax, cmax, ws.q_tri, ws.q_mid,
+                                                    cnt, cnt_fb);
     HARP_LAUNCHED();
     const Sink sink{ws.acc, ws.gid, ws.accG};
     if (plan.tri_probe == HARP_PROBE_BSEARCH) HARP_TRY(launch_tiers<true>(g, ws, wmax, cmax, reuse, s));
@@ -590,8 +594,8 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
         const size_t bytes = (size_t)fb_blocks * 8 * (size_t)per_warp * sizeof(int32_t);
         int32_t* scratch = nullptr;
         HARP_CK(cudaMallocAsync((void**)&scratch, bytes, s));
-        k_tri_fallback<<<fb_blocks, 256, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, n, wmax, cmax, cnt, scratch,
-                                                 per_warp, ws.te, sink);
+        k_tri_fallback<<<fb_blocks, 256, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_mid, cnt_fb, scratch, per_warp,
+                                                 ws.te, sink);
         note_launch();
         cudaError_t e = cudaGetLastError();
         cudaFreeAsync(scratch, s);

@@ -23,7 +23,7 @@ import numpy as np
 WARP_MAX_TRI = 32
 CTA_SMALL_MAX = 256
 CTA_MAX = 1024
-WIN_WORDS = 51200
+WIN_WORDS = {2: 25600, 3: 16384, 4: 12288}  # counter words per wedge window by resident blocks per SM
 
 
 def _simple_edges(n, src, dst):
@@ -58,8 +58,8 @@ def rank_space(n, src, dst):
             "split": split, "dplus": deg - split}
 
 
-def meter(n, src, dst, c4_warp_max=512, c4_cta_max=8192):
-    """Per-kernel work and algorithmic bytes (dict of dicts)."""
+def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
+    """Per-kernel work and algorithmic bytes (dict of dicts) under the given wedge plan fields."""
     G = rank_space(n, src, dst)
     m = G["m"]
     deg, indptr, rows, cols, pos = G["deg"], G["indptr"], G["rows"], G["cols"], G["pos"]
@@ -108,17 +108,17 @@ def meter(n, src, dst, c4_warp_max=512, c4_cta_max=8192):
     seg = np.maximum(pos[rev] - fpos[rw], 0)
     W = np.bincount(ru, weights=seg, minlength=n).astype(np.int64)
     dm = split
-    tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= c4_warp_max, 0, np.where(W <= c4_cta_max, 1, 2)))
+    # warp-local hash mode for W <= c4_warp_max, windowed counters above (no middle tier)
+    tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= min(c4_warp_max, 512), 0, 2))
+    words = WIN_WORDS[2 if c4_window_bytes >= 4 * WIN_WORDS[2] else (3 if c4_window_bytes >= 4 * WIN_WORDS[3] else 4)]
     u_ids = np.arange(n, dtype=np.int64)
-    by_dm = np.where(dm <= 255, 8, np.where(dm <= 65535, 16, 32))
     nwin = np.zeros(n, np.int64)
-    bounds = [n1, max(r256, n1), max(r64k, n1)]
+    bounds = [n1, max(r256, n1), max(r64k, n1), n]     # x bands by the degree of x: 8-, 16-, 32-bit counters
     for band, width_x in enumerate((8, 16, 32)):
         lo = np.minimum(bounds[band], u_ids)
-        hi = np.minimum(bounds[band + 1], u_ids) if band < 2 else u_ids
-        hi = np.maximum(hi, lo)
-        span = WIN_WORDS * (32 // np.minimum(by_dm, width_x))
-        nwin += (hi - lo + span - 1) // span
+        hi = np.maximum(np.minimum(bounds[band + 1], u_ids), lo)
+        span = words * (32 // width_x)
+        nwin += (hi - lo + span - 1) // span            # grid windows of the band that intersect [n1, u)
     nwin = np.where(tier == 2, nwin, 1)
     for t, name in ((0, "c4_small"), (1, "c4_mid"), (2, "c4_window")):
         sel = tier == t
