@@ -115,29 +115,43 @@ __device__ __forceinline__ int64_t windows_below(const int64_t* gi, int64_t u) {
     return total;
 }
 
+// The x-range of a graph's grid is [n1, hi) intersected with [x_lo, x_hi) (a partitioned wedge
+// block owns only the opposite vertices in that slice; a whole graph passes [0, INT64_MAX)).
 template <int WORDS>
 __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int64_t* __restrict__ gbase,
-                           int64_t G, int64_t* __restrict__ ginfo) {
+                           int64_t G, int64_t x_lo, int64_t x_hi, int64_t* __restrict__ ginfo) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lo = gbase ? gbase[g] : 0, hi = gbase ? gbase[g + 1] : n;
-        const int64_t n1 = first_above_in(deg, lo, hi, 1);
-        const int64_t r256 = first_above_in(deg, lo, hi, 255);
-        const int64_t r64k = first_above_in(deg, lo, hi, 65535);
+        const int64_t lo = gbase ? gbase[g] : 0;
+        int64_t hi = gbase ? gbase[g + 1] : n;
+        int64_t n1 = first_above_in(deg, lo, hi, 1);
+        int64_t r256 = first_above_in(deg, lo, hi, 255);
+        int64_t r64k = first_above_in(deg, lo, hi, 65535);
+        auto clamp = [&](int64_t v) { return v < x_lo ? x_lo : (v > x_hi ? x_hi : v); };
+        hi = hi < x_hi ? hi : x_hi;
+        n1 = clamp(n1);
+        n1 = n1 < hi ? n1 : hi;
+        r256 = clamp(r256);
+        r64k = clamp(r64k);
         int64_t* gi = ginfo + g * kGInfo;
         gi[GI_LO] = lo;
         gi[GI_HI] = hi;
         gi[GI_N1] = n1;
-        gi[GI_B1] = r256 > n1 ? r256 : n1;
-        gi[GI_B2] = r64k > n1 ? r64k : n1;
+        gi[GI_B1] = r256 > n1 ? (r256 < hi ? r256 : hi) : n1;
+        gi[GI_B2] = r64k > n1 ? (r64k < hi ? r64k : hi) : n1;
         gi[GI_NWIN] = windows_below<WORDS>(gi, hi);
     }
 }
 
-// rev[a] = pos_w(u) for every lower arc (u -> w) at row position a of u.  Each thread takes a run of
-// kRevRun consecutive arcs of the CSR (one search for the run's first row, then it walks forward), so
-// hub rows are spread over many threads.  arcs must equal off[n]; the walk never passes row n - 1.
+// rev[a] = pos_w(u) for every lower arc (u -> w) at position a of u's list.  Each thread takes a run
+// of kRevRun consecutive arcs (one search for the run's first row, then it walks forward), so hub
+// rows are spread over many threads.  arcs must equal off[n]; the walk never passes row n - 1.
+// Whole graph (ROWS = false): the lists are the row prefixes of (off, cols) and the position comes
+// from N+(w) (offp, colsp): d-(w) + rank of u in N+(w).  Partitioned (ROWS = true): the lists are
+// the roots' lower lists (off = loff, cols = lcols) and the position is searched in w's row of the
+// halo (offp = off, colsp = cols of the rows).
 constexpr int kRevRun = 16;
 
+template <bool ROWS>
 __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                                 const int64_t* __restrict__ offp, const int32_t* __restrict__ colsp,
                                                 const int32_t* __restrict__ deg, const int32_t* __restrict__ dplus,
@@ -166,7 +180,8 @@ __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off,
             if (a >= lower_end || lower_end - ub < 2) continue;  // only lower arcs of roots with d- >= 2
             const int32_t w = cols[a];
             const int64_t pb = offp[w];
-            rev[a] = (deg[w] - dplus[w]) + (int32_t)lower_bound_i32(colsp + pb, offp[w + 1] - pb, (int32_t)u);
+            if (ROWS) rev[a] = (int32_t)lower_bound_i32(colsp + pb, offp[w + 1] - pb, (int32_t)u);
+            else rev[a] = (deg[w] - dplus[w]) + (int32_t)lower_bound_i32(colsp + pb, offp[w + 1] - pb, (int32_t)u);
         }
     }
 }
@@ -187,10 +202,10 @@ __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __rest
             const int64_t wb = off[w];
             const int32_t f = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)gi[GI_N1]);
             fpos[w] = f;
-            if (nwin + 1 <= kGridCap) bpos[t] = f;
+            if (bpos && nwin + 1 <= kGridCap) bpos[t] = f;
             continue;
         }
-        if (nwin + 1 > kGridCap || k > nwin) continue;
+        if (!bpos || nwin + 1 > kGridCap || k > nwin) continue;
         int64_t bound = gi[GI_HI];
         if (k < nwin) {
             int64_t xhi;
@@ -293,7 +308,7 @@ __device__ __forceinline__ uint32_t hash_add(int32_t* keys, uint32_t* cnt, uint3
 // Classification: every root (warp per root, descending rank so heavy roots are queued first).
 // ---------------------------------------------------------------------------------------------
 template <int WORDS>
-__global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+__global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__ loff, const int32_t* __restrict__ lcols,
                                                      const int32_t* __restrict__ deg,
                                                      const int32_t* __restrict__ dplus,
                                                      const int32_t* __restrict__ fpos,
@@ -313,10 +328,10 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
         if (u < own_lo || u >= own_hi) continue;  // the owner rule: only this range's roots
         const int64_t dm = (int64_t)deg[u] - dplus[u];
         if (dm < 2) continue;
-        const int64_t ub = off[u];
+        const int64_t ub = loff[u];
         uint64_t W = 0;
         for (int64_t a = l; a < dm; a += 32) {
-            const int32_t f = fpos[cols[ub + a]];
+            const int32_t f = fpos[lcols[ub + a]];
             const int32_t p = rev[ub + a];
             W += p > f ? (uint64_t)(p - f) : 0;
         }
@@ -340,6 +355,8 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ cols,
+                                                            const int64_t* __restrict__ loff,
+                                                            const int32_t* __restrict__ lcols,
                                                             const int32_t* __restrict__ deg,
                                                             const int32_t* __restrict__ dplus,
                                                             const int32_t* __restrict__ fpos,
@@ -360,7 +377,7 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
         const int32_t u = q_small[k];
         const uint32_t W = (uint32_t)q_small[n + k];
         const int64_t dm = (int64_t)deg[u] - dplus[u];
-        const int64_t ub = off[u];
+        const int64_t ub = loff[u];
         uint32_t P = 32;
         while (P < 2 * W) P <<= 1;
         for (uint32_t i = l; i < P; i += 32) {
@@ -374,7 +391,7 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
             int64_t base = 0;
             int len = 0;
             if (a < dm) {
-                const int32_t wv = cols[ub + a];
+                const int32_t wv = lcols[ub + a];
                 const int32_t f = fpos[wv];
                 const int32_t p = rev[ub + a];
                 base = off[wv] + f;
@@ -431,6 +448,7 @@ __device__ __forceinline__ void flag_error(uint64_t* acc, unsigned long long bit
 
 template <int WIDTH, int WORDS>
 __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                                            const int32_t* __restrict__ lcols,
                                             const int32_t* __restrict__ fpos, const int32_t* __restrict__ rev,
                                             const int32_t* __restrict__ bpos, bool table, int64_t j, int64_t ub,
                                             int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
@@ -447,7 +465,7 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
         int64_t base = 0;
         int len = 0;
         if (a < dm) {
-            const int32_t wv = cols[ub + a];
+            const int32_t wv = lcols[ub + a];
             const int64_t wb = off[wv];
             int64_t p0, p1;
             if (first) p0 = fpos[wv];
@@ -508,6 +526,8 @@ __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int
 template <int MINB>
 __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* __restrict__ off,
                                                               const int32_t* __restrict__ cols,
+                                                              const int64_t* __restrict__ loff,
+                                                              const int32_t* __restrict__ lcols,
                                                               const int32_t* __restrict__ deg,
                                                               const int32_t* __restrict__ dplus,
                                                               const int32_t* __restrict__ fpos,
@@ -552,9 +572,9 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
         const bool last = xhi >= (int64_t)u;
         if (last) xhi = u;
         const bool first = j == 0;
-        const bool table = gi[GI_NWIN] + 1 <= kGridCap;
+        const bool table = bpos != nullptr && gi[GI_NWIN] + 1 <= kGridCap;
         const int64_t dm = (int64_t)deg[u] - dplus[u];
-        const int64_t ub = off[u];
+        const int64_t ub = loff[u];
         constexpr int WORDS = win_words(MINB);
         const int per = 32 / width;
         const int words = (int)((xhi - xlo + per - 1) / per);
@@ -562,13 +582,13 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
         __syncthreads();
         uint64_t a_c4 = 0;
         if (width == 8)
-            window_pass<8, WORDS>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<8, WORDS>(off, cols, lcols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                            sh, a_c4, acc);
         else if (width == 16)
-            window_pass<16, WORDS>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<16, WORDS>(off, cols, lcols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                             sh, a_c4, acc);
         else
-            window_pass<32, WORDS>(off, cols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<32, WORDS>(off, cols, lcols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                             sh, a_c4, acc);
         __syncthreads();
         if (sh.nsplit > 0) {
@@ -615,22 +635,33 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, cuda
     const Sink sink{ws.acc, ws.gid, ws.accG};
     int32_t* wcount = ws.q_win + n;
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
-    k_c4_ginfo<WORDS><<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.ginfo);
+    k_c4_ginfo<WORDS><<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.x_lo, ws.x_hi, ws.ginfo);
     HARP_LAUNCHED();
-    const int64_t arcs = ws.arcs >= 0 ? ws.arcs : 2 * g->m;  // must equal off[n]
-    k_c4_rev<<<grid_cap((arcs + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
-        ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, arcs, ws.rev);
+    // the roots' lower lists: row prefixes of a whole graph, or their own CSR in a partitioned block
+    const bool lists = ws.loff != nullptr;
+    const int64_t* loff = lists ? ws.loff : ws.off;
+    const int32_t* lcols = lists ? ws.lcols : ws.cols;
+    if (lists) {
+        const int64_t la = ws.lower_arcs;  // == loff[n]
+        k_c4_rev<true><<<grid_cap((la + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
+            ws.loff, ws.lcols, ws.off, ws.cols, ws.deg, ws.dplus, n, la, ws.rev);
+    } else {
+        const int64_t arcs = ws.arcs >= 0 ? ws.arcs : 2 * g->m;  // must equal off[n]
+        k_c4_rev<false><<<grid_cap((arcs + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
+            ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, arcs, ws.rev);
+    }
     HARP_LAUNCHED();
     k_c4_bpos<WORDS><<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n,
                                                                              ws.fpos, ws.bpos);
     HARP_LAUNCHED();
     k_c4_classify<WORDS><<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(
-        ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
+        loff, lcols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
         ws.q_mid, ws.q_win, wcount, ws.acc);
     HARP_LAUNCHED();
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
-    k_c4_small<<<152 * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.q_mid,
+    k_c4_small<<<152 * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus, ws.fpos,
+                                                          ws.rev, ws.q_mid,
                                                           n, ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_SMALL));
@@ -638,7 +669,8 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, cuda
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
     const size_t win_smem = (size_t)WORDS * sizeof(uint32_t);
     HARP_CK(cudaFuncSetAttribute(k_c4_window<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
-    k_c4_window<MINB><<<152 * MINB, kWinThreads, win_smem, s>>>(ws.off, ws.cols, ws.deg, ws.dplus, ws.fpos, ws.rev,
+    k_c4_window<MINB><<<152 * MINB, kWinThreads, win_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus,
+                                                                ws.fpos, ws.rev,
                                                                 ws.bpos, ws.gid, ws.ginfo, ws.q_win, ws.win_prefix,
                                                                 ws.acc, sink);
     HARP_LAUNCHED();

@@ -128,6 +128,14 @@ struct Workspace {
     // -1 = a whole graph, off[n] = 2m
     int64_t own_lo = 0, own_hi = INT64_MAX;
     int64_t arcs = -1;
+    // partitioned wedge pass: the roots' lower lists N-(u) in their own CSR (loff [n+1], lcols), the
+    // rows (off, cols) hold only x in [x_lo, x_hi) (the opposite vertices this block owns); nullptr =
+    // a whole graph, whose row prefixes are the lower lists.  bpos may be nullptr (boundaries are
+    // then searched per window).
+    const int64_t* loff = nullptr;
+    const int32_t* lcols = nullptr;
+    int64_t lower_arcs = 0;  // loff[n]
+    int64_t x_lo = 0, x_hi = INT64_MAX;
 };
 
 // The workspace layout for (n, m): assigns every array of ws inside [base, base + returned bytes)

@@ -1,26 +1,25 @@
 // Step a9: ownership-preserving partitioned counting (Section III-E) for graphs whose counting
 // footprint exceeds a device-memory budget.
 //
-// The host builds the simple graph in global rank order (rank = (degree, id)) and cuts the rank
-// space into contiguous ranges P_k sized to the budget.  The canonical owner certificate of an anchor
-// is the partition of the first vertex of its globally ordered anchor tuple: a triangle / 4-clique
-// anchor and all its per-edge contributions belong to its lowest vertex u, a wedge (4-cycle) anchor
-// to its top vertex u.  Partition k enumerates exactly the anchors it owns, over a halo that holds
-// every row those anchors read:
-//   * rows of u in P_k and of every lower neighbour w of such u, truncated to entries below P_k's
-//     upper bound (the wedge prefixes x < u and the lower lists N-(u) lie inside; a truncation only
-//     drops a row's suffix, so every row position used by the kernels equals the global one);
-//   * the out-lists N+(v) of every vertex v in P_k or adjacent to one (triangle intersections, the
-//     position of u in N+(w)).
-// Replicated halo rows therefore serve completion checks without contributing counts.  Sums of
-// anchor statistics are additive over partitions; per-edge triangle counts t_e receive contributions
-// from several partitions and are summed into one global array before sum_e C(t_e, 2) is formed.
-// The degree sums and the closure are evaluated once at the end, so every count is exact.
+// The host builds the simple graph in global rank order (rank = (degree, id)).  Every anchor has a
+// canonical owner certificate taken from its globally ordered tuple, and each device block counts
+// exactly the anchors it owns over a halo that holds every list those anchors read:
+//   * triangle / 4-clique / t_e anchors {u < v < w} belong to the rank range of u.  A triangle block
+//     for the range R holds the out-lists N+(v) of every v in R or in N+(R) (1 hop) and their t_e.
+//   * wedge (4-cycle) anchors (u top, x opposite, both middles below u) belong to the pair (rank range
+//     of u, x-slice of x): Sum_x C(cnt(x), 2) is additive over disjoint slices of x.  A wedge block
+//     for (R, X) holds the lower lists N-(u) of the roots u in R and, for every lower neighbour w of
+//     such a root, the part of w's row inside X below R's end (2 hops through lower-ranked vertices).
+// Replicated halo lists serve completion checks without contributing counts.  Per-edge triangle
+// counts t_e receive contributions from several triangle blocks and are summed into one global
+// array before Sum_e C(t_e, 2); the degree sums and the closure are evaluated once at the end, so
+// every count is exact.  Ranges are cut by one linear sweep each, as long as the exact halo size
+// fits the budget; a single vertex (or x-value) whose halo does not fit gives HARP_ENOMEM.
 #include <algorithm>
 #include <cstring>
-#include <utility>
 #include <new>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "harp_internal.cuh"
@@ -87,12 +86,17 @@ struct RankGraph {
     std::vector<int64_t> off;
     std::vector<int32_t> cols;
     std::vector<int32_t> deg, dplus;  // by rank
-    std::vector<int64_t> offp;        // out-arc numbering: N+(r) holds global out-arcs offp[r] ..
+    std::vector<int64_t> offp;        // global out-arc numbering: N+(r) holds out-arcs offp[r] ..
+    int64_t n1 = 0;                   // first rank of degree >= 2
 };
 
 harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst, RankGraph& g) {
     std::vector<uint64_t> keys;
-    keys.reserve((size_t)m_in);
+    try {
+        keys.reserve((size_t)m_in);
+    } catch (...) {
+        return HARP_ENOMEM;
+    }
     const int b = bits_of((uint64_t)n);
     for (int64_t e = 0; e < m_in; ++e) {
         const int32_t u = src[e], v = dst[e];
@@ -120,7 +124,11 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     std::vector<int32_t> rank((size_t)n);
     for (int64_t v = 0; v < n; ++v) rank[(size_t)v] = (int32_t)start[(size_t)deg0[(size_t)v]]++;
     std::vector<uint64_t> arcs;
-    arcs.reserve(2 * keys.size());
+    try {
+        arcs.reserve(2 * keys.size());
+    } catch (...) {
+        return HARP_ENOMEM;
+    }
     for (uint64_t k : keys) {
         const uint64_t a = (uint64_t)rank[k >> b], c = (uint64_t)rank[k & lowmask];
         arcs.push_back((a << 32) | c);
@@ -134,13 +142,16 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
         g.off[(arcs[i] >> 32) + 1]++;
         g.cols[i] = (int32_t)(arcs[i] & 0xffffffffull);
     }
+    std::vector<uint64_t>().swap(arcs);
     for (int64_t r = 0; r < n; ++r) g.off[(size_t)r + 1] += g.off[(size_t)r];
     g.deg.resize((size_t)n);
     g.dplus.resize((size_t)n);
     g.offp.assign((size_t)n + 1, 0);
+    g.n1 = n;
     for (int64_t r = 0; r < n; ++r) {
         const int64_t lo = g.off[(size_t)r], hi = g.off[(size_t)r + 1];
         g.deg[(size_t)r] = (int32_t)(hi - lo);
+        if (g.n1 == n && hi - lo >= 2) g.n1 = r;
         const int64_t split = std::upper_bound(g.cols.begin() + lo, g.cols.begin() + hi, (int32_t)r) -
                               (g.cols.begin() + lo);
         g.dplus[(size_t)r] = (int32_t)(hi - lo - split);
@@ -164,85 +175,398 @@ uint64_t choose3_h(uint64_t x) {
     return f[0] * f[1] * f[2];
 }
 
-// One partition's halo, laid out like the kernels' rank-order arrays (global ids, empty rows for
-// vertices outside the halo).
-struct Halo {
-    std::vector<int64_t> off, offp;
-    std::vector<int32_t> cols, colsp;
-    std::vector<int64_t> gpos;  // for every local out-arc row start: global out-arc id of N+(v)[0]
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device bytes of a triangle block: per-vertex arrays (offp, deg, dplus, queues), out-lists and t_e,
+// the fallback scratch and the accumulators.
+size_t tri_block_bytes(int64_t n, int64_t out_arcs, int64_t fb_scratch) {
+    const int64_t nn = n > 0 ? n : 1, oa = out_arcs > 0 ? out_arcs : 1;
+    return align256(8 * (size_t)(nn + 1)) + 4 * align256(4 * (size_t)nn) + 2 * align256(4 * (size_t)oa) +
+           align256((size_t)fb_scratch) + align256(8 * (size_t)kOutLen);
+}
+
+// Device bytes of a wedge block: per-vertex arrays (off, loff, win_prefix, deg, dplus, fpos, queues),
+// sliced rows, lower lists and their reverse positions, scan scratch and accumulators.
+size_t wedge_block_bytes(int64_t n, int64_t row_arcs, int64_t list_arcs) {
+    const int64_t nn = n > 0 ? n : 1, ra = row_arcs > 0 ? row_arcs : 1, la = list_arcs > 0 ? list_arcs : 1;
+    return 3 * align256(8 * (size_t)(nn + 1)) + 3 * align256(4 * (size_t)nn) + 2 * align256(8 * (size_t)nn) +
+           align256(4 * (size_t)ra) + 2 * align256(4 * (size_t)la) + align256(8 * (size_t)kGInfo) +
+           align256(8 * (scan_tmp_needed(nn) + 64)) + align256(8 * (size_t)kOutLen);
+}
+
+// Carve consecutive 256-byte aligned arrays out of one allocation.
+struct Carver {
+    unsigned char* p;
+    template <typename T>
+    T* take(size_t count) {
+        T* r = reinterpret_cast<T*>(p);
+        p += align256(sizeof(T) * (count > 0 ? count : 1));
+        return r;
+    }
 };
 
-void build_halo(const RankGraph& g, int64_t lo, int64_t hi, Halo& h) {
+// ------------------------------------------------------------------------------------------------
+// Triangle blocks: rank ranges R, halo = out-lists of R and N+(R).
+// ------------------------------------------------------------------------------------------------
+struct TriBlock {
+    int64_t lo, hi;
+};
+
+// Out-neighbour k of r (k < dplus[r]): the row suffix.
+inline int32_t out_nbr(const RankGraph& g, int64_t r, int64_t k) {
+    return g.cols[(size_t)(g.off[(size_t)r + 1] - g.dplus[(size_t)r] + k)];
+}
+
+// One sweep: extend the range while its exact halo (distinct out-lists) fits the budget.
+harp_status cut_triangle_ranges(const RankGraph& g, uint64_t budget, int32_t parts, int64_t fb_scratch,
+                                std::vector<TriBlock>& out, uint64_t& peak) {
     const int64_t n = g.n;
-    std::vector<uint8_t> inH((size_t)n, 0), inO((size_t)n, 0);
-    for (int64_t u = lo; u < hi; ++u) {
-        inH[(size_t)u] = 1;
-        inO[(size_t)u] = 1;
-        for (int64_t a = g.off[(size_t)u]; a < g.off[(size_t)u + 1]; ++a) {
-            const int32_t x = g.cols[(size_t)a];
-            inO[(size_t)x] = 1;             // neighbours: their out-lists (both directions)
-            if (x < u) inH[(size_t)x] = 1;  // lower neighbours: their rows (wedge prefixes)
+    std::vector<uint8_t> mark((size_t)n, 0);
+    std::vector<int32_t> touched;
+    auto extent = [&](int64_t lo, int64_t hi) {  // exact out-arcs of the halo of [lo, hi)
+        int64_t outs = 0;
+        touched.clear();
+        auto add = [&](int32_t v) {
+            if (!mark[(size_t)v]) {
+                mark[(size_t)v] = 1;
+                touched.push_back(v);
+                outs += g.dplus[(size_t)v];
+            }
+        };
+        for (int64_t u = lo; u < hi; ++u) {
+            add((int32_t)u);
+            for (int64_t k = 0; k < g.dplus[(size_t)u]; ++k) add(out_nbr(g, u, k));
         }
-    }
-    h.off.assign((size_t)n + 1, 0);
-    h.offp.assign((size_t)n + 1, 0);
-    for (int64_t v = 0; v < n; ++v) {
-        int64_t len = 0;
-        if (inH[(size_t)v]) {
-            const auto b = g.cols.begin() + g.off[(size_t)v], e = g.cols.begin() + g.off[(size_t)v + 1];
-            len = std::lower_bound(b, e, (int32_t)hi) - b;  // truncated below the range's upper bound
-        }
-        h.off[(size_t)v + 1] = h.off[(size_t)v] + len;
-        h.offp[(size_t)v + 1] = h.offp[(size_t)v] + (inO[(size_t)v] ? g.dplus[(size_t)v] : 0);
-    }
-    h.cols.resize((size_t)h.off[(size_t)n]);
-    h.colsp.resize((size_t)h.offp[(size_t)n]);
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t len = h.off[(size_t)v + 1] - h.off[(size_t)v];
-        if (len) std::memcpy(&h.cols[(size_t)h.off[(size_t)v]], &g.cols[(size_t)g.off[(size_t)v]], sizeof(int32_t) * (size_t)len);
-        const int64_t lp = h.offp[(size_t)v + 1] - h.offp[(size_t)v];
-        if (lp)
-            std::memcpy(&h.colsp[(size_t)h.offp[(size_t)v]], &g.cols[(size_t)(g.off[(size_t)v + 1] - lp)],
-                        sizeof(int32_t) * (size_t)lp);
-    }
-}
-
-// Device bytes a partition with this many halo arcs and out-arcs needs (the layout the counting
-// kernels use).
-size_t halo_bytes(int64_t n, int64_t arcs, int64_t out_arcs) {
-    Workspace probe;
-    const int64_t mws = std::max((arcs + 1) / 2, out_arcs);
-    return ws_layout(probe, nullptr, n, mws);
-}
-
-// The size of build_halo's result for [lo, hi) without copying it: (row arcs, out-arcs).  Monotone in
-// hi for a fixed lo (a longer range adds rows and raises the truncation bound).
-std::pair<int64_t, int64_t> halo_extent(const RankGraph& g, int64_t lo, int64_t hi, std::vector<uint8_t>& inH,
-                                        std::vector<uint8_t>& inO, std::vector<int32_t>& touched) {
-    touched.clear();
-    auto mark = [&](std::vector<uint8_t>& f, int32_t v, uint8_t bit) {
-        if (!(inH[(size_t)v] | inO[(size_t)v])) touched.push_back(v);
-        f[(size_t)v] |= bit;
+        for (int32_t v : touched) mark[(size_t)v] = 0;
+        return outs;
     };
-    for (int64_t u = lo; u < hi; ++u) {
-        mark(inH, (int32_t)u, 1);
-        mark(inO, (int32_t)u, 1);
-        for (int64_t a = g.off[(size_t)u]; a < g.off[(size_t)u + 1]; ++a) {
-            const int32_t x = g.cols[(size_t)a];
-            mark(inO, x, 1);
-            if (x < u) mark(inH, x, 1);
+    if (parts > 0) {
+        for (int32_t k = 0; k < parts; ++k) {
+            const TriBlock b{n * k / parts, n * (k + 1) / parts};
+            peak = std::max<uint64_t>(peak, tri_block_bytes(n, extent(b.lo, b.hi), fb_scratch));
+            out.push_back(b);
+        }
+        return HARP_OK;
+    }
+    int64_t lo = 0;
+    while (lo < n) {
+        int64_t outs = 0, hi = lo;
+        touched.clear();
+        while (hi < n) {
+            const int64_t outs0 = outs;
+            const size_t t0 = touched.size();
+            auto add = [&](int32_t v) {
+                if (!mark[(size_t)v]) {
+                    mark[(size_t)v] = 1;
+                    touched.push_back(v);
+                    outs += g.dplus[(size_t)v];
+                }
+            };
+            add((int32_t)hi);
+            for (int64_t k = 0; k < g.dplus[(size_t)hi]; ++k) add(out_nbr(g, hi, k));
+            if (tri_block_bytes(n, outs, fb_scratch) > budget) {
+                if (hi == lo) {
+                    for (int32_t v : touched) mark[(size_t)v] = 0;
+                    return HARP_ENOMEM;  // this vertex alone does not fit
+                }
+                for (size_t k = t0; k < touched.size(); ++k) mark[(size_t)touched[k]] = 0;  // undo hi
+                touched.resize(t0);
+                outs = outs0;
+                break;
+            }
+            ++hi;
+        }
+        for (int32_t v : touched) mark[(size_t)v] = 0;
+        peak = std::max<uint64_t>(peak, tri_block_bytes(n, outs, fb_scratch));
+        out.push_back({lo, hi});
+        lo = hi;
+    }
+    return HARP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Wedge blocks: rank ranges R of roots, each cut into x-slices X.
+// ------------------------------------------------------------------------------------------------
+struct WedgeBlock {
+    int64_t lo, hi;    // roots
+    int64_t xlo, xhi;  // opposite vertices
+};
+
+// Lower-list arcs of root u that enter a wedge block: its whole N-(u) when it can root a wedge.
+int64_t list_arcs_of(const RankGraph& g, int64_t u) {
+    const int64_t dm = g.deg[(size_t)u] - g.dplus[(size_t)u];
+    return dm >= 2 ? dm : 0;
+}
+
+harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts, std::vector<WedgeBlock>& out,
+                             uint64_t& peak) {
+    const int64_t n = g.n;
+    std::vector<std::pair<int64_t, int64_t>> ranges;
+    const size_t fixed = wedge_block_bytes(n, 0, 0);
+    if (parts > 0) {
+        for (int32_t k = 0; k < parts; ++k) ranges.push_back({n * k / parts, n * (k + 1) / parts});
+    } else {
+        // roots: their lists may take a third of what the per-vertex arrays leave
+        if (fixed > budget) return HARP_ENOMEM;
+        const uint64_t list_budget = (budget - fixed) / 3;
+        int64_t lo = 0;
+        while (lo < n) {
+            int64_t hi = lo, la = 0;
+            while (hi < n) {
+                const int64_t add = list_arcs_of(g, hi);
+                if (8 * (uint64_t)(la + add) > list_budget && hi > lo) break;
+                la += add;
+                ++hi;
+            }
+            if (8 * (uint64_t)la > list_budget) return HARP_ENOMEM;
+            ranges.push_back({lo, hi});
+            lo = hi;
         }
     }
-    int64_t arcs = 0, outs = 0;
-    for (int32_t v : touched) {
-        if (inH[(size_t)v]) {
-            const auto b = g.cols.begin() + g.off[(size_t)v], e = g.cols.begin() + g.off[(size_t)v + 1];
-            arcs += std::lower_bound(b, e, (int32_t)hi) - b;
+    // x-slices per root range: a histogram, by x, of the row elements the block would hold
+    std::vector<int64_t> hist((size_t)n, 0);
+    std::vector<uint8_t> mark((size_t)n, 0);
+    std::vector<int32_t> lower;
+    for (const auto& r : ranges) {
+        const int64_t lo = r.first, hi = r.second;
+        if (lo >= hi) continue;
+        int64_t la = 0;
+        lower.clear();
+        for (int64_t u = lo; u < hi; ++u) {
+            const int64_t dm = list_arcs_of(g, u);
+            la += dm;
+            for (int64_t a = 0; a < dm; ++a) {
+                const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
+                if (!mark[(size_t)w]) {
+                    mark[(size_t)w] = 1;
+                    lower.push_back(w);
+                }
+            }
         }
-        if (inO[(size_t)v]) outs += g.dplus[(size_t)v];
-        inH[(size_t)v] = inO[(size_t)v] = 0;
+        const int64_t xa = g.n1, xb = hi;  // opposite vertices of degree >= 2, below the range's end
+        for (int32_t w : lower) {
+            mark[(size_t)w] = 0;
+            const auto b = g.cols.begin() + g.off[(size_t)w], e = g.cols.begin() + g.off[(size_t)w + 1];
+            for (auto it = std::lower_bound(b, e, (int32_t)xa); it != e && *it < xb; ++it) hist[(size_t)*it]++;
+        }
+        if (parts > 0 || xa >= xb) {
+            int64_t rows = 0;
+            for (int64_t x = xa; x < xb; ++x) rows += hist[(size_t)x];
+            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
+            out.push_back({lo, hi, 0, n});
+        } else {
+            int64_t x0 = xa, rows = 0;
+            for (int64_t x = xa; x < xb; ++x) {
+                const int64_t h = hist[(size_t)x];
+                if (wedge_block_bytes(n, rows + h, la) > budget) {
+                    if (x == x0) {
+                        for (int64_t y = xa; y < xb; ++y) hist[(size_t)y] = 0;
+                        return HARP_ENOMEM;  // one x-value's rows alone do not fit
+                    }
+                    peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
+                    out.push_back({lo, hi, x0 == xa ? 0 : x0, x});
+                    x0 = x;
+                    rows = 0;
+                }
+                rows += h;
+            }
+            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
+            out.push_back({lo, hi, x0 == xa ? 0 : x0, n});
+        }
+        for (int64_t x = xa; x < xb; ++x) hist[(size_t)x] = 0;
     }
-    return {arcs, outs};
+    return HARP_OK;
+}
+
+// The device results of all blocks.
+struct PartSums {
+    uint64_t T = 0, K4 = 0, C4 = 0, PAWSUM = 0;
+    std::vector<uint32_t> te;  // global out-arc numbering
+};
+
+harp_status check_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return HARP_OK;
+    record_cuda_error(e);
+    return e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
+}
+
+harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev, int64_t fb, cudaStream_t s,
+                               PartSums& sum, uint64_t& h2d, uint64_t& halo_arcs) {
+    const int64_t n = g.n;
+    // halo: out-lists of R and N+(R), local numbering in rank order
+    std::vector<uint8_t> in((size_t)n, 0);
+    for (int64_t u = blk.lo; u < blk.hi; ++u) {
+        in[(size_t)u] = 1;
+        for (int64_t k = 0; k < g.dplus[(size_t)u]; ++k) in[(size_t)out_nbr(g, u, k)] = 1;
+    }
+    std::vector<int64_t> offp((size_t)n + 1, 0);
+    for (int64_t v = 0; v < n; ++v) offp[(size_t)v + 1] = offp[(size_t)v] + (in[(size_t)v] ? g.dplus[(size_t)v] : 0);
+    const int64_t outs = offp[(size_t)n];
+    std::vector<int32_t> colsp((size_t)(outs > 0 ? outs : 1));
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t len = offp[(size_t)v + 1] - offp[(size_t)v];
+        if (len)
+            std::memcpy(&colsp[(size_t)offp[(size_t)v]], &g.cols[(size_t)(g.off[(size_t)v + 1] - len)],
+                        sizeof(int32_t) * (size_t)len);
+    }
+    halo_arcs += (uint64_t)outs;
+    const size_t bytes = tri_block_bytes(n, outs, fb);
+    void* base = nullptr;
+    HARP_TRY(check_cuda(cudaMallocAsync(&base, bytes, s)));
+    Carver c{static_cast<unsigned char*>(base)};
+    Workspace ws;
+    ws.offp = c.take<int64_t>((size_t)n + 1);
+    ws.deg = c.take<int32_t>((size_t)n);
+    ws.dplus = c.take<int32_t>((size_t)n);
+    ws.q_tri = c.take<int32_t>((size_t)n);
+    ws.q_mid = c.take<int32_t>((size_t)n);
+    ws.colsp = c.take<int32_t>((size_t)outs);
+    ws.te = c.take<uint32_t>((size_t)outs);
+    c.take<unsigned char>((size_t)fb);  // the fallback allocates its own scratch: counted in the budget here
+    ws.acc = c.take<uint64_t>(kOutLen);
+    ws.own_lo = blk.lo;
+    ws.own_hi = blk.hi;
+    cudaError_t e = cudaMemcpyAsync(ws.offp, offp.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && outs)
+        e = cudaMemcpyAsync(ws.colsp, colsp.data(), sizeof(int32_t) * (size_t)outs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws.deg, g.deg.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.dplus, g.dplus.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.te, 0, sizeof(uint32_t) * (size_t)(outs > 0 ? outs : 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s);
+    harp_status st = check_cuda(e);
+    h2d += 8 * (uint64_t)(n + 1) + 4 * (uint64_t)outs + 8 * (uint64_t)n;
+    harp_csr view;  // the kernels' view: global n, m and maximum degree
+    view.device = dev;
+    view.stream = s;
+    view.n = n;
+    view.m = g.m;
+    view.max_deg = n ? *std::max_element(g.deg.begin(), g.deg.end()) : 0;
+    harp_plan plan;
+    normalise_plan(nullptr, &plan);
+    if (st == HARP_OK && n > 0) st = count_triangles_k4(&view, ws, plan, s);
+    std::vector<uint32_t> te_local((size_t)outs);
+    uint64_t acc[kOutLen] = {0};
+    if (st == HARP_OK) {
+        e = cudaMemcpyAsync(acc, ws.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && outs)
+            e = cudaMemcpyAsync(te_local.data(), ws.te, sizeof(uint32_t) * (size_t)outs, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        st = check_cuda(e);
+        if (st == HARP_OK && acc[ACC_ERR]) st = HARP_EDEVICE;
+    }
+    cudaFreeAsync(base, s);
+    if (st != HARP_OK) return st;
+    sum.T += acc[ACC_T];
+    sum.K4 += acc[ACC_K4];
+    sum.PAWSUM += acc[ACC_PAWSUM];
+    for (int64_t v = 0; v < n; ++v) {  // local out-arcs -> global out-arc ids
+        const int64_t lb = offp[(size_t)v], len = offp[(size_t)v + 1] - lb, gb = g.offp[(size_t)v];
+        for (int64_t k = 0; k < len; ++k) sum.te[(size_t)(gb + k)] += te_local[(size_t)(lb + k)];
+    }
+    return HARP_OK;
+}
+
+harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, cudaStream_t s, PartSums& sum,
+                            uint64_t& h2d, uint64_t& halo_arcs) {
+    const int64_t n = g.n;
+    // lower lists of the roots in R that can root a wedge
+    std::vector<int64_t> loff((size_t)n + 1, 0);
+    for (int64_t u = 0; u < n; ++u)
+        loff[(size_t)u + 1] = loff[(size_t)u] + ((u >= blk.lo && u < blk.hi) ? list_arcs_of(g, u) : 0);
+    const int64_t la = loff[(size_t)n];
+    std::vector<int32_t> lcols((size_t)(la > 0 ? la : 1));
+    std::vector<uint8_t> in((size_t)n, 0);
+    for (int64_t u = blk.lo; u < blk.hi; ++u) {
+        const int64_t len = loff[(size_t)u + 1] - loff[(size_t)u];
+        for (int64_t a = 0; a < len; ++a) {
+            const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
+            lcols[(size_t)(loff[(size_t)u] + a)] = w;
+            in[(size_t)w] = 1;
+        }
+    }
+    // rows of the lower neighbours, restricted to the slice [xa, xb) of opposite vertices
+    const int64_t xa = std::max<int64_t>(blk.xlo, g.n1), xb = std::min<int64_t>(blk.xhi, blk.hi);
+    std::vector<int64_t> off((size_t)n + 1, 0), rb((size_t)n, 0);
+    for (int64_t w = 0; w < n; ++w) {
+        int64_t len = 0;
+        if (in[(size_t)w] && xa < xb) {
+            const auto b = g.cols.begin() + g.off[(size_t)w], e = g.cols.begin() + g.off[(size_t)w + 1];
+            const auto p = std::lower_bound(b, e, (int32_t)xa);
+            rb[(size_t)w] = p - g.cols.begin();
+            len = std::lower_bound(p, e, (int32_t)xb) - p;
+        }
+        off[(size_t)w + 1] = off[(size_t)w] + len;
+    }
+    const int64_t ra = off[(size_t)n];
+    if (la == 0 || ra == 0) return HARP_OK;  // no root or no opposite vertex: nothing to count here
+    std::vector<int32_t> cols((size_t)ra);
+    for (int64_t w = 0; w < n; ++w) {
+        const int64_t len = off[(size_t)w + 1] - off[(size_t)w];
+        if (len)
+            std::memcpy(&cols[(size_t)off[(size_t)w]], &g.cols[(size_t)rb[(size_t)w]], sizeof(int32_t) * (size_t)len);
+    }
+    halo_arcs += (uint64_t)(ra + la);
+    const size_t bytes = wedge_block_bytes(n, ra, la);
+    void* base = nullptr;
+    HARP_TRY(check_cuda(cudaMallocAsync(&base, bytes, s)));
+    Carver c{static_cast<unsigned char*>(base)};
+    Workspace ws;
+    ws.off = c.take<int64_t>((size_t)n + 1);
+    int64_t* d_loff = c.take<int64_t>((size_t)n + 1);
+    ws.win_prefix = c.take<int64_t>((size_t)n + 1);
+    ws.deg = c.take<int32_t>((size_t)n);
+    ws.dplus = c.take<int32_t>((size_t)n);
+    ws.fpos = c.take<int32_t>((size_t)n);
+    ws.q_mid = c.take<int32_t>(2 * (size_t)n);
+    ws.q_win = c.take<int32_t>(2 * (size_t)n);
+    ws.cols = c.take<int32_t>((size_t)ra);
+    int32_t* d_lcols = c.take<int32_t>((size_t)la);
+    ws.rev = c.take<int32_t>((size_t)la);
+    ws.ginfo = c.take<int64_t>(kGInfo);
+    ws.scan_tmp_len = scan_tmp_needed(n > 0 ? n : 1) + 64;
+    ws.scan_tmp = c.take<int64_t>(ws.scan_tmp_len);
+    ws.acc = c.take<uint64_t>(kOutLen);
+    ws.bpos = nullptr;  // boundaries searched per window (no per-vertex table)
+    ws.loff = d_loff;
+    ws.lcols = d_lcols;
+    ws.lower_arcs = la;
+    ws.own_lo = blk.lo;
+    ws.own_hi = blk.hi;
+    ws.x_lo = xa;
+    ws.x_hi = xb;
+    cudaError_t e = cudaMemcpyAsync(ws.off, off.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_loff, loff.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws.cols, cols.data(), sizeof(int32_t) * (size_t)ra, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_lcols, lcols.data(), sizeof(int32_t) * (size_t)la, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws.deg, g.deg.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.dplus, g.dplus.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s);
+    harp_status st = check_cuda(e);
+    h2d += 16 * (uint64_t)(n + 1) + 4 * (uint64_t)(ra + la) + 8 * (uint64_t)n;
+    harp_csr view;
+    view.device = dev;
+    view.stream = s;
+    view.n = n;
+    view.m = g.m;
+    view.max_deg = 0;
+    harp_plan plan;
+    normalise_plan(nullptr, &plan);
+    if (st == HARP_OK) st = count_wedge_c4(&view, ws, plan, s);
+    uint64_t acc[kOutLen] = {0};
+    if (st == HARP_OK) {
+        e = cudaMemcpyAsync(acc, ws.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        st = check_cuda(e);
+        if (st == HARP_OK && acc[ACC_ERR]) st = HARP_EDEVICE;
+    }
+    cudaFreeAsync(base, s);
+    if (st != HARP_OK) return st;
+    sum.C4 += acc[ACC_C4];
+    return HARP_OK;
 }
 
 }  // namespace
@@ -264,122 +588,26 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
         HARP_CK(cudaMemGetInfo(&fr, &tot));
         budget_bytes = fr / 2;
     }
-    // Cut rank space into ranges: a fixed count if asked, otherwise greedily, each range the longest
-    // whose halo fits the budget (binary search; the halo size is monotone in the range's end).  A
-    // single vertex whose halo exceeds the budget cannot be counted under it: HARP_ENOMEM.
-    std::vector<int64_t> cuts{0};
-    if (parts > 0) {
-        for (int32_t k = 1; k < parts; ++k) cuts.push_back(n * k / parts);
-        cuts.push_back(n);
-    } else {
-        std::vector<uint8_t> inH((size_t)n, 0), inO((size_t)n, 0);
-        std::vector<int32_t> touched;
-        auto fits = [&](int64_t lo, int64_t hi) {
-            const auto ext = halo_extent(g, lo, hi, inH, inO, touched);
-            return halo_bytes(n, ext.first, ext.second) <= budget_bytes;
-        };
-        int64_t lo = 0;
-        while (lo < n) {
-            if (!fits(lo, lo + 1)) return HARP_ENOMEM;
-            int64_t good = lo + 1, bad = n + 1;  // fits(lo, good) holds; fits(lo, bad) does not (n + 1: none)
-            if (fits(lo, n)) good = n;
-            else bad = n;
-            while (bad - good > 1) {
-                const int64_t mid = good + (bad - good) / 2;
-                if (fits(lo, mid)) good = mid;
-                else bad = mid;
-            }
-            cuts.push_back(good);
-            lo = good;
-        }
-    }
-    std::vector<uint32_t> te_global((size_t)g.offp[(size_t)n], 0);
-    uint64_t T = 0, K4 = 0, C4 = 0, PAWSUM = 0;
-    uint64_t host_bytes = 0, device_peak = 0, halo_arcs = 0;
+    int64_t dmax = 1;
+    while (dmax * dmax < 2 * g.m) ++dmax;
+    const int64_t fb = 152 * 8 * (dmax + 32) * 4;  // the triangle fallback's per-warp frontier buffers
+    std::vector<TriBlock> tri;
+    std::vector<WedgeBlock> wedge;
+    uint64_t device_peak = 0, h2d = 0, halo_arcs = 0;
+    HARP_TRY(cut_triangle_ranges(g, budget_bytes, parts, fb, tri, device_peak));
+    HARP_TRY(cut_wedge_blocks(g, budget_bytes, parts, wedge, device_peak));
+    PartSums sum;
+    sum.te.assign((size_t)g.offp[(size_t)n], 0);
     cudaStream_t s = nullptr;
     HARP_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     harp_status st = HARP_OK;
-    for (size_t k = 0; k + 1 < cuts.size() && st == HARP_OK; ++k) {
-        const int64_t lo = cuts[k], hi = cuts[k + 1];
-        if (lo >= hi) continue;
-        Halo h;
-        build_halo(g, lo, hi, h);
-        const int64_t arcs = (int64_t)h.cols.size(), out_arcs = (int64_t)h.colsp.size();
-        halo_arcs += (uint64_t)(arcs + out_arcs);
-        const int64_t mws = std::max((arcs + 1) / 2, out_arcs);
-        Workspace probe;
-        const size_t bytes = ws_layout(probe, nullptr, n, mws);
-        if (bytes > device_peak) device_peak = bytes;
-        void* base = nullptr;
-        cudaError_t e = cudaMallocAsync(&base, bytes, s);
-        if (e != cudaSuccess) {
-            record_cuda_error(e);
-            st = e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
-            break;
-        }
-        Workspace ws;
-        ws_layout(ws, static_cast<unsigned char*>(base), n, mws);
-        ws.own_lo = lo;
-        ws.own_hi = hi;
-        ws.arcs = arcs;
-        // host -> device: the halo and the global degree arrays (the transfer Table IV measures)
-        e = cudaMemcpyAsync(ws.off, h.off.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && arcs)
-            e = cudaMemcpyAsync(ws.cols, h.cols.data(), sizeof(int32_t) * (size_t)arcs, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ws.offp, h.offp.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && out_arcs)
-            e = cudaMemcpyAsync(ws.colsp, h.colsp.data(), sizeof(int32_t) * (size_t)out_arcs, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ws.deg, g.deg.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ws.dplus, g.dplus.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ws.te, 0, sizeof(uint32_t) * (size_t)(out_arcs > 0 ? out_arcs : 1), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s);
-        host_bytes += 8 * (uint64_t)(n + 1) * 2 + 4 * (uint64_t)(arcs + out_arcs) + 8 * (uint64_t)n;
-        if (e != cudaSuccess) {
-            record_cuda_error(e);
-            st = HARP_ECUDA;
-        }
-        harp_csr view;  // the kernels' view: global n and m (m sizes the hub fallback), halo arrays
-        view.device = dev;
-        view.stream = s;
-        view.n = n;
-        view.m = g.m;
-        int32_t maxd = 0;
-        for (int32_t d : g.deg) maxd = d > maxd ? d : maxd;
-        view.max_deg = maxd;
-        view.off = ws.off;
-        view.cols = ws.cols;
-        harp_plan plan;
-        normalise_plan(nullptr, &plan);
-        if (st == HARP_OK && n > 0) st = count_triangles_k4(&view, ws, plan, s);
-        if (st == HARP_OK && n > 0) st = count_wedge_c4(&view, ws, plan, s);
-        std::vector<uint32_t> te_local((size_t)out_arcs);
-        uint64_t acc[kOutLen];
-        if (st == HARP_OK) {
-            e = cudaMemcpyAsync(acc, ws.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && out_arcs)
-                e = cudaMemcpyAsync(te_local.data(), ws.te, sizeof(uint32_t) * (size_t)out_arcs, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) {
-                record_cuda_error(e);
-                st = HARP_ECUDA;
-            } else if (acc[ACC_ERR]) {
-                st = HARP_EDEVICE;
-            }
-        }
-        cudaFreeAsync(base, s);
-        if (st != HARP_OK) break;
-        T += acc[ACC_T];
-        K4 += acc[ACC_K4];
-        C4 += acc[ACC_C4];
-        PAWSUM += acc[ACC_PAWSUM];
-        for (int64_t v = 0; v < n; ++v) {  // local out-arcs -> global out-arc ids
-            const int64_t lb = h.offp[(size_t)v], len = h.offp[(size_t)v + 1] - lb;
-            const int64_t gb = g.offp[(size_t)v];
-            for (int64_t k2 = 0; k2 < len; ++k2) te_global[(size_t)(gb + k2)] += te_local[(size_t)(lb + k2)];
-        }
+    for (size_t k = 0; k < tri.size() && st == HARP_OK; ++k) {
+        if (tri[k].lo >= tri[k].hi || g.m == 0) continue;
+        st = run_triangle_block(g, tri[k], dev, fb, s, sum, h2d, halo_arcs);
+    }
+    for (size_t k = 0; k < wedge.size() && st == HARP_OK; ++k) {
+        if (wedge[k].lo >= wedge[k].hi || g.m == 0) continue;
+        st = run_wedge_block(g, wedge[k], dev, s, sum, h2d, halo_arcs);
     }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -389,13 +617,14 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     for (int64_t r = 0; r < n; ++r) {
         const uint64_t dr = (uint64_t)g.deg[(size_t)r];
         S += choose3_h(dr);
-        for (int64_t a = g.off[(size_t)r + 1] - g.dplus[(size_t)r]; a < g.off[(size_t)r + 1]; ++a)
-            PW += (dr - 1) * ((uint64_t)g.deg[(size_t)g.cols[(size_t)a]] - 1);
+        for (int64_t k = 0; k < g.dplus[(size_t)r]; ++k)
+            PW += (dr - 1) * ((uint64_t)g.deg[(size_t)out_nbr(g, r, k)] - 1);
     }
-    for (uint32_t t : te_global) D += choose2_h(t);
-    const uint64_t P = PW - 3 * T, pawn = PAWSUM - 6 * T;
+    for (uint32_t t : sum.te) D += choose2_h(t);
+    const uint64_t T = sum.T, K4 = sum.K4;
+    const uint64_t P = PW - 3 * T, pawn = sum.PAWSUM - 6 * T;
     const uint64_t diamond = D - 6 * K4;
-    const uint64_t c4 = C4 - diamond - 3 * K4;
+    const uint64_t c4 = sum.C4 - diamond - 3 * K4;
     const uint64_t paw = pawn - 4 * diamond - 12 * K4;
     const uint64_t path = P - 2 * paw - 4 * c4 - 6 * diamond - 12 * K4;
     const uint64_t star = S - paw - 2 * diamond - 4 * K4;
@@ -406,10 +635,10 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     counts_out[HARP_DIAMOND] = diamond;
     counts_out[HARP_CLIQUE4] = K4;
     if (stats) {
-        stats->partitions = (int64_t)cuts.size() - 1;
+        stats->partitions = (int64_t)(tri.size() + wedge.size());
         stats->m = g.m;
         stats->halo_arcs = (int64_t)halo_arcs;
-        stats->h2d_bytes = host_bytes;
+        stats->h2d_bytes = h2d;
         stats->device_peak_bytes = device_peak;
     }
     return HARP_OK;

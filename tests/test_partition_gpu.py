@@ -43,7 +43,7 @@ def test_forced_partitions_match_whole_graph(harp, k):
         whole = harp.count4_edges(g.n, g.src, g.dst)
         got, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34, parts=k)
         assert got.tolist() == whole.tolist(), (g.name, k)
-        assert st["partitions"] == k
+        assert st["partitions"] == 2 * k               # k triangle ranges and k wedge ranges
 
 
 @pytest.mark.parametrize("make", [lambda: graphgen.rmat(15, 16, seed=4), lambda: graphgen.rgg(40000, 16, 9),
@@ -52,14 +52,14 @@ def test_budget_sized_partitions_and_oracle(harp, make):
     g = make()
     want = O.count4_combo(g.n, g.src, g.dst)
     whole, st1 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34)
-    assert st1["partitions"] == 1
+    assert st1["partitions"] == 2                      # one triangle block, one wedge block
     # the largest range of 16 equal ranges fits any range the greedy cut can start (its halo contains
     # the halo of every single vertex of that range); below the whole graph's footprint it must cut
     _, st16 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34, parts=16)
     budget = st16["device_peak_bytes"]
     got, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=budget)
     if budget < st1["device_peak_bytes"]:
-        assert st["partitions"] > 1
+        assert st["partitions"] > 2
     assert st["device_peak_bytes"] <= budget
     assert got.tolist() == whole.tolist() == want.tolist()
     with pytest.raises(harp.HarpError) as ei:    # below every single-vertex halo of the top range
