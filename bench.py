@@ -18,6 +18,11 @@ path (one harp_count4 per graph) over the same graphs; counts are compared graph
 through the continuous-batching server, against plain one-graph-per-launch processing (build + count,
 in arrival order) of the same stream: p50 / p99 latency and edges/s.
 
+`--workload partitioned`: the partitioned large graph (Chung-Lu, exponent 2.1, max expected degree 1e6,
+mean degree 48; n = 5e7 gives about 1.2e9 edges) counted through harp_count4_partitioned under a 24 GiB
+device cap: one JSON line with edges/s over the whole call (host edge list to counts) and the share of
+host-device transfer in it.  `--n` shrinks the graph for trial runs.
+
 --impl reference runs the CPU oracle (plain non-induced counts + containment inversion) on the host
 cores instead: each step counts an R-MAT scale-17 sample of the same family.
 """
@@ -271,6 +276,49 @@ def served_at_rate(harp, np, gs, rate, seed, budget):
             "peak_resident_bytes": st["peak_resident_bytes"]}
 
 
+def run_partitioned(args):
+    """The partitioned large-graph workload: one harp_count4_partitioned call (timed end to end)."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_2607_12074_gb300 import _build, harp
+
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    _build.build()
+    harp.lib()
+    t0 = time.perf_counter()
+    g = graphgen.chung_lu_large(args.n)
+    t_gen = time.perf_counter() - t0
+    budget = int(args.cap_gib * (1 << 30))
+    runs = []
+    for k in range(args.warmup + args.steps):
+        with ClockSampler(local) as clocks:
+            t = time.perf_counter()
+            counts, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=budget)
+            wall = time.perf_counter() - t
+        if k >= args.warmup:
+            runs.append((wall, st, clocks.summary()))
+    wall, st, clk = min(runs, key=lambda r: r[0])
+    m = st["m"]
+    line = {"metric": METRIC, "value": m / wall, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"chung_lu(n={g.n}, gamma=2.1, max expected degree {1e6 * g.n / 5e7:g}, "
+                                   f"mean degree 48, seed 1), partitioned under a {args.cap_gib:g} GiB device cap",
+                       "n": g.n, "m": m, "parallelism": "single", "l2": "inputs larger than L2"},
+            "partition": {"blocks": st["partitions"], "device_peak_bytes": st["device_peak_bytes"],
+                          "halo_arcs": st["halo_arcs"], "h2d_bytes": st["h2d_bytes"], "host_ms": st["host_ms"],
+                          "transfer_ms": st["transfer_ms"], "device_ms": st["device_ms"],
+                          "transfer_share": st["transfer_ms"] / (1000 * wall)},
+            "generate_s": t_gen, "clocks": clk, "counts": [int(x) for x in counts]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,9 +330,14 @@ def main():
     ap.add_argument("--no-meter", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
+    ap.add_argument("--workload", default="plain", choices=("plain", "partitioned"))
+    ap.add_argument("--n", type=int, default=50_000_000, help="vertices of the partitioned workload")
+    ap.add_argument("--cap-gib", type=float, default=24.0, help="device cap of the partitioned workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "partitioned":
+        return run_partitioned(args)
     args.warmup = max(args.warmup, 3)
 
     world, rank, local = dist_env()

@@ -152,10 +152,37 @@ def chung_lu(n: int, gamma: float, max_weight: float, mean_degree: float, seed: 
             lo = mid
     i0 = math.sqrt(lo * hi)
     c = max_weight * i0 ** (-ex)
+    name = f"chung_lu(n={n},gamma={gamma},seed={seed})"
+    if rows is None and n >= 1_000_000:
+        # every row draws from its own stream, so row chunks are independent: generate balanced
+        # chunks on threads (the C call releases the interpreter lock) and concatenate in row order
+        import threading
+        w = c * np.power(np.arange(n, dtype=np.float64) + i0, ex)
+        S = float(w.sum())
+        tail = np.cumsum(w[::-1])[::-1] - w                       # sum_{v > u} w_v
+        expect = np.minimum(w * tail / S, np.arange(n, 0, -1) - 1.0)  # expected edges of row u
+        cum = np.cumsum(expect)
+        parts = max(1, min(64, (os.cpu_count() or 4) * 2))
+        cuts = [0] + [int(np.searchsorted(cum, cum[-1] * k / parts)) for k in range(1, parts)] + [n]
+        cuts = sorted(set(cuts))
+        out = [None] * (len(cuts) - 1)
+
+        def work(k):
+            a, b = cuts[k], cuts[k + 1]
+            est = float(cum[b - 1] - (cum[a - 1] if a > 0 else 0.0))
+            cap = int(est * 1.05 + 6 * math.sqrt(est + 1)) + 1024
+            out[k] = _call_growing(_load().gg_chung_lu, (n, gamma, c, i0, seed, a, b), cap)
+
+        th = [threading.Thread(target=work, args=(k,)) for k in range(len(out))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return Graph(n, np.concatenate([o[0] for o in out]), np.concatenate([o[1] for o in out]), name)
     r0, r1 = rows if rows is not None else (0, n)
     cap = int((r1 - r0) * mean_degree * 0.6) + 1024
     src, dst = _call_growing(_load().gg_chung_lu, (n, gamma, c, i0, seed, r0, r1), cap)
-    return Graph(n, src, dst, f"chung_lu(n={n},gamma={gamma},seed={seed})")
+    return Graph(n, src, dst, name)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -179,6 +206,20 @@ class BatchSpec:
     n: int
     k: float       # mean degree (er, rgg)
     m: int         # edges per new vertex (ba)
+
+
+def chung_lu_large(n: int = 50_000_000, seed: int = 1) -> Graph:
+    """The partitioned large-graph workload: Chung-Lu, exponent 2.1, max expected degree 1e6, mean
+    degree 48 (about 1.2e9 edges at n = 5e7).  Smaller n keeps the shape for trial runs."""
+    return chung_lu(n, 2.1, 1e6 * n / 50_000_000, 48.0, seed)
+
+
+def chung_lu_subsample(n_sub: int = 1_000_000, n_full: int = 50_000_000, seed: int = 1) -> Graph:
+    """Stand-in for the subgraph of ``chung_lu_large`` induced on a uniform n_sub-vertex subset: a
+    vertex keeps each neighbour with probability n_sub / n_full, so the subset is Chung-Lu with the
+    weights scaled by that fraction (max expected degree 1e6 f, mean degree 48 f)."""
+    f = n_sub / n_full
+    return chung_lu(n_sub, 2.1, 1e6 * f, 48.0 * f, seed)
 
 
 def batch_spec(seed: int, n_lo: int = 50, n_hi: int = 20000) -> BatchSpec:

@@ -122,7 +122,10 @@ typedef struct harp_plan {
     uint32_t tri_probe;          /* HARP_PROBE_* for the triangle / 4-clique anchor                */
     uint32_t tri_warp_max;       /* out-degree <= this (<= 32): warp-local mode; above: CTA mode   */
     uint32_t tri_cta_max;        /* out-degree <= this (<= 1024): frontiers staged in shared memory */
-                                 /* (CTA mode); above: unstaged fallback, every extension a miss    */
+                                 /* (CTA mode)                                                      */
+    uint32_t tri_big_max;        /* out-degree <= this (<= 4096), above tri_cta_max: frontiers      */
+                                 /* staged in an L2-resident global scratch; above: unstaged        */
+                                 /* fallback, every extension a miss                                */
     uint32_t c4_warp_max_work;   /* wedge work W(u) <= this: warp-local hash table                 */
     uint32_t c4_cta_max_work;    /* W(u) <= this: CTA hash table; above: CTA windowed counters     */
     uint32_t c4_window_bytes;    /* shared-memory bytes of one dense counter window                */
@@ -240,6 +243,9 @@ typedef struct harp_partition_stats {
     int64_t halo_arcs;           /* arcs copied to the device over all ranges (rows + out-lists)  */
     uint64_t h2d_bytes;          /* host-to-device bytes over all ranges                          */
     uint64_t device_peak_bytes;  /* largest per-range device allocation                           */
+    double host_ms;              /* host work: rank-order graph, range cuts, halo assembly, closure */
+    double transfer_ms;          /* host <-> device copies (CUDA events around the copies)        */
+    double device_ms;            /* counting kernels (CUDA events around the kernels)             */
 } harp_partition_stats;
 
 /* src, dst: HOST int32[m_in] (read only).  budget_bytes: device bytes one range may use (0 = half

@@ -156,7 +156,7 @@ harp_status enqueue_batch(harp_batch* b, const harp_plan& plan, cudaStream_t s) 
 
 bool same_plan(const harp_plan& a, const harp_plan& b) {
     return a.basis == b.basis && a.tri_probe == b.tri_probe && a.tri_warp_max == b.tri_warp_max &&
-           a.tri_cta_max == b.tri_cta_max &&
+           a.tri_cta_max == b.tri_cta_max && a.tri_big_max == b.tri_big_max &&
            a.c4_warp_max_work == b.c4_warp_max_work && a.c4_cta_max_work == b.c4_cta_max_work &&
            a.c4_window_bytes == b.c4_window_bytes && a.flags == b.flags;
 }

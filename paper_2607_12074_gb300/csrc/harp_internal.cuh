@@ -77,6 +77,8 @@ enum : int {
     T_TRI_M = 38,          // ticket of the 512-wide CTA triangle kernel
     ACC_SIG_HITS = 39,     // 4-clique extensions answered by a staged signature frontier
     Q_TRI_FB = 40,         // length of the unstaged-fallback triangle queue
+    Q_TRI_BIG = 41,        // length of the global-staged triangle queue
+    T_TRI_BIG = 42,        // its ticket
     kOutLen = 48
 };
 

@@ -16,6 +16,7 @@
 // every count is exact.  Ranges are cut by one linear sweep each, as long as the exact halo size
 // fits the budget; a single vertex (or x-value) whose halo does not fit gives HARP_ENOMEM.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -26,6 +27,25 @@
 
 namespace harp {
 namespace {
+
+unsigned host_threads() {
+    unsigned nt = std::thread::hardware_concurrency();
+    return nt < 1 ? 1 : (nt > 64 ? 64 : nt);
+}
+
+// f(lo, hi, t) over contiguous slices of [0, n), one per host thread (inline when n is small).
+template <typename F>
+void parallel_for(int64_t n, F&& f) {
+    const unsigned nt = n < (1 << 16) ? 1 : host_threads();
+    if (nt == 1) {
+        f((int64_t)0, n, 0u);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] { f(n * (int64_t)t / (int64_t)nt, n * (int64_t)(t + 1) / (int64_t)nt, t); });
+    for (auto& x : th) x.join();
+}
 
 // LSD radix sort of 64-bit keys on the host (16-bit digits over the significant bits), threads split
 // every pass by contiguous slices so the sort stays stable.
@@ -93,28 +113,40 @@ struct RankGraph {
 harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst, RankGraph& g) {
     std::vector<uint64_t> keys;
     try {
-        keys.reserve((size_t)m_in);
+        keys.resize((size_t)m_in);
     } catch (...) {
         return HARP_ENOMEM;
     }
     const int b = bits_of((uint64_t)n);
-    for (int64_t e = 0; e < m_in; ++e) {
-        const int32_t u = src[e], v = dst[e];
-        if (u < 0 || v < 0 || u >= n || v >= n) return HARP_EINVAL;
-        if (u == v) continue;
-        const uint64_t lo = (uint64_t)(u < v ? u : v), hi = (uint64_t)(u < v ? v : u);
-        keys.push_back((lo << b) | hi);
-    }
-    host_radix_sort(keys, 2 * b);
+    const uint64_t none = ~(uint64_t)0;  // self-loops: sorts last, dropped below
+    std::vector<uint8_t> bad(host_threads(), 0);
+    parallel_for(m_in, [&](int64_t lo, int64_t hi, unsigned t) {
+        for (int64_t e = lo; e < hi; ++e) {
+            const int32_t u = src[e], v = dst[e];
+            if (u < 0 || v < 0 || u >= n || v >= n) {
+                bad[t] = 1;
+                keys[(size_t)e] = none;
+                continue;
+            }
+            keys[(size_t)e] = u == v ? none
+                                     : (((uint64_t)(u < v ? u : v) << b) | (uint64_t)(u < v ? v : u));
+        }
+    });
+    for (uint8_t x : bad)
+        if (x) return HARP_EINVAL;
+    host_radix_sort(keys, 64);
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    if (!keys.empty() && keys.back() == none) keys.pop_back();
     g.n = n;
     g.m = (int64_t)keys.size();
     const uint64_t lowmask = ((uint64_t)1 << b) - 1;
     std::vector<int32_t> deg0((size_t)n, 0);
-    for (uint64_t k : keys) {
-        deg0[k >> b]++;
-        deg0[k & lowmask]++;
-    }
+    parallel_for(g.m, [&](int64_t lo, int64_t hi, unsigned) {
+        for (int64_t i = lo; i < hi; ++i) {
+            __atomic_fetch_add(&deg0[keys[(size_t)i] >> b], 1, __ATOMIC_RELAXED);
+            __atomic_fetch_add(&deg0[keys[(size_t)i] & lowmask], 1, __ATOMIC_RELAXED);
+        }
+    });
     // rank = (degree, id): counting sort by degree, ids ascending inside a degree
     int32_t maxd = 0;
     for (int32_t d : deg0) maxd = d > maxd ? d : maxd;
@@ -125,36 +157,51 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     for (int64_t v = 0; v < n; ++v) rank[(size_t)v] = (int32_t)start[(size_t)deg0[(size_t)v]]++;
     std::vector<uint64_t> arcs;
     try {
-        arcs.reserve(2 * keys.size());
+        arcs.resize(2 * keys.size());
     } catch (...) {
         return HARP_ENOMEM;
     }
-    for (uint64_t k : keys) {
-        const uint64_t a = (uint64_t)rank[k >> b], c = (uint64_t)rank[k & lowmask];
-        arcs.push_back((a << 32) | c);
-        arcs.push_back((c << 32) | a);
-    }
+    parallel_for(g.m, [&](int64_t lo, int64_t hi, unsigned) {
+        for (int64_t i = lo; i < hi; ++i) {
+            const uint64_t k = keys[(size_t)i];
+            const uint64_t a = (uint64_t)rank[k >> b], c = (uint64_t)rank[k & lowmask];
+            arcs[2 * (size_t)i] = (a << 32) | c;
+            arcs[2 * (size_t)i + 1] = (c << 32) | a;
+        }
+    });
     std::vector<uint64_t>().swap(keys);
     host_radix_sort(arcs, 32 + b);
+    const int64_t A = (int64_t)arcs.size();
     g.off.assign((size_t)n + 1, 0);
     g.cols.resize(arcs.size());
-    for (size_t i = 0; i < arcs.size(); ++i) {
-        g.off[(arcs[i] >> 32) + 1]++;
-        g.cols[i] = (int32_t)(arcs[i] & 0xffffffffull);
-    }
+    // rows are sorted: off[r] = first arc of a row >= r, set where the row changes
+    parallel_for(A, [&](int64_t lo, int64_t hi, unsigned) {
+        for (int64_t i = lo; i < hi; ++i) {
+            g.cols[(size_t)i] = (int32_t)(arcs[(size_t)i] & 0xffffffffull);
+            const int64_t r = (int64_t)(arcs[(size_t)i] >> 32);
+            const int64_t rp = i > 0 ? (int64_t)(arcs[(size_t)i - 1] >> 32) : -1;
+            for (int64_t x = rp + 1; x <= r; ++x) g.off[(size_t)x] = i;
+            if (i == A - 1)
+                for (int64_t x = r + 1; x <= n; ++x) g.off[(size_t)x] = A;
+        }
+    });
+    if (A == 0) std::fill(g.off.begin(), g.off.end(), 0);
     std::vector<uint64_t>().swap(arcs);
-    for (int64_t r = 0; r < n; ++r) g.off[(size_t)r + 1] += g.off[(size_t)r];
     g.deg.resize((size_t)n);
     g.dplus.resize((size_t)n);
+    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
+        for (int64_t r = lo; r < hi; ++r) {
+            const int64_t a = g.off[(size_t)r], z = g.off[(size_t)r + 1];
+            g.deg[(size_t)r] = (int32_t)(z - a);
+            const int64_t split =
+                std::upper_bound(g.cols.begin() + a, g.cols.begin() + z, (int32_t)r) - (g.cols.begin() + a);
+            g.dplus[(size_t)r] = (int32_t)(z - a - split);
+        }
+    });
     g.offp.assign((size_t)n + 1, 0);
     g.n1 = n;
     for (int64_t r = 0; r < n; ++r) {
-        const int64_t lo = g.off[(size_t)r], hi = g.off[(size_t)r + 1];
-        g.deg[(size_t)r] = (int32_t)(hi - lo);
-        if (g.n1 == n && hi - lo >= 2) g.n1 = r;
-        const int64_t split = std::upper_bound(g.cols.begin() + lo, g.cols.begin() + hi, (int32_t)r) -
-                              (g.cols.begin() + lo);
-        g.dplus[(size_t)r] = (int32_t)(hi - lo - split);
+        if (g.n1 == n && g.deg[(size_t)r] >= 2) g.n1 = r;
         g.offp[(size_t)r + 1] = g.offp[(size_t)r] + g.dplus[(size_t)r];
     }
     return HARP_OK;
@@ -181,8 +228,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // the fallback scratch and the accumulators.
 size_t tri_block_bytes(int64_t n, int64_t out_arcs, int64_t fb_scratch) {
     const int64_t nn = n > 0 ? n : 1, oa = out_arcs > 0 ? out_arcs : 1;
-    return align256(8 * (size_t)(nn + 1)) + 4 * align256(4 * (size_t)nn) + 2 * align256(4 * (size_t)oa) +
-           align256((size_t)fb_scratch) + align256(8 * (size_t)kOutLen);
+    return align256(8 * (size_t)(nn + 1)) + 3 * align256(4 * (size_t)nn) + align256(8 * (size_t)nn) +
+           2 * align256(4 * (size_t)oa) + align256((size_t)fb_scratch) + align256(8 * (size_t)kOutLen);
 }
 
 // Device bytes of a wedge block: per-vertex arrays (off, loff, win_prefix, deg, dplus, fpos, queues),
@@ -378,11 +425,24 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
     return HARP_OK;
 }
 
-// The device results of all blocks.
+// The device results of all blocks, and where the time went.
 struct PartSums {
     uint64_t T = 0, K4 = 0, C4 = 0, PAWSUM = 0;
     std::vector<uint32_t> te;  // global out-arc numbering
+    double transfer_ms = 0, device_ms = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // copies in | kernels | copies out | end
 };
+
+// Milliseconds between the recorded phase events of one block (after it synchronised).
+void add_phase_times(PartSums& sum) {
+    float a = 0, b = 0, c = 0;
+    if (cudaEventElapsedTime(&a, sum.ev[0], sum.ev[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, sum.ev[1], sum.ev[2]) == cudaSuccess &&
+        cudaEventElapsedTime(&c, sum.ev[2], sum.ev[3]) == cudaSuccess) {
+        sum.transfer_ms += a + c;
+        sum.device_ms += b;
+    }
+}
 
 harp_status check_cuda(cudaError_t e) {
     if (e == cudaSuccess) return HARP_OK;
@@ -403,12 +463,14 @@ harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev,
     for (int64_t v = 0; v < n; ++v) offp[(size_t)v + 1] = offp[(size_t)v] + (in[(size_t)v] ? g.dplus[(size_t)v] : 0);
     const int64_t outs = offp[(size_t)n];
     std::vector<int32_t> colsp((size_t)(outs > 0 ? outs : 1));
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t len = offp[(size_t)v + 1] - offp[(size_t)v];
-        if (len)
-            std::memcpy(&colsp[(size_t)offp[(size_t)v]], &g.cols[(size_t)(g.off[(size_t)v + 1] - len)],
-                        sizeof(int32_t) * (size_t)len);
-    }
+    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
+        for (int64_t v = lo; v < hi; ++v) {
+            const int64_t len = offp[(size_t)v + 1] - offp[(size_t)v];
+            if (len)
+                std::memcpy(&colsp[(size_t)offp[(size_t)v]], &g.cols[(size_t)(g.off[(size_t)v + 1] - len)],
+                            sizeof(int32_t) * (size_t)len);
+        }
+    });
     halo_arcs += (uint64_t)outs;
     const size_t bytes = tri_block_bytes(n, outs, fb);
     void* base = nullptr;
@@ -419,13 +481,14 @@ harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev,
     ws.deg = c.take<int32_t>((size_t)n);
     ws.dplus = c.take<int32_t>((size_t)n);
     ws.q_tri = c.take<int32_t>((size_t)n);
-    ws.q_mid = c.take<int32_t>((size_t)n);
+    ws.q_mid = c.take<int32_t>(2 * (size_t)n);
     ws.colsp = c.take<int32_t>((size_t)outs);
     ws.te = c.take<uint32_t>((size_t)outs);
-    c.take<unsigned char>((size_t)fb);  // the fallback allocates its own scratch: counted in the budget here
+    c.take<unsigned char>((size_t)fb);  // the triangle kernels allocate their own scratch: counted here
     ws.acc = c.take<uint64_t>(kOutLen);
     ws.own_lo = blk.lo;
     ws.own_hi = blk.hi;
+    cudaEventRecord(sum.ev[0], s);
     cudaError_t e = cudaMemcpyAsync(ws.offp, offp.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && outs)
         e = cudaMemcpyAsync(ws.colsp, colsp.data(), sizeof(int32_t) * (size_t)outs, cudaMemcpyHostToDevice, s);
@@ -444,26 +507,32 @@ harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev,
     view.max_deg = n ? *std::max_element(g.deg.begin(), g.deg.end()) : 0;
     harp_plan plan;
     normalise_plan(nullptr, &plan);
+    cudaEventRecord(sum.ev[1], s);
     if (st == HARP_OK && n > 0) st = count_triangles_k4(&view, ws, plan, s);
+    cudaEventRecord(sum.ev[2], s);
     std::vector<uint32_t> te_local((size_t)outs);
     uint64_t acc[kOutLen] = {0};
     if (st == HARP_OK) {
         e = cudaMemcpyAsync(acc, ws.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && outs)
             e = cudaMemcpyAsync(te_local.data(), ws.te, sizeof(uint32_t) * (size_t)outs, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(sum.ev[3], s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         st = check_cuda(e);
         if (st == HARP_OK && acc[ACC_ERR]) st = HARP_EDEVICE;
+        if (st == HARP_OK) add_phase_times(sum);
     }
     cudaFreeAsync(base, s);
     if (st != HARP_OK) return st;
     sum.T += acc[ACC_T];
     sum.K4 += acc[ACC_K4];
     sum.PAWSUM += acc[ACC_PAWSUM];
-    for (int64_t v = 0; v < n; ++v) {  // local out-arcs -> global out-arc ids
-        const int64_t lb = offp[(size_t)v], len = offp[(size_t)v + 1] - lb, gb = g.offp[(size_t)v];
-        for (int64_t k = 0; k < len; ++k) sum.te[(size_t)(gb + k)] += te_local[(size_t)(lb + k)];
-    }
+    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {  // local out-arcs -> global out-arc ids
+        for (int64_t v = lo; v < hi; ++v) {
+            const int64_t lb = offp[(size_t)v], len = offp[(size_t)v + 1] - lb, gb = g.offp[(size_t)v];
+            for (int64_t k = 0; k < len; ++k) sum.te[(size_t)(gb + k)] += te_local[(size_t)(lb + k)];
+        }
+    });
     return HARP_OK;
 }
 
@@ -488,24 +557,30 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     // rows of the lower neighbours, restricted to the slice [xa, xb) of opposite vertices
     const int64_t xa = std::max<int64_t>(blk.xlo, g.n1), xb = std::min<int64_t>(blk.xhi, blk.hi);
     std::vector<int64_t> off((size_t)n + 1, 0), rb((size_t)n, 0);
-    for (int64_t w = 0; w < n; ++w) {
-        int64_t len = 0;
-        if (in[(size_t)w] && xa < xb) {
-            const auto b = g.cols.begin() + g.off[(size_t)w], e = g.cols.begin() + g.off[(size_t)w + 1];
-            const auto p = std::lower_bound(b, e, (int32_t)xa);
-            rb[(size_t)w] = p - g.cols.begin();
-            len = std::lower_bound(p, e, (int32_t)xb) - p;
+    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {  // slice lengths, then a prefix sum
+        for (int64_t w = lo; w < hi; ++w) {
+            int64_t len = 0;
+            if (in[(size_t)w] && xa < xb) {
+                const auto b = g.cols.begin() + g.off[(size_t)w], e = g.cols.begin() + g.off[(size_t)w + 1];
+                const auto p = std::lower_bound(b, e, (int32_t)xa);
+                rb[(size_t)w] = p - g.cols.begin();
+                len = std::lower_bound(p, e, (int32_t)xb) - p;
+            }
+            off[(size_t)w + 1] = len;
         }
-        off[(size_t)w + 1] = off[(size_t)w] + len;
-    }
+    });
+    for (int64_t w = 0; w < n; ++w) off[(size_t)w + 1] += off[(size_t)w];
     const int64_t ra = off[(size_t)n];
     if (la == 0 || ra == 0) return HARP_OK;  // no root or no opposite vertex: nothing to count here
     std::vector<int32_t> cols((size_t)ra);
-    for (int64_t w = 0; w < n; ++w) {
-        const int64_t len = off[(size_t)w + 1] - off[(size_t)w];
-        if (len)
-            std::memcpy(&cols[(size_t)off[(size_t)w]], &g.cols[(size_t)rb[(size_t)w]], sizeof(int32_t) * (size_t)len);
-    }
+    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
+        for (int64_t w = lo; w < hi; ++w) {
+            const int64_t len = off[(size_t)w + 1] - off[(size_t)w];
+            if (len)
+                std::memcpy(&cols[(size_t)off[(size_t)w]], &g.cols[(size_t)rb[(size_t)w]],
+                            sizeof(int32_t) * (size_t)len);
+        }
+    });
     halo_arcs += (uint64_t)(ra + la);
     const size_t bytes = wedge_block_bytes(n, ra, la);
     void* base = nullptr;
@@ -535,6 +610,7 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     ws.own_hi = blk.hi;
     ws.x_lo = xa;
     ws.x_hi = xb;
+    cudaEventRecord(sum.ev[0], s);
     cudaError_t e = cudaMemcpyAsync(ws.off, off.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_loff, loff.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
@@ -555,13 +631,17 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     view.max_deg = 0;
     harp_plan plan;
     normalise_plan(nullptr, &plan);
+    cudaEventRecord(sum.ev[1], s);
     if (st == HARP_OK) st = count_wedge_c4(&view, ws, plan, s);
+    cudaEventRecord(sum.ev[2], s);
     uint64_t acc[kOutLen] = {0};
     if (st == HARP_OK) {
         e = cudaMemcpyAsync(acc, ws.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(sum.ev[3], s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         st = check_cuda(e);
         if (st == HARP_OK && acc[ACC_ERR]) st = HARP_EDEVICE;
+        if (st == HARP_OK) add_phase_times(sum);
     }
     cudaFreeAsync(base, s);
     if (st != HARP_OK) return st;
@@ -581,6 +661,7 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     if (n > 2147483647LL || m_in > 2147483647LL) return HARP_EOVERFLOW;
     int dev = 0;
     HARP_CK(cudaGetDevice(&dev));
+    const auto t0 = std::chrono::steady_clock::now();
     RankGraph g;
     HARP_TRY(build_rank_graph(n, m_in, src, dst, g));
     if (budget_bytes == 0) {
@@ -590,7 +671,9 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     }
     int64_t dmax = 1;
     while (dmax * dmax < 2 * g.m) ++dmax;
-    const int64_t fb = 152 * 8 * (dmax + 32) * 4;  // the triangle fallback's per-warp frontier buffers
+    // scratch the triangle kernels allocate: the fallback's per-warp frontier buffers and the
+    // global-staged tier's rows (4096 x 4096 bits per block, one block per SM)
+    const int64_t fb = 152 * 8 * (dmax + 32) * 4 + (dmax > 1024 ? (int64_t)152 * 4096 * 128 * 4 : 0);
     std::vector<TriBlock> tri;
     std::vector<WedgeBlock> wedge;
     uint64_t device_peak = 0, h2d = 0, halo_arcs = 0;
@@ -601,6 +684,8 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     cudaStream_t s = nullptr;
     HARP_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     harp_status st = HARP_OK;
+    for (cudaEvent_t& ev : sum.ev)
+        if (st == HARP_OK) st = check_cuda(cudaEventCreate(&ev));
     for (size_t k = 0; k < tri.size() && st == HARP_OK; ++k) {
         if (tri[k].lo >= tri[k].hi || g.m == 0) continue;
         st = run_triangle_block(g, tri[k], dev, fb, s, sum, h2d, halo_arcs);
@@ -611,16 +696,33 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
+    for (cudaEvent_t ev : sum.ev)
+        if (ev) cudaEventDestroy(ev);
     if (st != HARP_OK) return st;
     // degree sums by owner (every vertex / edge once) and the global sum_e C(t_e, 2)
+    std::vector<uint64_t> pS(host_threads(), 0), pPW(host_threads(), 0), pD(host_threads(), 0);
+    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned t) {
+        uint64_t s3 = 0, pw = 0;
+        for (int64_t r = lo; r < hi; ++r) {
+            const uint64_t dr = (uint64_t)g.deg[(size_t)r];
+            s3 += choose3_h(dr);
+            for (int64_t k = 0; k < g.dplus[(size_t)r]; ++k)
+                pw += (dr - 1) * ((uint64_t)g.deg[(size_t)out_nbr(g, r, k)] - 1);
+        }
+        pS[t] += s3;
+        pPW[t] += pw;
+    });
+    parallel_for((int64_t)sum.te.size(), [&](int64_t lo, int64_t hi, unsigned t) {
+        uint64_t d = 0;
+        for (int64_t i = lo; i < hi; ++i) d += choose2_h(sum.te[(size_t)i]);
+        pD[t] += d;
+    });
     uint64_t S = 0, PW = 0, D = 0;
-    for (int64_t r = 0; r < n; ++r) {
-        const uint64_t dr = (uint64_t)g.deg[(size_t)r];
-        S += choose3_h(dr);
-        for (int64_t k = 0; k < g.dplus[(size_t)r]; ++k)
-            PW += (dr - 1) * ((uint64_t)g.deg[(size_t)out_nbr(g, r, k)] - 1);
+    for (size_t t = 0; t < pS.size(); ++t) {
+        S += pS[t];
+        PW += pPW[t];
+        D += pD[t];
     }
-    for (uint32_t t : sum.te) D += choose2_h(t);
     const uint64_t T = sum.T, K4 = sum.K4;
     const uint64_t P = PW - 3 * T, pawn = sum.PAWSUM - 6 * T;
     const uint64_t diamond = D - 6 * K4;
@@ -640,6 +742,10 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
         stats->halo_arcs = (int64_t)halo_arcs;
         stats->h2d_bytes = h2d;
         stats->device_peak_bytes = device_peak;
+        const double total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats->transfer_ms = sum.transfer_ms;
+        stats->device_ms = sum.device_ms;
+        stats->host_ms = total - sum.transfer_ms - sum.device_ms;
     }
     return HARP_OK;
 }

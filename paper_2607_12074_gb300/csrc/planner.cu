@@ -72,6 +72,7 @@ void default_plan(harp_plan* p) {
     p->tri_probe = HARP_PROBE_HASH;
     p->tri_warp_max = 32;
     p->tri_cta_max = 1024;
+    p->tri_big_max = 4096;
     p->c4_warp_max_work = 512;
     p->c4_cta_max_work = 8192;
     p->c4_window_bytes = 200 * 1024;
@@ -87,6 +88,7 @@ void normalise_plan(const harp_plan* in, harp_plan* out) {
     if (in->tri_probe) out->tri_probe = in->tri_probe;
     if (in->tri_warp_max) out->tri_warp_max = in->tri_warp_max > 32 ? 32 : in->tri_warp_max;
     if (in->tri_cta_max) out->tri_cta_max = in->tri_cta_max > 1024 ? 1024 : in->tri_cta_max;
+    if (in->tri_big_max) out->tri_big_max = in->tri_big_max > 4096 ? 4096 : in->tri_big_max;
     if (in->c4_warp_max_work) out->c4_warp_max_work = in->c4_warp_max_work;
     if (in->c4_cta_max_work) out->c4_cta_max_work = in->c4_cta_max_work;
     if (in->c4_window_bytes) out->c4_window_bytes = in->c4_window_bytes;

@@ -18,7 +18,9 @@
 // is long) up to the largest element of L, and looks each element up in L (its index j).
 // Warp-local mode: d <= tri_warp_max (<= 32), rows are single words, one warp per anchor.
 // CTA mode: up to tri_cta_max (<= 1024) in three sizes (256 / 512 / 1024), rows in shared memory, one
-// block per anchor.  Fallback (larger d, hubs of very large graphs): per out-arc ordered
+// block per anchor.  Global-staged mode (up to tri_big_max <= 4096, hubs of very large skewed
+// graphs): the same rows in a per-block scratch that stays in L2 (d^2 / 8 bytes), each row built in
+// a per-warp shared buffer and written out once.  Fallback (larger d): per out-arc ordered
 // intersections through global memory with binary-searched membership; 4-cliques by binary search
 // in N+(w).  Membership of y in L is a hash lookup (HARP_PROBE_HASH) or a binary search of the
 // sorted L in shared memory (HARP_PROBE_BSEARCH).
@@ -42,42 +44,47 @@ constexpr int kInf = 0x7fffffff;
 constexpr int32_t kNoKey = -1;
 
 // Anchor queues: in ws.q_tri (n entries) warp-mode anchors (2 <= d <= tri_warp_max) from the front
-// and CTA-mode anchors from the back; fallback anchors in their own queue (ws.q_mid, free until the
-// wedge pass).  Vertices are scanned in descending rank, so high-degree anchors tend to be queued
+// and CTA-mode anchors from the back; fallback anchors in ws.q_mid[0, n) and global-staged anchors in
+// ws.q_mid[n, 2n) (q_mid is free until the wedge pass).  Vertices are scanned in descending rank, so high-degree anchors tend to be queued
 // (and taken) first.
 //
-// Tier of an anchor of out-degree d: -1 none, 0 warp, 1/2/3 CTA 256/512/1024, 4 fallback.
-// wmax <= 32 and cmax <= kCtaMax (the plan's tri_warp_max / tri_cta_max).
-__device__ __forceinline__ int tri_class(int d, int wmax, int cmax) {
+// Tier of an anchor of out-degree d: -1 none, 0 warp, 1/2/3 CTA 256/512/1024, 4 global-staged,
+// 5 fallback.  wmax <= 32, cmax <= kCtaMax, bmax <= kBigMax (tri_warp_max / tri_cta_max / tri_big_max).
+constexpr int kBigMax = 4096;
+__device__ __forceinline__ int tri_class(int d, int wmax, int cmax, int bmax) {
     if (d < 2) return -1;
     if (d <= wmax) return 0;
-    if (d > cmax) return 4;
+    if (d > cmax) return d <= bmax ? 4 : 5;
     return d <= kCta1 ? 1 : (d <= kCta2 ? 2 : 3);
 }
 
 __global__ void k_tri_classify(const int32_t* __restrict__ dplus, int64_t n, int64_t own_lo, int64_t own_hi,
-                               int wmax, int cmax, int32_t* __restrict__ q, int32_t* __restrict__ q_fb,
-                               unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ cnt_fb) {
+                               int wmax, int cmax, int bmax, int32_t* __restrict__ q, int32_t* __restrict__ q_fb,
+                               unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ cnt_fb,
+                               unsigned long long* __restrict__ cnt_big) {
     const int l = lane_id();
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - l; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = n - 1 - (base + l);
         int cls = -1;
-        if (u >= own_lo && u < own_hi && u < n) cls = tri_class(dplus[u], wmax, cmax);
-        cls = cls == 4 ? 2 : (cls > 0 ? 1 : cls);  // 0: warp queue, 1: CTA queue, 2: fallback queue
+        if (u >= own_lo && u < own_hi && u < n) cls = tri_class(dplus[u], wmax, cmax, bmax);
+        // 0: warp queue, 1: CTA queue, 2: fallback queue, 3: global-staged queue
+        cls = cls == 5 ? 2 : (cls == 4 ? 3 : (cls > 0 ? 1 : cls));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 4; ++c) {
             const uint32_t mask = __ballot_sync(kFull, cls == c);
             if (!mask) continue;
             unsigned long long start = 0;
             const int leader = __ffs(mask) - 1;
-            if (l == leader) start = atomicAdd(c < 2 ? &cnt[c] : cnt_fb, (unsigned long long)__popc(mask));
+            unsigned long long* ctr = c < 2 ? &cnt[c] : (c == 2 ? cnt_fb : cnt_big);
+            if (l == leader) start = atomicAdd(ctr, (unsigned long long)__popc(mask));
             start = __shfl_sync(kFull, start, leader);
             if (cls == c) {
                 const unsigned long long k = start + __popc(mask & lanemask_lt());
                 if (c == 0) q[k] = (int32_t)u;
                 else if (c == 1) q[n - 1 - (int64_t)k] = (int32_t)u;
-                else q_fb[k] = (int32_t)u;
+                else if (c == 2) q_fb[k] = (int32_t)u;
+                else q_fb[n + (int64_t)k] = (int32_t)u;
             }
         }
     }
@@ -312,7 +319,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
                                                      const int32_t* __restrict__ colsp,
                                                      const int32_t* __restrict__ deg,
                                                      const int32_t* __restrict__ q, int64_t n, int cls,
-                                                     int wmax, int cmax, bool reuse,
+                                                     int wmax, int cmax, int bmax, bool reuse,
                                                      const unsigned long long* __restrict__ cnt,
                                                      unsigned long long* __restrict__ ticket,
                                                      uint32_t* __restrict__ te, Sink sink) {
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
         const int32_t u = q[n - 1 - k];
         const int64_t ub = offp[u];
         const int d = (int)(offp[u + 1] - ub);
-        if (tri_class(d, wmax, cmax) != cls) continue;
+        if (tri_class(d, wmax, cmax, bmax) != cls) continue;
         const int W = (d + 31) >> 5;
         const int WS = W | 1;
         for (int i = threadIdx.x; i < d; i += THREADS) {
@@ -447,6 +454,164 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
 }
 
 // ---------------------------------------------------------------------------------------------
+// Global-staged mode (kCtaMax < d <= kBigMax): one 512-thread block per anchor, the d rows of d bits
+// in the block's slice of a global scratch (row stride W = ceil(d / 32) words; at most 2 MiB, so it
+// stays in L2).  A warp builds one row at a time in its shared buffer (membership of y in L by binary
+// search of the sorted L in shared memory) and writes it out; after a block barrier the 4-clique
+// extension reads the staged rows back, exactly as the CTA mode does from shared memory.
+// ---------------------------------------------------------------------------------------------
+constexpr int kBigThreads = 512;
+constexpr int kBigWarps = kBigThreads / 32;
+constexpr int kBigWords = kBigMax / 32;
+
+struct BigSmem {
+    int32_t L[kBigMax];
+    uint32_t own[kBigMax];
+    uint32_t row[kBigWarps][kBigWords];
+    uint64_t red[32];
+};
+
+__global__ void __launch_bounds__(kBigThreads, 1) k_tri_big(const int64_t* __restrict__ offp,
+                                                            const int32_t* __restrict__ colsp,
+                                                            const int32_t* __restrict__ deg,
+                                                            const int32_t* __restrict__ q_big,
+                                                            const unsigned long long* __restrict__ cnt_big,
+                                                            unsigned long long* __restrict__ ticket, bool reuse,
+                                                            uint32_t* __restrict__ scratch,
+                                                            uint32_t* __restrict__ te, Sink sink) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BigSmem& s = *reinterpret_cast<BigSmem*>(smem_raw);
+    __shared__ int64_t s_item;
+    const int w = threadIdx.x >> 5, l = lane_id();
+    uint32_t* R = scratch + (size_t)blockIdx.x * kBigMax * kBigWords;
+    uint32_t* buf = s.row[w];
+    const int64_t nq = (int64_t)*cnt_big;
+    uint64_t tri = 0, k4 = 0, paw = 0, hits = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const int64_t k = s_item;
+        __syncthreads();
+        if (k >= nq) break;
+        const int32_t u = q_big[k];
+        const int64_t ub = offp[u];
+        const int d = (int)(offp[u + 1] - ub);  // cmax < d <= kBigMax by classification
+        const int W = (d + 31) >> 5;
+        for (int i = threadIdx.x; i < d; i += kBigThreads) {
+            s.L[i] = colsp[ub + i];
+            s.own[i] = 0;
+        }
+        __syncthreads();
+        const int32_t last = s.L[d - 1];
+        // rows: warp per row, built in the warp's shared buffer, then written to the scratch
+        for (int i = w; i < d; i += kBigWarps) {
+            for (int x = l; x < W; x += 32) buf[x] = 0;
+            __syncwarp();
+            uint32_t hits_i = 0;
+            if (i < d - 1) {
+                const int32_t v = s.L[i];
+                const int32_t next = s.L[i + 1];
+                const int64_t e = offp[v + 1];
+                int64_t b = offp[v];
+                if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
+                auto probe = [&](int32_t y, int64_t p) {
+                    if (y >= next && y <= last) {
+                        const int j = find_sorted(s.L, d, y);
+                        if (j >= 0) {
+                            atomicAdd(&te[p], 1u);
+                            atomicOr(&buf[j >> 5], 1u << (j & 31));
+                            atomicAdd(&s.own[j], 1u);
+                            ++hits_i;
+                        }
+                    }
+                };
+                probe_list(colsp, b, e, last, probe);
+            }
+            hits_i = warp_sum(hits_i);
+            if (l == 0 && hits_i) atomicAdd(&s.own[i], hits_i);
+            __syncwarp();
+            for (int x = l; x < W; x += 32) R[(size_t)i * W + x] = buf[x];
+            __syncwarp();
+        }
+        __syncthreads();  // every row is in the scratch
+        uint64_t a_tri = 0, a_k4 = 0, a_paw = 0;
+        for (int i = w; i < d - 1; i += kBigWarps) {
+            const uint32_t* Ri = R + (size_t)i * W;
+            for (int x = l; x < W; x += 32) buf[x] = Ri[x];
+            __syncwarp();
+            // the set bits of row i in chunks of 32 words (one word per lane), dealt to the lanes
+            for (int c0 = 0; c0 < W; c0 += 32) {
+                const uint32_t myw = c0 + l < W ? buf[c0 + l] : 0u;
+                const int cnt_w = __popc(myw);
+                int pre = cnt_w;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, pre, o);
+                    if (l >= o) pre += y;
+                }
+                const int B = __shfl_sync(kFull, pre, 31);
+                pre -= cnt_w;
+                a_tri += (l == 0) ? (uint64_t)B : 0;
+                for (int k0 = 0; k0 < B; k0 += 32) {
+                    const int kk = k0 + l;
+                    int o = 0;
+#pragma unroll
+                    for (int sft = 16; sft >= 1; sft >>= 1) {
+                        const int e = __shfl_sync(kFull, pre, o + sft);
+                        if (e <= kk) o += sft;
+                    }
+                    const uint32_t word = __shfl_sync(kFull, myw, o);
+                    const int rank = kk - __shfl_sync(kFull, pre, o);
+                    if (kk < B) {
+                        const int j = ((c0 + o) << 5) + (int)__fns(word, 0, rank + 1);
+                        uint32_t cnt = 0;
+                        if (reuse) {  // the staged frontier of (u, L[j])
+                            const uint32_t* Rj = R + (size_t)j * W;
+                            for (int x = c0 + o; x < W; ++x) cnt += __popc(buf[x] & Rj[x]);
+                        } else {      // recompute from N+(L[j]) in global memory
+                            const int32_t wv = s.L[j];
+                            for (int64_t p = offp[wv], pe = offp[wv + 1]; p < pe; ++p) {
+                                const int32_t y = colsp[p];
+                                if (y > last) break;
+                                const int jj = find_sorted(s.L, d, y);
+                                if (jj >= 0 && ((buf[jj >> 5] >> (jj & 31)) & 1u)) ++cnt;
+                            }
+                        }
+                        a_k4 += cnt;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        for (int i = threadIdx.x; i < d; i += kBigThreads) {
+            const uint32_t o = s.own[i];
+            if (o) {
+                atomicAdd(&te[ub + i], o);
+                a_paw += (uint64_t)o * (uint64_t)deg[s.L[i]];
+            }
+        }
+        a_paw += a_tri * (uint64_t)deg[u];
+        if (reuse) hits += a_tri;
+        __syncthreads();
+        if (sink.batch()) {
+            const uint64_t t1 = block_sum_u64(a_tri, s.red);
+            const uint64_t t2 = block_sum_u64(a_k4, s.red);
+            const uint64_t t3 = block_sum_u64(a_paw, s.red);
+            if (threadIdx.x == 0) {
+                sink_add(sink, u, G_T, t1);
+                sink_add(sink, u, G_K4, t2);
+                sink_add(sink, u, G_PAWSUM, t3);
+            }
+        } else {
+            tri += a_tri;
+            k4 += a_k4;
+            paw += a_paw;
+        }
+    }
+    flush_block(sink, tri, k4, paw, hits, s.red);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Fallback for out-degree > kCtaMax (1024): per out-arc (u, v) the frontier S_uv = N+(u) n N+(v) is
 // materialised (compaction) in a per-warp global buffer, then reused for the 4-clique extension.
 // ---------------------------------------------------------------------------------------------
@@ -537,12 +702,12 @@ __global__ void __launch_bounds__(256) k_tri_fallback(const int64_t* __restrict_
 
 template <int DMAX, int THREADS, bool BS>
 harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slot, int blocks_per_sm, int wmax,
-                       int cmax, bool reuse, cudaStream_t s) {
+                       int cmax, int bmax, bool reuse, cudaStream_t s) {
     const size_t smem = sizeof(CtaSmem<DMAX>);
     HARP_CK(cudaFuncSetAttribute(k_tri_cta<DMAX, THREADS, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     k_tri_cta<DMAX, THREADS, BS><<<152 * blocks_per_sm, THREADS, smem, s>>>(
-        ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, wmax, cmax, reuse,
+        ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, wmax, cmax, bmax, reuse,
         (const unsigned long long*)&ws.acc[Q_TRI_WARP], (unsigned long long*)&ws.acc[ticket_slot], ws.te,
         Sink{ws.acc, ws.gid, ws.accG});
     HARP_LAUNCHED();
@@ -550,16 +715,17 @@ harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slo
 }
 
 template <bool BS>
-harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, bool reuse, cudaStream_t s) {
+harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, int bmax, bool reuse,
+                         cudaStream_t s) {
     const Sink sink{ws.acc, ws.gid, ws.accG};
     k_tri_warp<BS><<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri,
                                                    (const unsigned long long*)&ws.acc[Q_TRI_WARP], reuse, ws.te, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_TRI_WARP));
-    HARP_TRY((launch_cta<kCta1, 256, BS>(g, ws, 1, T_TRI_S, 4, wmax, cmax, reuse, s)));
+    HARP_TRY((launch_cta<kCta1, 256, BS>(g, ws, 1, T_TRI_S, 4, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
-    HARP_TRY((launch_cta<kCta2, 256, BS>(g, ws, 2, T_TRI_M, 4, wmax, cmax, reuse, s)));
-    HARP_TRY((launch_cta<kCtaMax, 512, BS>(g, ws, 3, T_TRI_L, 1, wmax, cmax, reuse, s)));
+    HARP_TRY((launch_cta<kCta2, 256, BS>(g, ws, 2, T_TRI_M, 4, wmax, cmax, bmax, reuse, s)));
+    HARP_TRY((launch_cta<kCtaMax, 512, BS>(g, ws, 3, T_TRI_L, 1, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
     return HARP_OK;
 }
@@ -573,22 +739,44 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     if (n == 0 || g->m == 0) return HARP_OK;  // no marks: the segments read as zero
     const int wmax = (int)plan.tri_warp_max;  // normalised: 1..32
     const int cmax = (int)plan.tri_cta_max;   // normalised: 1..kCtaMax
+    const int bmax = (int)plan.tri_big_max;   // normalised: 1..kBigMax
     const bool reuse = !(plan.flags & HARP_PLAN_NO_REUSE);
     unsigned long long* cnt = (unsigned long long*)&ws.acc[Q_TRI_WARP];
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     unsigned long long* cnt_fb = (unsigned long long*)&ws.acc[Q_TRI_FB];
-    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, wmax, cmax, ws.q_tri, ws.q_mid,
-                                                    cnt, cnt_fb);
+    unsigned long long* cnt_big = (unsigned long long*)&ws.acc[Q_TRI_BIG];
+    k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, wmax, cmax, bmax, ws.q_tri,
+                                                    ws.q_mid, cnt, cnt_fb, cnt_big);
     HARP_LAUNCHED();
     const Sink sink{ws.acc, ws.gid, ws.accG};
-    if (plan.tri_probe == HARP_PROBE_BSEARCH) HARP_TRY(launch_tiers<true>(g, ws, wmax, cmax, reuse, s));
-    else HARP_TRY(launch_tiers<false>(g, ws, wmax, cmax, reuse, s));
-    // fallback: per-warp frontier buffers of the largest possible out-degree (bounded by sqrt(2m))
+    if (plan.tri_probe == HARP_PROBE_BSEARCH) HARP_TRY(launch_tiers<true>(g, ws, wmax, cmax, bmax, reuse, s));
+    else HARP_TRY(launch_tiers<false>(g, ws, wmax, cmax, bmax, reuse, s));
+    // the largest possible out-degree is bounded by sqrt(2m) and by the maximum degree
     int64_t dmax = 1;
     while (dmax * dmax < 2 * g->m) ++dmax;
     if (dmax > g->max_deg) dmax = g->max_deg;
-    if (dmax > cmax) {
+    if (dmax > cmax && bmax > cmax) {  // global-staged tier: one block per SM, scratch of kBigMax rows
+        const size_t bytes = (size_t)152 * kBigMax * kBigWords * sizeof(uint32_t);
+        uint32_t* scratch = nullptr;
+        HARP_CK(cudaMallocAsync((void**)&scratch, bytes, s));
+        const size_t smem = sizeof(BigSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_tri_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            k_tri_big<<<152, kBigThreads, smem, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_mid + n, cnt_big,
+                                                      (unsigned long long*)&ws.acc[T_TRI_BIG], reuse, scratch, ws.te,
+                                                      sink);
+            note_launch();
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(scratch, s);
+        if (e != cudaSuccess) {
+            record_cuda_error(e);
+            return HARP_ECUDA;
+        }
+    }
+    // fallback: per-warp frontier buffers of the largest possible out-degree
+    if (dmax > cmax && dmax > bmax) {
         const int fb_blocks = 152;
         const int64_t per_warp = dmax + 32;
         const size_t bytes = (size_t)fb_blocks * 8 * (size_t)per_warp * sizeof(int32_t);

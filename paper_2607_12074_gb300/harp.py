@@ -45,6 +45,7 @@ class harp_plan(ctypes.Structure):
         ("tri_probe", ctypes.c_uint32),
         ("tri_warp_max", ctypes.c_uint32),
         ("tri_cta_max", ctypes.c_uint32),
+        ("tri_big_max", ctypes.c_uint32),
         ("c4_warp_max_work", ctypes.c_uint32),
         ("c4_cta_max_work", ctypes.c_uint32),
         ("c4_window_bytes", ctypes.c_uint32),
@@ -75,7 +76,8 @@ class harp_select_opts(ctypes.Structure):
 
 class harp_partition_stats(ctypes.Structure):
     _fields_ = [("partitions", ctypes.c_int64), ("m", ctypes.c_int64), ("halo_arcs", ctypes.c_int64),
-                ("h2d_bytes", ctypes.c_uint64), ("device_peak_bytes", ctypes.c_uint64)]
+                ("h2d_bytes", ctypes.c_uint64), ("device_peak_bytes", ctypes.c_uint64), ("host_ms", ctypes.c_double),
+                ("transfer_ms", ctypes.c_double), ("device_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -75,3 +75,17 @@ def test_partitioned_errors(harp):
     with pytest.raises(harp.HarpError) as ei:
         harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1024)  # the per-vertex arrays alone exceed it
     assert ei.value.status == harp.HARP_ENOMEM
+
+
+def test_chung_lu_subsample_under_a_cap(harp):
+    """The partitioned large graph's 1M-vertex subsample stand-in, run the same way (budget-sized
+    triangle ranges and wedge slices), against the oracle."""
+    g = graphgen.chung_lu_subsample()
+    want = O.count4_combo(g.n, g.src, g.dst)
+    whole, st1 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34)
+    _, st16 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34, parts=16)
+    budget = (st1["device_peak_bytes"] + st16["device_peak_bytes"]) // 2
+    got, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=budget)
+    assert st["partitions"] > 2 and st["device_peak_bytes"] <= budget
+    assert st["transfer_ms"] >= 0 and st["device_ms"] > 0
+    assert got.tolist() == whole.tolist() == want.tolist()

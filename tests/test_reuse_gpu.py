@@ -29,10 +29,10 @@ def harp():
 
 
 def hub_fan(nb=1030, nc=1100):
-    """Anchors whose out-degree exceeds the largest staged size: vertex a and every c in C have the
+    """Anchors whose out-degree exceeds the shared-memory stage: vertex a and every c in C have the
     nb vertices of B (degree nc + 1 or more) as out-neighbours, and a path through B closes
-    triangles (a, b_i, b_i+1) and (c, b_i, b_i+1) in the unstaged fallback.  A disjoint K40 adds
-    staged anchors."""
+    triangles (a, b_i, b_i+1) and (c, b_i, b_i+1): global-staged by default, unstaged fallback when
+    tri_big_max forbids that stage.  A disjoint K40 adds shared-memory-staged anchors."""
     a, B, C = 0, np.arange(1, 1 + nb), np.arange(1 + nb, 1 + nb + nc)
     k_src, k_dst = complete(40)
     base = 1 + nb + nc
@@ -74,7 +74,9 @@ def test_reuse_switch_and_capacity_never_change_counts(harp):
     variants = {
         "no_reuse": plan(H, flags=H.HARP_PLAN_NO_REUSE),
         "cta256": plan(H, tri_cta_max=256),
-        "cta1": plan(H, tri_cta_max=1),                       # every anchor above the warp mode unstaged
+        "cta1": plan(H, tri_cta_max=1),                       # above the warp mode: global-staged
+        "nobig": plan(H, tri_big_max=1),                      # above the CTA mode: unstaged fallback
+        "cta1_nobig": plan(H, tri_cta_max=1, tri_big_max=1),  # every anchor above the warp mode unstaged
         "warp8": plan(H, tri_warp_max=8),
         "bsearch": plan(H, tri_probe=H.HARP_PROBE_BSEARCH),
         "bsearch_no_reuse": plan(H, tri_probe=H.HARP_PROBE_BSEARCH, flags=H.HARP_PLAN_NO_REUSE),
@@ -83,19 +85,19 @@ def test_reuse_switch_and_capacity_never_change_counts(harp):
         counts, stats, look, hits = run(H, g)
         assert look == stats[0], g.name                      # one lookup per triangle
         assert hits <= look
-        if g.name == "HUBFAN":                               # out-degrees above 1024: unstaged misses
-            assert 0 < hits < look
-        elif g.name in ("K40", "K300", "CP200", "W3000"):
-            assert hits == look                              # everything staged
+        if g.name in ("K40", "K300", "CP200", "W3000", "HUBFAN"):
+            assert hits == look                              # everything staged (shared or global)
         for name, p in variants.items():
             c2, s2, l2, h2 = run(H, g, p)
             assert c2 == counts and s2 == stats, (g.name, name)
             assert l2 == look
             if "no_reuse" in name:
                 assert h2 == 0, (g.name, name)
-            elif name in ("cta256", "cta1"):
+            elif "nobig" in name:
                 assert h2 <= hits, (g.name, name)
-            else:                                            # same staging, other probe / warp split
+                if g.name == "HUBFAN":                       # out-degree 1030 unstaged: misses
+                    assert 0 < h2 < look
+            else:                                            # same staging, other tier split or probe
                 assert h2 == hits, (g.name, name)
 
 
@@ -103,7 +105,8 @@ def test_reuse_counts_against_oracle(harp):
     H = harp
     g = graphgen.chung_lu(8000, 2.1, 1500, 12, 11)
     want = O.count4_combo(g.n, g.src, g.dst).tolist()
-    for p in (None, plan(H, flags=H.HARP_PLAN_NO_REUSE), plan(H, tri_cta_max=1)):
+    for p in (None, plan(H, flags=H.HARP_PLAN_NO_REUSE), plan(H, tri_cta_max=1),
+              plan(H, tri_cta_max=1, flags=H.HARP_PLAN_NO_REUSE), plan(H, tri_cta_max=1, tri_big_max=1)):
         assert run(H, g, p)[0] == want
 
 
