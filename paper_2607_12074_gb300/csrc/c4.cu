@@ -186,8 +186,37 @@ __global__ void __launch_bounds__(256) k_c4_rev(const int64_t* __restrict__ off,
     }
 }
 
+// The boundary table keeps kGridCap entries per row: entry k is the row position of grid boundary
+// k << s, where s is the smallest shift with ceil((nwin + 1) / 2^s) <= kGridCap (boundary i < nwin is
+// the start of window i, boundary nwin the end of the grid).  s = 0 (every boundary) for grids of at
+// most kGridCap - 1 windows; larger grids keep every 2^s-th boundary and the rest is found from the
+// nearest kept one by a galloping search.
+__device__ __forceinline__ int table_shift(int64_t nwin) {
+    int sl = 0;
+    while (((nwin + 1 + ((int64_t)1 << sl) - 1) >> sl) > kGridCap) ++sl;
+    return sl;
+}
+
+// First index in [lo, hi) whose element is >= key (a sorted), searching outward from lo: cost grows
+// with the log of the distance, not of the row length.
+__device__ __forceinline__ int64_t gallop_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t key) {
+    if (lo >= hi || __ldg(a + lo) >= key) return lo;
+    int64_t prev = lo, step = 1;  // a[prev] < key
+    while (prev + step < hi && __ldg(a + prev + step) < key) {
+        prev += step;
+        step <<= 1;
+    }
+    int64_t l = prev + 1, r = prev + step < hi ? prev + step : hi;  // the answer lies in [l, r]
+    while (l < r) {
+        const int64_t mid = (l + r) >> 1;
+        if (__ldg(a + mid) < key) l = mid + 1;
+        else r = mid;
+    }
+    return l;
+}
+
 // fpos[w] = row position of w's first neighbour of degree >= 2 (the graph's n1 boundary), and
-// bpos[w * kGridCap + k] = row position of the k-th boundary of w's grid (k <= nwin), if it fits
+// bpos[w * kGridCap + k] = row position of grid boundary k << s (see table_shift)
 template <int WORDS>
 __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                           const int32_t* __restrict__ gid, const int64_t* __restrict__ ginfo, int64_t n,
@@ -202,15 +231,16 @@ __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __rest
             const int64_t wb = off[w];
             const int32_t f = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)gi[GI_N1]);
             fpos[w] = f;
-            if (bpos && nwin + 1 <= kGridCap) bpos[t] = f;
+            if (bpos) bpos[t] = f;
             continue;
         }
-        if (!bpos || nwin + 1 > kGridCap || k > nwin) continue;
+        const int64_t i = (int64_t)k << table_shift(nwin);
+        if (!bpos || i > nwin) continue;
         int64_t bound = gi[GI_HI];
-        if (k < nwin) {
+        if (i < nwin) {
             int64_t xhi;
             int width;
-            grid_window<WORDS>(gi, k, bound, xhi, width);
+            grid_window<WORDS>(gi, i, bound, xhi, width);
         }
         const int64_t wb = off[w];
         bpos[t] = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)bound);
@@ -450,7 +480,8 @@ template <int WIDTH, int WORDS>
 __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                             const int32_t* __restrict__ lcols,
                                             const int32_t* __restrict__ fpos, const int32_t* __restrict__ rev,
-                                            const int32_t* __restrict__ bpos, bool table, int64_t j, int64_t ub,
+                                            const int32_t* __restrict__ bpos, bool table, int sl, int64_t nwin,
+                                            int64_t j, int64_t ub,
                                             int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
                                             WinShared& sh, uint64_t& c4, uint64_t* acc) {
     const int l = lane_id();
@@ -468,13 +499,16 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
             const int32_t wv = lcols[ub + a];
             const int64_t wb = off[wv];
             int64_t p0, p1;
-            if (first) p0 = fpos[wv];
-            else if (table) p0 = bpos[(int64_t)wv * kGridCap + j];
-            else p0 = lower_bound_i32(cols + wb, off[wv + 1] - wb, xlo);
-            if (last) p1 = rev[ub + a];
-            else if (table) p1 = bpos[(int64_t)wv * kGridCap + j + 1];
-            else p1 = lower_bound_i32(cols + wb, off[wv + 1] - wb, xhi);
             const int64_t rowlen = off[wv + 1] - wb;
+            const int64_t mask = ((int64_t)1 << sl) - 1;
+            if (first) p0 = fpos[wv];
+            else if (table && (j & mask) == 0) p0 = bpos[(int64_t)wv * kGridCap + (j >> sl)];
+            else if (table) p0 = gallop_i32(cols + wb, bpos[(int64_t)wv * kGridCap + (j >> sl)], rowlen, xlo);
+            else p0 = lower_bound_i32(cols + wb, rowlen, xlo);
+            if (last) p1 = rev[ub + a];
+            else if (table && ((j + 1) & mask) == 0 && j + 1 <= nwin) p1 = bpos[(int64_t)wv * kGridCap + ((j + 1) >> sl)];
+            else if (table) p1 = gallop_i32(cols + wb, p0 < 0 ? 0 : p0, rowlen, xhi);
+            else p1 = lower_bound_i32(cols + wb, rowlen, xhi);
             if (p0 < 0 || p1 > rowlen) {
                 flag_error(acc, 2ull);
                 p0 = p1 = 0;
@@ -572,7 +606,9 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
         const bool last = xhi >= (int64_t)u;
         if (last) xhi = u;
         const bool first = j == 0;
-        const bool table = bpos != nullptr && gi[GI_NWIN] + 1 <= kGridCap;
+        const int64_t nwin = gi[GI_NWIN];
+        const bool table = bpos != nullptr;
+        const int sl = table_shift(nwin);
         const int64_t dm = (int64_t)deg[u] - dplus[u];
         const int64_t ub = loff[u];
         constexpr int WORDS = win_words(MINB);
@@ -582,13 +618,13 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
         __syncthreads();
         uint64_t a_c4 = 0;
         if (width == 8)
-            window_pass<8, WORDS>(off, cols, lcols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<8, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                            sh, a_c4, acc);
         else if (width == 16)
-            window_pass<16, WORDS>(off, cols, lcols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<16, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                             sh, a_c4, acc);
         else
-            window_pass<32, WORDS>(off, cols, lcols, fpos, rev, bpos, table, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+            window_pass<32, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                             sh, a_c4, acc);
         __syncthreads();
         if (sh.nsplit > 0) {

@@ -132,8 +132,8 @@ struct Workspace {
     int64_t arcs = -1;
     // partitioned wedge pass: the roots' lower lists N-(u) in their own CSR (loff [n+1], lcols), the
     // rows (off, cols) hold only x in [x_lo, x_hi) (the opposite vertices this block owns); nullptr =
-    // a whole graph, whose row prefixes are the lower lists.  bpos may be nullptr (boundaries are
-    // then searched per window).
+    // a whole graph, whose row prefixes are the lower lists.  bpos may be nullptr (window boundaries
+    // are then searched in every row).
     const int64_t* loff = nullptr;
     const int32_t* lcols = nullptr;
     int64_t lower_arcs = 0;  // loff[n]

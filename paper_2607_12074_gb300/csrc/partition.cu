@@ -232,11 +232,12 @@ size_t tri_block_bytes(int64_t n, int64_t out_arcs, int64_t fb_scratch) {
            2 * align256(4 * (size_t)oa) + align256((size_t)fb_scratch) + align256(8 * (size_t)kOutLen);
 }
 
-// Device bytes of a wedge block: per-vertex arrays (off, loff, win_prefix, deg, dplus, fpos, queues),
-// sliced rows, lower lists and their reverse positions, scan scratch and accumulators.
+// Device bytes of a wedge block: per-vertex arrays (off, loff, win_prefix, deg, dplus, fpos, queues,
+// boundary table), sliced rows, lower lists and their reverse positions, scan scratch, accumulators.
 size_t wedge_block_bytes(int64_t n, int64_t row_arcs, int64_t list_arcs) {
     const int64_t nn = n > 0 ? n : 1, ra = row_arcs > 0 ? row_arcs : 1, la = list_arcs > 0 ? list_arcs : 1;
     return 3 * align256(8 * (size_t)(nn + 1)) + 3 * align256(4 * (size_t)nn) + 2 * align256(8 * (size_t)nn) +
+           align256(4 * (size_t)kGridCap * (size_t)nn) +
            align256(4 * (size_t)ra) + 2 * align256(4 * (size_t)la) + align256(8 * (size_t)kGInfo) +
            align256(8 * (scan_tmp_needed(nn) + 64)) + align256(8 * (size_t)kOutLen);
 }
@@ -602,7 +603,7 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     ws.scan_tmp_len = scan_tmp_needed(n > 0 ? n : 1) + 64;
     ws.scan_tmp = c.take<int64_t>(ws.scan_tmp_len);
     ws.acc = c.take<uint64_t>(kOutLen);
-    ws.bpos = nullptr;  // boundaries searched per window (no per-vertex table)
+    ws.bpos = c.take<int32_t>((size_t)kGridCap * (size_t)n);
     ws.loff = d_loff;
     ws.lcols = d_lcols;
     ws.lower_arcs = la;
