@@ -254,10 +254,15 @@ __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __rest
 // ---------------------------------------------------------------------------------------------
 constexpr int kUnroll = 4;
 
+// Every visitor f(x) returns the previous value of x's counter; the helpers add those values into
+// sum.  NARROW: a value fits 16 bits (8- and 16-bit counters, hash counters), so kUnroll of them are
+// summed in 32 bits before one 64-bit add.
+
 // Warp-cooperative traversal of 32 segments (lane l owns cols[base_l .. base_l + len_l)):
 // flattened so that every lane takes one element per round.
-template <typename F>
-__device__ __forceinline__ void warp_flat(const int32_t* __restrict__ cols, int64_t base, int len, F&& f) {
+template <bool NARROW, typename F>
+__device__ __forceinline__ void warp_flat(const int32_t* __restrict__ cols, int64_t base, int len, F&& f,
+                                          uint64_t& sum) {
     const int l = lane_id();
     int incl = len;
 #pragma unroll
@@ -282,41 +287,60 @@ __device__ __forceinline__ void warp_flat(const int32_t* __restrict__ cols, int6
             const int oe = __shfl_sync(kFull, excl, o);
             xs[r] = t < total ? __ldg(cols + ob + (t - oe)) : 0;
         }
+        uint32_t part = 0;
 #pragma unroll
         for (int r = 0; r < kUnroll; ++r)
-            if (t0 + r * 32 + l < total) f(xs[r]);
+            if (t0 + r * 32 + l < total) {
+                if (NARROW) part += f(xs[r]);
+                else sum += f(xs[r]);
+            }
+        if (NARROW) sum += part;
     }
 }
 
-// n consecutive elements from b, read by the whole warp (coalesced), kUnroll loads in flight per lane.
-template <typename F>
-__device__ __forceinline__ void warp_run(const int32_t* __restrict__ cols, int64_t b, int64_t n, F&& f) {
+// n consecutive elements from b, read by the whole warp (coalesced), kUnroll loads in flight per
+// lane: whole chunks of 32 * kUnroll without bounds tests, then one guarded tail chunk.
+template <bool NARROW, typename F>
+__device__ __forceinline__ void warp_run(const int32_t* __restrict__ cols, int64_t b, int n, F&& f, uint64_t& sum) {
     const int l = lane_id();
-    for (int64_t k0 = 0; k0 < n; k0 += 32 * kUnroll) {
+    const int32_t* __restrict__ p = cols + b + l;
+    constexpr int kCh = 32 * kUnroll;
+    int k0 = 0;
+    for (; k0 + kCh <= n; k0 += kCh) {
         int32_t xs[kUnroll];
 #pragma unroll
+        for (int r = 0; r < kUnroll; ++r) xs[r] = __ldg(p + k0 + r * 32);
+        uint32_t part = 0;
+#pragma unroll
         for (int r = 0; r < kUnroll; ++r) {
-            const int64_t k = k0 + r * 32 + l;
-            xs[r] = k < n ? __ldg(cols + b + k) : 0;
+            if (NARROW) part += f(xs[r]);
+            else sum += f(xs[r]);
         }
+        if (NARROW) sum += part;
+    }
+    if (k0 < n) {
+        int32_t xs[kUnroll];
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) xs[r] = k0 + r * 32 + l < n ? __ldg(p + k0 + r * 32) : 0;
 #pragma unroll
         for (int r = 0; r < kUnroll; ++r)
-            if (k0 + r * 32 + l < n) f(xs[r]);
+            if (k0 + r * 32 + l < n) sum += f(xs[r]);
     }
 }
 
 // Long segments one after the other, each read by the whole warp (coalesced); short ones flattened.
-template <typename F>
-__device__ __forceinline__ void warp_segments(const int32_t* __restrict__ cols, int64_t base, int len, F&& f) {
+template <bool NARROW, typename F>
+__device__ __forceinline__ void warp_segments(const int32_t* __restrict__ cols, int64_t base, int len, F&& f,
+                                              uint64_t& sum) {
     uint32_t longs = __ballot_sync(kFull, len >= kLong);
     while (longs) {
         const int src = __ffs(longs) - 1;
         longs &= longs - 1;
         const int64_t b = __shfl_sync(kFull, base, src);
         const int n = __shfl_sync(kFull, len, src);
-        warp_run(cols, b, n, f);
+        warp_run<NARROW>(cols, b, n, f, sum);
     }
-    warp_flat(cols, base, len >= kLong ? 0 : len, f);
+    warp_flat<NARROW>(cols, base, len >= kLong ? 0 : len, f, sum);
 }
 
 // shared-memory hash table: keys[] (kEmpty = free), cnt[]; returns the counter's previous value
@@ -427,7 +451,7 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
                 base = off[wv] + f;
                 len = p > f ? p - f : 0;
             }
-            warp_flat(cols, base, len, [&](int32_t x) { a_c4 += hash_add(my_keys, my_cnt, P - 1, x); });
+            warp_flat<true>(cols, base, len, [&](int32_t x) { return hash_add(my_keys, my_cnt, P - 1, x); }, a_c4);
         }
         if (sink.batch()) {
             a_c4 = warp_sum(a_c4);
@@ -485,7 +509,7 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
                                             int64_t dm, int32_t xlo, int32_t xhi, bool first, bool last, uint32_t* cw,
                                             WinShared& sh, uint64_t& c4, uint64_t* acc) {
     const int l = lane_id();
-    auto add = [&](int32_t x) { c4 += counter_add<WIDTH, WORDS>(cw, (uint32_t)(x - xlo)); };
+    auto add = [&](int32_t x) { return counter_add<WIDTH, WORDS>(cw, (uint32_t)(x - xlo)); };
     const int ngroups = (int)((dm + 31) >> 5);
     for (;;) {
         int g = 0;
@@ -528,7 +552,7 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
                 len = 0;
             }
         }
-        warp_segments(cols, base, len, add);
+        warp_segments<WIDTH != 32>(cols, base, len, add, c4);
     }
 }
 
@@ -553,7 +577,8 @@ __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int
         const int64_t b = sh.split_base[e] + (int64_t)(t - sh.split_pre[e]) * kChunk;
         const int64_t end = sh.split_base[e] + sh.split_len[e];
         const int64_t stop = b + kChunk < end ? b + kChunk : end;
-        warp_run(cols, b, stop - b, [&](int32_t x) { c4 += counter_add<WIDTH, WORDS>(cw, (uint32_t)(x - xlo)); });
+        warp_run<WIDTH != 32>(cols, b, (int)(stop - b),
+                              [&](int32_t x) { return counter_add<WIDTH, WORDS>(cw, (uint32_t)(x - xlo)); }, c4);
     }
 }
 
