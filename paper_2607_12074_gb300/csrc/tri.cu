@@ -306,13 +306,23 @@ struct CtaSmem {
     static constexpr int W = DMAX / 32;             // words per row
     static constexpr int WS = W | 1;                // odd row stride: no bank conflicts
     static constexpr int HB = (DMAX <= 256) ? 10 : ((DMAX <= 512) ? 11 : 12);  // 4 * DMAX hash slots
+    static constexpr int FB = HB + 2;               // filter: 16 * DMAX bits, one per hash value
     int32_t L[DMAX];
     uint32_t own[DMAX];
     uint32_t R[DMAX * WS];
     int32_t hk[1 << HB];
     uint16_t hv[1 << HB];
+    uint32_t filt[(1 << FB) / 32];
     uint64_t red[32];
 };
+
+// Membership filter in front of the hash lookup: bit (top FB bits of hash32(y)) is set for every key,
+// so a clear bit proves y is not in L (most probes miss; a miss then costs one shared load).
+template <int FB>
+__device__ __forceinline__ bool filter_may_hold(const uint32_t* filt, int32_t y) {
+    const uint32_t h = hash32((uint32_t)y) >> (32 - FB);
+    return (filt[h >> 5] >> (h & 31)) & 1u;
+}
 
 template <int DMAX, int THREADS, bool BS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64_t* __restrict__ offp,
@@ -349,12 +359,19 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_tri_cta(const int64
         }
         for (int i = threadIdx.x; i < d * WS; i += THREADS) s.R[i] = 0;
         for (int i = threadIdx.x; i < (1 << S::HB); i += THREADS) s.hk[i] = kNoKey;
+        for (int i = threadIdx.x; i < (1 << S::FB) / 32; i += THREADS) s.filt[i] = 0;
         __syncthreads();
-        if (!BS)
-            for (int i = threadIdx.x; i < d; i += THREADS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
+        for (int i = threadIdx.x; i < d; i += THREADS) {
+            if (!BS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
+            const uint32_t h = hash32((uint32_t)s.L[i]) >> (32 - S::FB);
+            atomicOr(&s.filt[h >> 5], 1u << (h & 31));
+        }
         __syncthreads();
         const int32_t last = s.L[d - 1];
-        auto lookup = [&](int32_t y) { return BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y); };
+        auto lookup = [&](int32_t y) {
+            if (!filter_may_hold<S::FB>(s.filt, y)) return -1;
+            return BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
+        };
         // rows: warp per row, ordered intersection of N+(L[i]) with L
         for (int i = w; i < d - 1; i += NW) {
             const int32_t v = s.L[i];
