@@ -437,9 +437,15 @@ def main():
         achieved = alg / (seg_avg[dom] / 1000) / 1e9
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tfile):
+        if os.path.exists(tfile):  # DRAM bytes of one ncu capture, valid while the kernel is unchanged
+            import hashlib
             with open(tfile) as f:
-                traffic = json.load(f).get(dom)
+                rec = json.load(f)
+            src = os.path.join(ROOT, rec.get("source", ""))
+            if dom in rec and os.path.isfile(src):
+                with open(src, "rb") as f:
+                    if hashlib.sha256(f.read()).hexdigest()[:16] == rec.get("source_sha256_16"):
+                        traffic = rec[dom]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                     "algorithmic_bytes": alg, "kernel_ms": seg_avg[dom]}
