@@ -582,6 +582,49 @@ __device__ __forceinline__ void split_pass(const int32_t* __restrict__ cols, int
     }
 }
 
+// Everything an item (root, grid window) needs before its lower neighbours are walked.  Resolving it
+// is a chain of dependent loads (ticket, search of the item's root, the root, its grid window, its
+// list), so one thread resolves the next item while the block works on the current one.
+struct WinItem {
+    int64_t t;  // ticket; >= the item total: no more items
+    int64_t j, xlo, xhi, nwin, dm, ub;
+    int32_t u;
+    int width, sl, first, last;
+};
+
+template <int WORDS>
+__device__ __forceinline__ void resolve_item(WinItem& it, int64_t t, int64_t total, int64_t nroots,
+                                             const int64_t* __restrict__ win_prefix,
+                                             const int32_t* __restrict__ q_win, const int32_t* __restrict__ gid,
+                                             const int64_t* __restrict__ ginfo, const int32_t* __restrict__ deg,
+                                             const int32_t* __restrict__ dplus, const int64_t* __restrict__ loff) {
+    it.t = t;
+    if (t >= total) return;
+    int64_t lo = 0, hi = nroots;  // root index: last k with win_prefix[k] <= t
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (win_prefix[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const int32_t u = q_win[lo];
+    const int64_t j = t - win_prefix[lo];
+    const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
+    int64_t xlo = 0, xhi = 0;
+    int width = 32;
+    grid_window<WORDS>(gi, j, xlo, xhi, width);
+    it.last = xhi >= (int64_t)u;
+    it.xhi = it.last ? u : xhi;
+    it.xlo = xlo;
+    it.first = j == 0;
+    it.j = j;
+    it.u = u;
+    it.width = width;
+    it.nwin = gi[GI_NWIN];
+    it.sl = table_shift(it.nwin);
+    it.dm = (int64_t)deg[u] - dplus[u];
+    it.ub = loff[u];
+}
+
 template <int MINB>
 __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* __restrict__ off,
                                                               const int32_t* __restrict__ cols,
@@ -599,48 +642,38 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
                                                               uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t* cw = reinterpret_cast<uint32_t*>(smem_raw);
-    __shared__ int64_t s_item;
+    constexpr int WORDS = win_words(MINB);
+    __shared__ WinItem s_next;
     __shared__ WinShared sh;
     __shared__ uint64_t red[32];
     const int64_t nroots = (int64_t)acc[Q_C4_WIN];
     const int64_t total = win_prefix[nroots];
     unsigned long long* ticket = (unsigned long long*)&acc[T_C4_WIN];
+    const bool table = bpos != nullptr;
     uint64_t c4 = 0;
+    if (threadIdx.x == 0)
+        resolve_item<WORDS>(s_next, (int64_t)atomicAdd(ticket, 1ull), total, nroots, win_prefix, q_win, gid, ginfo,
+                            deg, dplus, loff);
+    __syncthreads();
     for (;;) {
+        const WinItem it = s_next;
+        if (it.t >= total) break;
+        const int32_t u = it.u;
+        const int64_t j = it.j, xlo = it.xlo, xhi = it.xhi, nwin = it.nwin, dm = it.dm, ub = it.ub;
+        const int width = it.width, sl = it.sl;
+        const bool first = it.first, last = it.last;
         if (threadIdx.x == 0) {
-            s_item = (int64_t)atomicAdd(ticket, 1ull);
             sh.group = 0;
             sh.nsplit = 0;
             sh.chunk = 0;
         }
-        __syncthreads();
-        const int64_t t = s_item;
-        if (t >= total) break;
-        int64_t lo = 0, hi = nroots;  // root index: last k with win_prefix[k] <= t
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (win_prefix[mid] <= t) lo = mid;
-            else hi = mid;
-        }
-        const int32_t u = q_win[lo];
-        const int64_t j = t - win_prefix[lo];
-        const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
-        int64_t xlo = 0, xhi = 0;
-        int width = 32;
-        grid_window<win_words(MINB)>(gi, j, xlo, xhi, width);
-        const bool last = xhi >= (int64_t)u;
-        if (last) xhi = u;
-        const bool first = j == 0;
-        const int64_t nwin = gi[GI_NWIN];
-        const bool table = bpos != nullptr;
-        const int sl = table_shift(nwin);
-        const int64_t dm = (int64_t)deg[u] - dplus[u];
-        const int64_t ub = loff[u];
-        constexpr int WORDS = win_words(MINB);
         const int per = 32 / width;
         const int words = (int)((xhi - xlo + per - 1) / per);
         for (int i = threadIdx.x; i < words; i += kWinThreads) cw[i] = 0;
-        __syncthreads();
+        __syncthreads();  // every thread holds this item; counters and work counters are reset
+        if (threadIdx.x == 0)  // the next item, resolved while the block walks this one
+            resolve_item<WORDS>(s_next, (int64_t)atomicAdd(ticket, 1ull), total, nroots, win_prefix, q_win, gid,
+                                ginfo, deg, dplus, loff);
         uint64_t a_c4 = 0;
         if (width == 8)
             window_pass<8, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
@@ -674,7 +707,7 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
         } else {
             c4 += a_c4;
         }
-        __syncthreads();  // every thread is done with this item's shared state before thread 0 resets it
+        __syncthreads();  // every thread is done with this item's shared state; s_next is resolved
     }
     c4 = block_sum_u64(c4, red);
     if (threadIdx.x == 0 && c4) atomicAdd((unsigned long long*)&acc[ACC_C4], (unsigned long long)c4);
