@@ -309,13 +309,19 @@ struct CtaSmem {
     static constexpr int W = DMAX / 32;             // words per row
     static constexpr int WS = W | 1;                // odd row stride: no bank conflicts
     static constexpr int HB = (DMAX <= 256) ? 10 : ((DMAX <= 512) ? 11 : 12);  // 4 * DMAX hash slots
-    static constexpr int FB = HB + 2;               // filter: 16 * DMAX bits, one per hash value
+    static constexpr int FB = HB + 2;                                          // filter: 16 bits per key
+    // The 256 mode resolves every row's probe range up front (short lists: one binary search per
+    // thread); the larger modes keep the warp-wide search per row, which measured faster on their
+    // longer lists.
+    static constexpr bool PRE = DMAX <= 256;
     int32_t L[DMAX];
     uint32_t own[DMAX];
     uint32_t R[DMAX * WS];
     int32_t hk[1 << HB];
     uint16_t hv[1 << HB];
     uint32_t filt[(1 << FB) / 32];
+    int64_t rb[PRE ? DMAX : 1];  // row i probes colsp[rb[i], re[i]): N+(L[i]) from its first element >= L[i+1]
+    int64_t re[PRE ? DMAX : 1];
     uint64_t red[32];
 };
 
@@ -368,6 +374,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
             if (!BS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
             const uint32_t h = hash32((uint32_t)s.L[i]) >> (32 - S::FB);
             atomicOr(&s.filt[h >> 5], 1u << (h & 31));
+            if (S::PRE && i < d - 1) {  // every row's probe range at once: dependent loads overlap across rows
+                const int32_t v = s.L[i];
+                const int64_t b = offp[v], e = offp[v + 1];
+                s.rb[i] = b + lower_bound_i32(colsp + b, e - b, s.L[i + 1]);
+                s.re[i] = e;
+            }
         }
         __syncthreads();
         const int32_t last = s.L[d - 1];
@@ -377,11 +389,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
         };
         // rows: warp per row, ordered intersection of N+(L[i]) with L
         for (int i = w; i < d - 1; i += NW) {
-            const int32_t v = s.L[i];
             const int32_t next = s.L[i + 1];
-            const int64_t e = offp[v + 1];
-            int64_t b = offp[v];
-            if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
+            int64_t b, e;
+            if (S::PRE) {
+                b = s.rb[i];
+                e = s.re[i];
+            } else {
+                const int32_t v = s.L[i];
+                e = offp[v + 1];
+                b = offp[v];
+                if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
+            }
             uint32_t hits = 0;
             auto probe = [&](int32_t y, int64_t p) {
                 if (y >= next && y <= last) {
