@@ -119,6 +119,22 @@ def oracle_sample_rate(scale: int, threads: int = 0):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def max_over_ranks(value: float, world: int, device: str) -> float:
+    """The largest value over all ranks (a replicated job takes as long as its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(m: int, world: int, step_ms: float) -> float:
+    """Whole-job edges/s of `world` replicas that each count the m-edge graph in step_ms (the max)."""
+    return world * m / (step_ms / 1000.0)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -394,10 +410,7 @@ def main():
     harp.harp_set_profiling(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(t_step, world, "cuda")
 
     # ---- end to end through the public API from pinned host memory (build + count per step)
     src_h = torch.from_numpy(g.src).pin_memory()
@@ -455,7 +468,7 @@ def main():
         cpu = {"value": r["m"] / r["seconds"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": f"R-MAT scale 18 (same a,b,c, ef 16, seed 1; m={r['m']}), oracle count4_combo, "
                          f"{r['seconds']:.1f} s"}
-    value = world * m / (t_step / 1000)
+    value = replica_throughput(m, world, t_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
