@@ -328,6 +328,8 @@ def run_partitioned(args):
                        "n": g.n, "m": m, "parallelism": "single", "l2": "inputs larger than L2"},
             "partition": {"blocks": st["partitions"], "device_peak_bytes": st["device_peak_bytes"],
                           "halo_arcs": st["halo_arcs"], "h2d_bytes": st["h2d_bytes"], "host_ms": st["host_ms"],
+                          "host_graph_ms": st["graph_ms"], "host_cut_ms": st["cut_ms"],
+                          "device_tri_ms": st["tri_ms"], "device_wedge_ms": st["wedge_ms"],
                           "transfer_ms": st["transfer_ms"], "device_ms": st["device_ms"],
                           "transfer_share": st["transfer_ms"] / (1000 * wall)},
             "generate_s": t_gen, "clocks": clk, "counts": [int(x) for x in counts]}

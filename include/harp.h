@@ -246,6 +246,10 @@ typedef struct harp_partition_stats {
     double host_ms;              /* host work: rank-order graph, range cuts, halo assembly, closure */
     double transfer_ms;          /* host <-> device copies (CUDA events around the copies)        */
     double device_ms;            /* counting kernels (CUDA events around the kernels)             */
+    double graph_ms;             /* part of host_ms: the rank-order graph                         */
+    double cut_ms;               /* part of host_ms: cutting the triangle ranges and wedge blocks */
+    double tri_ms;               /* part of device_ms: triangle blocks                            */
+    double wedge_ms;             /* part of device_ms: wedge blocks                               */
 } harp_partition_stats;
 
 /* src, dst: HOST int32[m_in] (read only).  budget_bytes: device bytes one range may use (0 = half

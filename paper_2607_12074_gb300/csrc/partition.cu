@@ -16,6 +16,7 @@
 // every count is exact.  Ranges are cut by one linear sweep each, as long as the exact halo size
 // fits the budget; a single vertex (or x-value) whose halo does not fit gives HARP_ENOMEM.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -47,146 +48,192 @@ void parallel_for(int64_t n, F&& f) {
     for (auto& x : th) x.join();
 }
 
-// LSD radix sort of 64-bit keys on the host (16-bit digits over the significant bits), threads split
-// every pass by contiguous slices so the sort stays stable.
-void host_radix_sort(std::vector<uint64_t>& a, int bits) {
-    const size_t n = a.size();
-    if (n < 2 || bits <= 0) return;
-    std::vector<uint64_t> b(n);
-    unsigned nt = std::thread::hardware_concurrency();
-    if (nt < 1) nt = 1;
-    if (nt > 64) nt = 64;
-    if (n < (size_t)1 << 16) nt = 1;
-    const int digit = 16;
-    std::vector<std::vector<size_t>> hist(nt, std::vector<size_t>((size_t)1 << digit));
-    for (int shift = 0; shift < bits; shift += digit) {
-        const uint64_t mask = ((uint64_t)1 << digit) - 1;
-        auto slice = [&](unsigned t, size_t& lo, size_t& hi) {
-            lo = n * t / nt;
-            hi = n * (t + 1) / nt;
-        };
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nt; ++t)
-            th.emplace_back([&, t] {
-                size_t lo, hi;
-                slice(t, lo, hi);
-                std::fill(hist[t].begin(), hist[t].end(), 0);
-                for (size_t i = lo; i < hi; ++i) hist[t][(a[i] >> shift) & mask]++;
-            });
-        for (auto& x : th) x.join();
-        th.clear();
-        size_t run = 0;
-        for (size_t d = 0; d < ((size_t)1 << digit); ++d)
-            for (unsigned t = 0; t < nt; ++t) {
-                const size_t c = hist[t][d];
-                hist[t][d] = run;
-                run += c;
-            }
-        for (unsigned t = 0; t < nt; ++t)
-            th.emplace_back([&, t] {
-                size_t lo, hi;
-                slice(t, lo, hi);
-                std::vector<size_t>& h = hist[t];
-                for (size_t i = lo; i < hi; ++i) b[h[(a[i] >> shift) & mask]++] = a[i];
-            });
-        for (auto& x : th) x.join();
-        a.swap(b);
+// Allocator whose resize leaves new elements uninitialised: multi-gigabyte arrays that are written in
+// full right after (rows, halo copies, device read-backs) are not zero-filled first on one core.
+template <typename T>
+struct NoInit : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = NoInit<U>;
+    };
+    NoInit() = default;
+    template <typename U>
+    NoInit(const NoInit<U>&) {}
+    template <typename U>
+    void construct(U*) noexcept {}
+    template <typename U, typename... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
     }
-}
-
-int bits_of(uint64_t x) {
-    int b = 0;
-    while (b < 64 && ((uint64_t)1 << b) <= x) ++b;
-    return b < 1 ? 1 : b;
-}
+};
+template <typename T>
+using buf = std::vector<T, NoInit<T>>;
 
 // The simple graph in global rank order: symmetric CSR with sorted rows (host memory).
 struct RankGraph {
     int64_t n = 0, m = 0;
     std::vector<int64_t> off;
-    std::vector<int32_t> cols;
+    buf<int32_t> cols;
     std::vector<int32_t> deg, dplus;  // by rank
     std::vector<int64_t> offp;        // global out-arc numbering: N+(r) holds out-arcs offp[r] ..
     int64_t n1 = 0;                   // first rank of degree >= 2
 };
 
+// f(lo, hi) over chunks of [0, n) taken from a shared counter by every host thread (rows of very
+// different lengths, e.g. hubs at the start of the id range, stay balanced).
+template <typename F>
+void parallel_dynamic(int64_t n, int64_t chunk, F&& f) {
+    const unsigned nt = (n + chunk - 1) / chunk < 2 ? 1 : host_threads();
+    std::atomic<int64_t> next{0};
+    auto run = [&] {
+        for (;;) {
+            const int64_t lo = next.fetch_add(chunk);
+            if (lo >= n) return;
+            f(lo, lo + chunk < n ? lo + chunk : n);
+        }
+    };
+    if (nt == 1) {
+        run();
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(run);
+    for (auto& x : th) x.join();
+}
+
+// The rank-order CSR without atomics: arcs are partitioned by source-id bucket (per-thread histograms
+// and thread-private cursors), each bucket - a few thousand rows - is turned into its rows locally,
+// every row is sorted and deduplicated, the rank order (degree, id) is a counting sort by degree, and
+// the rows are copied to their ranks with relabelled entries and sorted again.
 harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst, RankGraph& g) {
-    std::vector<uint64_t> keys;
+    int sh = 0;  // bucket of a vertex: v >> sh, about 1024 buckets
+    while ((n >> sh) > 1024) ++sh;
+    const int64_t nb = (n >> sh) + 1;
+    const unsigned nt = m_in < (1 << 16) ? 1 : host_threads();
+    std::vector<std::vector<int64_t>> hist(nt, std::vector<int64_t>((size_t)nb, 0));
+    std::vector<uint8_t> bad(nt, 0);
+    auto slice = [&](unsigned t, int64_t& lo, int64_t& hi) {
+        lo = m_in * (int64_t)t / (int64_t)nt;
+        hi = m_in * (int64_t)(t + 1) / (int64_t)nt;
+    };
+    {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t)
+            th.emplace_back([&, t] {
+                int64_t lo, hi;
+                slice(t, lo, hi);
+                std::vector<int64_t>& h = hist[t];
+                for (int64_t e = lo; e < hi; ++e) {
+                    const int32_t u = src[e], v = dst[e];
+                    if (u < 0 || v < 0 || u >= n || v >= n) {
+                        bad[t] = 1;
+                        continue;
+                    }
+                    if (u == v) continue;
+                    h[(size_t)(u >> sh)]++;
+                    h[(size_t)(v >> sh)]++;
+                }
+            });
+        for (auto& x : th) x.join();
+    }
+    for (uint8_t x : bad)
+        if (x) return HARP_EINVAL;
+    std::vector<int64_t> bstart((size_t)nb + 1, 0);
+    for (int64_t k = 0; k < nb; ++k) {  // bucket k: [bstart[k], bstart[k+1]); thread t's part in order
+        int64_t run = bstart[(size_t)k];
+        for (unsigned t = 0; t < nt; ++t) {
+            const int64_t c = hist[t][(size_t)k];
+            hist[t][(size_t)k] = run;
+            run += c;
+        }
+        bstart[(size_t)k + 1] = run;
+    }
+    const int64_t A = bstart[(size_t)nb];
+    buf<uint64_t> pairs;  // (row << 32) | column, in bucket order
     try {
-        keys.resize((size_t)m_in);
+        pairs.resize((size_t)(A > 0 ? A : 1));
     } catch (...) {
         return HARP_ENOMEM;
     }
-    const int b = bits_of((uint64_t)n);
-    const uint64_t none = ~(uint64_t)0;  // self-loops: sorts last, dropped below
-    std::vector<uint8_t> bad(host_threads(), 0);
-    parallel_for(m_in, [&](int64_t lo, int64_t hi, unsigned t) {
-        for (int64_t e = lo; e < hi; ++e) {
-            const int32_t u = src[e], v = dst[e];
-            if (u < 0 || v < 0 || u >= n || v >= n) {
-                bad[t] = 1;
-                keys[(size_t)e] = none;
-                continue;
-            }
-            keys[(size_t)e] = u == v ? none
-                                     : (((uint64_t)(u < v ? u : v) << b) | (uint64_t)(u < v ? v : u));
-        }
-    });
-    for (uint8_t x : bad)
-        if (x) return HARP_EINVAL;
-    host_radix_sort(keys, 64);
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    if (!keys.empty() && keys.back() == none) keys.pop_back();
-    g.n = n;
-    g.m = (int64_t)keys.size();
-    const uint64_t lowmask = ((uint64_t)1 << b) - 1;
+    {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t)
+            th.emplace_back([&, t] {
+                int64_t lo, hi;
+                slice(t, lo, hi);
+                std::vector<int64_t>& cur = hist[t];
+                for (int64_t e = lo; e < hi; ++e) {
+                    const int32_t u = src[e], v = dst[e];
+                    if (u == v) continue;
+                    pairs[(size_t)cur[(size_t)(u >> sh)]++] = ((uint64_t)(uint32_t)u << 32) | (uint32_t)v;
+                    pairs[(size_t)cur[(size_t)(v >> sh)]++] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)u;
+                }
+            });
+        for (auto& x : th) x.join();
+    }
+    std::vector<std::vector<int64_t>>().swap(hist);
+    // each bucket into its rows (positions of the id-order CSR are the bucket's own range)
+    std::vector<int64_t> off0((size_t)n + 1, 0);
+    buf<int32_t> c0;
+    try {
+        c0.resize((size_t)(A > 0 ? A : 1));
+    } catch (...) {
+        return HARP_ENOMEM;
+    }
     std::vector<int32_t> deg0((size_t)n, 0);
-    parallel_for(g.m, [&](int64_t lo, int64_t hi, unsigned) {
-        for (int64_t i = lo; i < hi; ++i) {
-            __atomic_fetch_add(&deg0[keys[(size_t)i] >> b], 1, __ATOMIC_RELAXED);
-            __atomic_fetch_add(&deg0[keys[(size_t)i] & lowmask], 1, __ATOMIC_RELAXED);
+    parallel_dynamic(nb, 1, [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t r0 = k << sh, r1 = std::min<int64_t>((k + 1) << sh, n);
+            if (r0 >= r1) continue;
+            std::vector<int64_t> pos((size_t)(r1 - r0 + 1), 0);
+            for (int64_t i = bstart[(size_t)k]; i < bstart[(size_t)k + 1]; ++i)
+                pos[(size_t)((int64_t)(pairs[(size_t)i] >> 32) - r0) + 1]++;
+            for (int64_t r = 0; r < r1 - r0; ++r) pos[(size_t)r + 1] += pos[(size_t)r];
+            for (int64_t r = r0; r < r1; ++r) off0[(size_t)r] = bstart[(size_t)k] + pos[(size_t)(r - r0)];
+            for (int64_t i = bstart[(size_t)k]; i < bstart[(size_t)k + 1]; ++i) {
+                const uint64_t pr = pairs[(size_t)i];
+                c0[(size_t)(bstart[(size_t)k] + pos[(size_t)((int64_t)(pr >> 32) - r0)]++)] = (int32_t)(uint32_t)pr;
+            }
+            for (int64_t r = r0; r < r1; ++r) {  // after the scatter pos[r - r0] is the start of row r + 1
+                auto b = c0.begin() + off0[(size_t)r];
+                auto e = c0.begin() + bstart[(size_t)k] + pos[(size_t)(r - r0)];
+                std::sort(b, e);
+                deg0[(size_t)r] = (int32_t)(std::unique(b, e) - b);
+            }
         }
     });
+    off0[(size_t)n] = A;
+    buf<uint64_t>().swap(pairs);
     // rank = (degree, id): counting sort by degree, ids ascending inside a degree
     int32_t maxd = 0;
     for (int32_t d : deg0) maxd = d > maxd ? d : maxd;
     std::vector<int64_t> start((size_t)maxd + 2, 0);
     for (int32_t d : deg0) start[(size_t)d + 1]++;
     for (size_t d = 0; d + 1 < start.size(); ++d) start[d + 1] += start[d];
-    std::vector<int32_t> rank((size_t)n);
-    for (int64_t v = 0; v < n; ++v) rank[(size_t)v] = (int32_t)start[(size_t)deg0[(size_t)v]]++;
-    std::vector<uint64_t> arcs;
+    std::vector<int32_t> rank((size_t)n), order((size_t)n);
+    for (int64_t v = 0; v < n; ++v) {
+        const int32_t r = (int32_t)start[(size_t)deg0[(size_t)v]]++;
+        rank[(size_t)v] = r;
+        order[(size_t)r] = (int32_t)v;
+    }
+    g.n = n;
+    g.off.assign((size_t)n + 1, 0);
+    for (int64_t r = 0; r < n; ++r) g.off[(size_t)r + 1] = g.off[(size_t)r] + deg0[(size_t)order[(size_t)r]];
+    g.m = g.off[(size_t)n] / 2;
     try {
-        arcs.resize(2 * keys.size());
+        g.cols.resize((size_t)g.off[(size_t)n]);
     } catch (...) {
         return HARP_ENOMEM;
     }
-    parallel_for(g.m, [&](int64_t lo, int64_t hi, unsigned) {
-        for (int64_t i = lo; i < hi; ++i) {
-            const uint64_t k = keys[(size_t)i];
-            const uint64_t a = (uint64_t)rank[k >> b], c = (uint64_t)rank[k & lowmask];
-            arcs[2 * (size_t)i] = (a << 32) | c;
-            arcs[2 * (size_t)i + 1] = (c << 32) | a;
+    parallel_dynamic(n, 1024, [&](int64_t lo, int64_t hi) {
+        for (int64_t r = lo; r < hi; ++r) {
+            const int32_t v = order[(size_t)r];
+            const int64_t b0 = off0[(size_t)v], d = deg0[(size_t)v], b = g.off[(size_t)r];
+            for (int64_t k = 0; k < d; ++k) g.cols[(size_t)(b + k)] = rank[(size_t)c0[(size_t)(b0 + k)]];
+            std::sort(g.cols.begin() + b, g.cols.begin() + b + d);
         }
     });
-    std::vector<uint64_t>().swap(keys);
-    host_radix_sort(arcs, 32 + b);
-    const int64_t A = (int64_t)arcs.size();
-    g.off.assign((size_t)n + 1, 0);
-    g.cols.resize(arcs.size());
-    // rows are sorted: off[r] = first arc of a row >= r, set where the row changes
-    parallel_for(A, [&](int64_t lo, int64_t hi, unsigned) {
-        for (int64_t i = lo; i < hi; ++i) {
-            g.cols[(size_t)i] = (int32_t)(arcs[(size_t)i] & 0xffffffffull);
-            const int64_t r = (int64_t)(arcs[(size_t)i] >> 32);
-            const int64_t rp = i > 0 ? (int64_t)(arcs[(size_t)i - 1] >> 32) : -1;
-            for (int64_t x = rp + 1; x <= r; ++x) g.off[(size_t)x] = i;
-            if (i == A - 1)
-                for (int64_t x = r + 1; x <= n; ++x) g.off[(size_t)x] = A;
-        }
-    });
-    if (A == 0) std::fill(g.off.begin(), g.off.end(), 0);
-    std::vector<uint64_t>().swap(arcs);
+    buf<int32_t>().swap(c0);
     g.deg.resize((size_t)n);
     g.dplus.resize((size_t)n);
     parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
@@ -265,29 +312,49 @@ inline int32_t out_nbr(const RankGraph& g, int64_t r, int64_t k) {
     return g.cols[(size_t)(g.off[(size_t)r + 1] - g.dplus[(size_t)r] + k)];
 }
 
-// One sweep: extend the range while its exact halo (distinct out-lists) fits the budget.
+// Exact out-arcs of the triangle halo of [lo, hi) (distinct out-lists of R and N+(R)), on all host
+// cores: each vertex is claimed once through its mark byte.  mark is all zero on entry and on return.
+int64_t tri_extent(const RankGraph& g, int64_t lo, int64_t hi, std::vector<uint8_t>& mark) {
+    std::vector<int64_t> part(host_threads(), 0);
+    std::vector<std::vector<int32_t>> claimed(host_threads());
+    parallel_for(hi - lo, [&](int64_t a, int64_t b, unsigned t) {
+        int64_t outs = 0;
+        auto add = [&](int32_t v) {
+            if (__atomic_exchange_n(&mark[(size_t)v], (uint8_t)1, __ATOMIC_RELAXED) == 0) {
+                claimed[t].push_back(v);
+                outs += g.dplus[(size_t)v];
+            }
+        };
+        for (int64_t u = lo + a; u < lo + b; ++u) {
+            add((int32_t)u);
+            for (int64_t k = 0; k < g.dplus[(size_t)u]; ++k) add(out_nbr(g, u, k));
+        }
+        part[t] = outs;
+    });
+    int64_t outs = 0;
+    for (size_t t = 0; t < part.size(); ++t) {
+        outs += part[t];
+        for (int32_t v : claimed[t]) mark[(size_t)v] = 0;
+    }
+    return outs;
+}
+
+// Ranges of triangle anchors: the whole rank space when its halo fits, else one sweep that extends
+// each range while its exact halo fits the budget.
 harp_status cut_triangle_ranges(const RankGraph& g, uint64_t budget, int32_t parts, int64_t fb_scratch,
                                 std::vector<TriBlock>& out, uint64_t& peak) {
     const int64_t n = g.n;
     std::vector<uint8_t> mark((size_t)n, 0);
     std::vector<int32_t> touched;
-    auto extent = [&](int64_t lo, int64_t hi) {  // exact out-arcs of the halo of [lo, hi)
-        int64_t outs = 0;
-        touched.clear();
-        auto add = [&](int32_t v) {
-            if (!mark[(size_t)v]) {
-                mark[(size_t)v] = 1;
-                touched.push_back(v);
-                outs += g.dplus[(size_t)v];
-            }
-        };
-        for (int64_t u = lo; u < hi; ++u) {
-            add((int32_t)u);
-            for (int64_t k = 0; k < g.dplus[(size_t)u]; ++k) add(out_nbr(g, u, k));
+    auto extent = [&](int64_t lo, int64_t hi) { return tri_extent(g, lo, hi, mark); };
+    if (parts == 0) {
+        const int64_t all = extent(0, n);
+        if (tri_block_bytes(n, all, fb_scratch) <= budget) {
+            peak = std::max<uint64_t>(peak, tri_block_bytes(n, all, fb_scratch));
+            out.push_back({0, n});
+            return HARP_OK;
         }
-        for (int32_t v : touched) mark[(size_t)v] = 0;
-        return outs;
-    };
+    }
     if (parts > 0) {
         for (int32_t k = 0; k < parts; ++k) {
             const TriBlock b{n * k / parts, n * (k + 1) / parts};
@@ -371,57 +438,96 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
             lo = hi;
         }
     }
-    // x-slices per root range: a histogram, by x, of the row elements the block would hold
-    std::vector<int64_t> hist((size_t)n, 0);
+    // x-slices per root range, cut from a histogram of the row elements the block would hold, counted
+    // per x-bucket (at most 65,536 buckets, per-thread counts, no atomics); slices end on bucket
+    // boundaries, and a bucket that cannot fit alone is cut exactly, per x.
+    int bs = 0;
+    while ((n >> bs) >= 65536) ++bs;
+    const int64_t nbk = (n >> bs) + 1;
+    const unsigned nt = host_threads();
+    std::vector<std::vector<int64_t>> hist(nt, std::vector<int64_t>((size_t)nbk, 0));
+    std::vector<int64_t> hsum((size_t)nbk, 0);
     std::vector<uint8_t> mark((size_t)n, 0);
-    std::vector<int32_t> lower;
+    std::vector<std::vector<int32_t>> lower(nt);
+    std::vector<int32_t> all;
     for (const auto& r : ranges) {
         const int64_t lo = r.first, hi = r.second;
         if (lo >= hi) continue;
         int64_t la = 0;
-        lower.clear();
-        for (int64_t u = lo; u < hi; ++u) {
-            const int64_t dm = list_arcs_of(g, u);
-            la += dm;
-            for (int64_t a = 0; a < dm; ++a) {
-                const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
-                if (!mark[(size_t)w]) {
-                    mark[(size_t)w] = 1;
-                    lower.push_back(w);
+        for (int64_t u = lo; u < hi; ++u) la += list_arcs_of(g, u);
+        for (auto& l : lower) l.clear();
+        parallel_for(hi - lo, [&](int64_t a0, int64_t b0, unsigned t) {
+            for (int64_t u = lo + a0; u < lo + b0; ++u) {
+                const int64_t dm = list_arcs_of(g, u);
+                for (int64_t a = 0; a < dm; ++a) {
+                    const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
+                    if (__atomic_exchange_n(&mark[(size_t)w], (uint8_t)1, __ATOMIC_RELAXED) == 0) lower[t].push_back(w);
                 }
             }
-        }
+        });
+        all.clear();
+        for (auto& l : lower) all.insert(all.end(), l.begin(), l.end());
         const int64_t xa = g.n1, xb = hi;  // opposite vertices of degree >= 2, below the range's end
-        for (int32_t w : lower) {
-            mark[(size_t)w] = 0;
+        auto seg = [&](int32_t w, int64_t x0, int64_t x1, auto&& visit) {  // row w's elements in [x0, x1)
             const auto b = g.cols.begin() + g.off[(size_t)w], e = g.cols.begin() + g.off[(size_t)w + 1];
-            for (auto it = std::lower_bound(b, e, (int32_t)xa); it != e && *it < xb; ++it) hist[(size_t)*it]++;
+            for (auto it = std::lower_bound(b, e, (int32_t)x0); it != e && *it < x1; ++it) visit(*it);
+        };
+        {
+            std::vector<std::thread> th;
+            for (unsigned t = 0; t < nt; ++t)
+                th.emplace_back([&, t] {
+                    std::vector<int64_t>& h = hist[t];
+                    std::fill(h.begin(), h.end(), 0);
+                    const size_t a0 = all.size() * t / nt, b0 = all.size() * (t + 1) / nt;
+                    for (size_t k = a0; k < b0; ++k) seg(all[k], xa, xb, [&](int32_t x) { h[(size_t)(x >> bs)]++; });
+                });
+            for (auto& x : th) x.join();
         }
-        if (parts > 0 || xa >= xb) {
-            int64_t rows = 0;
-            for (int64_t x = xa; x < xb; ++x) rows += hist[(size_t)x];
-            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
+        for (int64_t k = 0; k < nbk; ++k) {
+            int64_t c = 0;
+            for (unsigned t = 0; t < nt; ++t) c += hist[t][(size_t)k];
+            hsum[(size_t)k] = c;
+        }
+        for (int32_t w : all) mark[(size_t)w] = 0;
+        int64_t rows_total = 0;
+        for (int64_t k = 0; k < nbk; ++k) rows_total += hsum[(size_t)k];
+        if (parts > 0 || xa >= xb || wedge_block_bytes(n, rows_total, la) <= budget) {
+            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows_total, la));
             out.push_back({lo, hi, 0, n});
-        } else {
-            int64_t x0 = xa, rows = 0;
-            for (int64_t x = xa; x < xb; ++x) {
-                const int64_t h = hist[(size_t)x];
-                if (wedge_block_bytes(n, rows + h, la) > budget) {
-                    if (x == x0) {
-                        for (int64_t y = xa; y < xb; ++y) hist[(size_t)y] = 0;
-                        return HARP_ENOMEM;  // one x-value's rows alone do not fit
-                    }
-                    peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
-                    out.push_back({lo, hi, x0 == xa ? 0 : x0, x});
-                    x0 = x;
-                    rows = 0;
-                }
-                rows += h;
-            }
-            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
-            out.push_back({lo, hi, x0 == xa ? 0 : x0, n});
+            continue;
         }
-        for (int64_t x = xa; x < xb; ++x) hist[(size_t)x] = 0;
+        int64_t x0 = xa, rows = 0;
+        auto close = [&](int64_t x) {  // the slice [x0, x) holds `rows` row elements
+            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows, la));
+            out.push_back({lo, hi, x0 == xa ? 0 : x0, x});
+            x0 = x;
+            rows = 0;
+        };
+        for (int64_t k = xa >> bs; k <= (xb - 1) >> bs; ++k) {
+            const int64_t h = hsum[(size_t)k];
+            if (wedge_block_bytes(n, rows + h, la) <= budget) {
+                rows += h;
+                continue;
+            }
+            const int64_t kb = std::max<int64_t>(k << bs, xa), ke = std::min<int64_t>((k + 1) << bs, xb);
+            if (rows > 0 && wedge_block_bytes(n, h, la) <= budget) {  // close before the bucket
+                close(kb);
+                rows = h;
+                continue;
+            }
+            // the bucket does not fit beside (or at all): cut it per x with exact counts
+            std::vector<int64_t> px((size_t)(ke - kb), 0);
+            for (int32_t w : all) seg(w, kb, ke, [&](int32_t x) { px[(size_t)(x - kb)]++; });
+            for (int64_t x = kb; x < ke; ++x) {
+                const int64_t c = px[(size_t)(x - kb)];
+                if (wedge_block_bytes(n, rows + c, la) > budget) {
+                    if (rows == 0) return HARP_ENOMEM;  // one x-value's rows alone do not fit
+                    close(x);
+                }
+                rows += c;
+            }
+        }
+        close(n);
     }
     return HARP_OK;
 }
@@ -430,18 +536,19 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
 struct PartSums {
     uint64_t T = 0, K4 = 0, C4 = 0, PAWSUM = 0;
     std::vector<uint32_t> te;  // global out-arc numbering
-    double transfer_ms = 0, device_ms = 0;
+    double transfer_ms = 0, device_ms = 0, tri_ms = 0, wedge_ms = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // copies in | kernels | copies out | end
 };
 
 // Milliseconds between the recorded phase events of one block (after it synchronised).
-void add_phase_times(PartSums& sum) {
+void add_phase_times(PartSums& sum, bool wedge) {
     float a = 0, b = 0, c = 0;
     if (cudaEventElapsedTime(&a, sum.ev[0], sum.ev[1]) == cudaSuccess &&
         cudaEventElapsedTime(&b, sum.ev[1], sum.ev[2]) == cudaSuccess &&
         cudaEventElapsedTime(&c, sum.ev[2], sum.ev[3]) == cudaSuccess) {
         sum.transfer_ms += a + c;
         sum.device_ms += b;
+        (wedge ? sum.wedge_ms : sum.tri_ms) += b;
     }
 }
 
@@ -463,7 +570,7 @@ harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev,
     std::vector<int64_t> offp((size_t)n + 1, 0);
     for (int64_t v = 0; v < n; ++v) offp[(size_t)v + 1] = offp[(size_t)v] + (in[(size_t)v] ? g.dplus[(size_t)v] : 0);
     const int64_t outs = offp[(size_t)n];
-    std::vector<int32_t> colsp((size_t)(outs > 0 ? outs : 1));
+    buf<int32_t> colsp((size_t)(outs > 0 ? outs : 1));
     parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
         for (int64_t v = lo; v < hi; ++v) {
             const int64_t len = offp[(size_t)v + 1] - offp[(size_t)v];
@@ -511,7 +618,7 @@ harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev,
     cudaEventRecord(sum.ev[1], s);
     if (st == HARP_OK && n > 0) st = count_triangles_k4(&view, ws, plan, s);
     cudaEventRecord(sum.ev[2], s);
-    std::vector<uint32_t> te_local((size_t)outs);
+    buf<uint32_t> te_local((size_t)outs);
     uint64_t acc[kOutLen] = {0};
     if (st == HARP_OK) {
         e = cudaMemcpyAsync(acc, ws.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
@@ -521,7 +628,7 @@ harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev,
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         st = check_cuda(e);
         if (st == HARP_OK && acc[ACC_ERR]) st = HARP_EDEVICE;
-        if (st == HARP_OK) add_phase_times(sum);
+        if (st == HARP_OK) add_phase_times(sum, false);
     }
     cudaFreeAsync(base, s);
     if (st != HARP_OK) return st;
@@ -545,7 +652,7 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     for (int64_t u = 0; u < n; ++u)
         loff[(size_t)u + 1] = loff[(size_t)u] + ((u >= blk.lo && u < blk.hi) ? list_arcs_of(g, u) : 0);
     const int64_t la = loff[(size_t)n];
-    std::vector<int32_t> lcols((size_t)(la > 0 ? la : 1));
+    buf<int32_t> lcols((size_t)(la > 0 ? la : 1));
     std::vector<uint8_t> in((size_t)n, 0);
     for (int64_t u = blk.lo; u < blk.hi; ++u) {
         const int64_t len = loff[(size_t)u + 1] - loff[(size_t)u];
@@ -573,7 +680,7 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     for (int64_t w = 0; w < n; ++w) off[(size_t)w + 1] += off[(size_t)w];
     const int64_t ra = off[(size_t)n];
     if (la == 0 || ra == 0) return HARP_OK;  // no root or no opposite vertex: nothing to count here
-    std::vector<int32_t> cols((size_t)ra);
+    buf<int32_t> cols((size_t)ra);
     parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
         for (int64_t w = lo; w < hi; ++w) {
             const int64_t len = off[(size_t)w + 1] - off[(size_t)w];
@@ -642,7 +749,7 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         st = check_cuda(e);
         if (st == HARP_OK && acc[ACC_ERR]) st = HARP_EDEVICE;
-        if (st == HARP_OK) add_phase_times(sum);
+        if (st == HARP_OK) add_phase_times(sum, true);
     }
     cudaFreeAsync(base, s);
     if (st != HARP_OK) return st;
@@ -665,6 +772,7 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     const auto t0 = std::chrono::steady_clock::now();
     RankGraph g;
     HARP_TRY(build_rank_graph(n, m_in, src, dst, g));
+    const auto t1 = std::chrono::steady_clock::now();
     if (budget_bytes == 0) {
         size_t fr = 0, tot = 0;
         HARP_CK(cudaMemGetInfo(&fr, &tot));
@@ -680,6 +788,7 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
     uint64_t device_peak = 0, h2d = 0, halo_arcs = 0;
     HARP_TRY(cut_triangle_ranges(g, budget_bytes, parts, fb, tri, device_peak));
     HARP_TRY(cut_wedge_blocks(g, budget_bytes, parts, wedge, device_peak));
+    const auto t2 = std::chrono::steady_clock::now();
     PartSums sum;
     sum.te.assign((size_t)g.offp[(size_t)n], 0);
     cudaStream_t s = nullptr;
@@ -747,6 +856,10 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
         stats->transfer_ms = sum.transfer_ms;
         stats->device_ms = sum.device_ms;
         stats->host_ms = total - sum.transfer_ms - sum.device_ms;
+        stats->graph_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        stats->cut_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+        stats->tri_ms = sum.tri_ms;
+        stats->wedge_ms = sum.wedge_ms;
     }
     return HARP_OK;
 }
