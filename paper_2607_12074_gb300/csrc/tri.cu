@@ -763,7 +763,7 @@ harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, i
     HARP_TRY((launch_cta<kCta1, 256, kCta1Blocks, BS>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
     HARP_TRY((launch_cta<kCta2, 256, 4, BS>(g, ws, 2, T_TRI_M, wmax, cmax, bmax, reuse, s)));
-    HARP_TRY((launch_cta<kCtaMax, 512, 1, BS>(g, ws, 3, T_TRI_L, wmax, cmax, bmax, reuse, s)));
+    HARP_TRY((launch_cta<kCtaMax, 1024, 1, BS>(g, ws, 3, T_TRI_L, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
     return HARP_OK;
 }
