@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long* qcnt_small = (unsigned long long*)&acc[Q_C4_MID];
     unsigned long long* qcnt_win = (unsigned long long*)&acc[Q_C4_WIN];
-    for (int64_t k = wid; k < n; k += nw) {
+    for (int64_t k = wid; k < n; k += nw) {  // descending rank: the heaviest roots are queued first
         const int32_t u = (int32_t)(n - 1 - k);
         if (u < own_lo || u >= own_hi) continue;  // the owner rule: only this range's roots
         const int64_t dm = (int64_t)deg[u] - dplus[u];
@@ -390,16 +390,17 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
             W += p > f ? (uint64_t)(p - f) : 0;
         }
         W = warp_sum(W);
-        if (W == 0 || l != 0) continue;
-        if (W <= warp_max) {
-            const unsigned long long slot = atomicAdd(qcnt_small, 1ull);
-            q_small[slot] = u;
-            q_small[n + slot] = (int32_t)W;
-        } else {
-            const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
-            const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
-            q_win[slot] = u;
-            wcount[slot] = (int32_t)windows_below<WORDS>(gi, u);
+        if (W > 0 && l == 0) {
+            if (W <= warp_max) {
+                const unsigned long long slot = atomicAdd(qcnt_small, 1ull);
+                q_small[slot] = u;
+                q_small[n + slot] = (int32_t)W;
+            } else {
+                const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
+                const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
+                q_win[slot] = u;
+                wcount[slot] = (int32_t)windows_below<WORDS>(gi, u);
+            }
         }
     }
 }

@@ -233,13 +233,18 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         auto lookup = [&](int32_t y) {
             return BS ? find_sorted(sL[w], d, y) : hash_get(sHk[w], sHv[w], kWarpHashBits, y);
         };
+        // every row's probe range at once, lane i for row i: N+(L[i]) from its first element >= L[i+1]
+        // (no smaller element can be in L); the lanes' dependent loads overlap
+        int64_t myb = 0, mye = 0;
+        if (l < d - 1) {
+            const int64_t b0 = offp[x];
+            mye = offp[x + 1];
+            myb = b0 + lower_bound_i32(colsp + b0, mye - b0, sL[w][l + 1]);
+        }
         uint32_t col = 0;  // # rows with bit l
         for (int i = 0; i < d - 1; ++i) {
-            const int32_t v = sL[w][i];
-            const int32_t next = sL[w][i + 1];  // no element of N+(v) below L[i+1] can be in L
-            const int64_t e = offp[v + 1];
-            int64_t b = offp[v];
-            if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
+            const int32_t next = sL[w][i + 1];
+            const int64_t b = __shfl_sync(kFull, myb, i), e = __shfl_sync(kFull, mye, i);
             uint32_t row = 0;
             auto probe = [&](int32_t y, int64_t p) {
                 if (y >= next && y <= last) {
