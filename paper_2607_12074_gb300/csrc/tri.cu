@@ -177,6 +177,26 @@ __device__ __forceinline__ void probe_list(const int32_t* __restrict__ colsp, in
     }
 }
 
+// Probe every element of colsp[b, e) (an exact range: no clip tests, no early exit), kRangeUnroll
+// warp-wide chunks of loads in flight.
+constexpr int kRangeUnroll = 4;
+
+template <typename F>
+__device__ __forceinline__ void probe_range(const int32_t* __restrict__ colsp, int64_t b, int64_t e, F&& probe) {
+    const int l = lane_id();
+    for (int64_t p0 = b; p0 < e; p0 += 32 * kRangeUnroll) {
+        int32_t ys[kRangeUnroll];
+#pragma unroll
+        for (int r = 0; r < kRangeUnroll; ++r) {
+            const int64_t p = p0 + r * 32 + l;
+            ys[r] = p < e ? colsp[p] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kRangeUnroll; ++r)
+            if (p0 + r * 32 + l < e) probe(ys[r], p0 + r * 32 + l);
+    }
+}
+
 // single-graph mode: one block reduction and one atomic per statistic at the end of the kernel;
 // the signature hits go to acc[ACC_SIG_HITS] in both modes
 __device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint64_t k4, uint64_t paw, uint64_t hits,
@@ -325,7 +345,8 @@ struct CtaSmem {
     int32_t hk[1 << HB];
     uint16_t hv[1 << HB];
     uint32_t filt[(1 << FB) / 32];
-    int64_t rb[PRE ? DMAX : 1];  // row i probes colsp[rb[i], re[i]): N+(L[i]) from its first element >= L[i+1]
+    // row i probes colsp[rb[i], re[i]): the elements of N+(L[i]) in [L[i+1], max L]
+    int64_t rb[PRE ? DMAX : 1];
     int64_t re[PRE ? DMAX : 1];
     uint64_t red[32];
 };
@@ -382,8 +403,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
             if (S::PRE && i < d - 1) {  // every row's probe range at once: dependent loads overlap across rows
                 const int32_t v = s.L[i];
                 const int64_t b = offp[v], e = offp[v + 1];
-                s.rb[i] = b + lower_bound_i32(colsp + b, e - b, s.L[i + 1]);
-                s.re[i] = e;
+                const int64_t lo = b + lower_bound_i32(colsp + b, e - b, s.L[i + 1]);
+                s.rb[i] = lo;
+                s.re[i] = lo + lower_bound_i32(colsp + lo, e - lo, s.L[d - 1] + 1);  // elements <= max L
             }
         }
         __syncthreads();
@@ -395,7 +417,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
         // rows: warp per row, ordered intersection of N+(L[i]) with L
         for (int i = w; i < d - 1; i += NW) {
             const int32_t next = s.L[i + 1];
-            int64_t b, e;
+            int64_t b = 0, e = 0;
             if (S::PRE) {
                 b = s.rb[i];
                 e = s.re[i];
@@ -417,7 +439,19 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
                     }
                 }
             };
-            probe_list(colsp, b, e, last, probe);
+            if (S::PRE) {
+                probe_range(colsp, b, e, [&](int32_t y, int64_t p) {  // y is in [next, last] already
+                    const int jj = lookup(y);
+                    if (jj >= 0) {
+                        atomicAdd(&te[p], 1u);
+                        atomicOr(&s.R[i * WS + (jj >> 5)], 1u << (jj & 31));
+                        atomicAdd(&s.own[jj], 1u);
+                        ++hits;
+                    }
+                });
+            } else {
+                probe_list(colsp, b, e, last, probe);
+            }
             hits = warp_sum(hits);
             if (l == 0 && hits) atomicAdd(&s.own[i], hits);
         }
