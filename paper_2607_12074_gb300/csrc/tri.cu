@@ -256,26 +256,22 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         // every row's probe range at once, lane i for row i: N+(L[i]) from its first element >= L[i+1]
         // (no smaller element can be in L); the lanes' dependent loads overlap
         int64_t myb = 0, mye = 0;
-        if (l < d - 1) {
-            const int64_t b0 = offp[x];
-            mye = offp[x + 1];
-            myb = b0 + lower_bound_i32(colsp + b0, mye - b0, sL[w][l + 1]);
+        if (l < d - 1) {  // [myb, mye): the elements of N+(L[l]) in [L[l+1], max L]
+            const int64_t b0 = offp[x], e0 = offp[x + 1];
+            myb = b0 + lower_bound_i32(colsp + b0, e0 - b0, sL[w][l + 1]);
+            mye = myb + lower_bound_i32(colsp + myb, e0 - myb, sL[w][d - 1] + 1);
         }
         uint32_t col = 0;  // # rows with bit l
         for (int i = 0; i < d - 1; ++i) {
-            const int32_t next = sL[w][i + 1];
             const int64_t b = __shfl_sync(kFull, myb, i), e = __shfl_sync(kFull, mye, i);
             uint32_t row = 0;
-            auto probe = [&](int32_t y, int64_t p) {
-                if (y >= next && y <= last) {
-                    const int j = lookup(y);
-                    if (j >= 0) {
-                        atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
-                        row |= 1u << j;
-                    }
+            probe_range(colsp, b, e, [&](int32_t y, int64_t p) {  // y is in [next, last] already
+                const int j = lookup(y);
+                if (j >= 0) {
+                    atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
+                    row |= 1u << j;
                 }
-            };
-            probe_list(colsp, b, e, last, probe);
+            });
             row = __reduce_or_sync(kFull, row);
             col += (row >> l) & 1u;
             if (l == i) sRow[w][i] = row;
