@@ -331,10 +331,10 @@ struct CtaSmem {
     static constexpr int WS = W | 1;                // odd row stride: no bank conflicts
     static constexpr int HB = (DMAX <= 256) ? 10 : ((DMAX <= 512) ? 11 : 12);  // 4 * DMAX hash slots
     static constexpr int FB = HB + 2;                                          // filter: 16 bits per key
-    // The 256 mode resolves every row's probe range up front (short lists: one binary search per
-    // thread); the larger modes keep the warp-wide search per row, which measured faster on their
-    // longer lists.
-    static constexpr bool PRE = DMAX <= 256;
+    // The 256 and 1024 modes resolve every row's exact probe range up front (one binary search per
+    // thread per bound); the 512 mode keeps the warp-wide search per row: the two range arrays would
+    // cost it a resident block per SM.
+    static constexpr bool PRE = DMAX <= 256 || DMAX >= 1024;
     int32_t L[DMAX];
     uint32_t own[DMAX];
     uint32_t R[DMAX * WS];
