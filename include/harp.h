@@ -250,6 +250,9 @@ typedef struct harp_partition_stats {
     double cut_ms;               /* part of host_ms: cutting the triangle ranges and wedge blocks */
     double tri_ms;               /* part of device_ms: triangle blocks                            */
     double wedge_ms;             /* part of device_ms: wedge blocks                               */
+    int64_t tri_blocks;          /* triangle blocks (rank ranges)                                 */
+    int64_t wedge_blocks;        /* wedge blocks ((rank range, x-slice) pairs)                    */
+    int64_t wedge_sliced;        /* wedge blocks that hold only a slice of their range's x values */
 } harp_partition_stats;
 
 /* src, dst: HOST int32[m_in] (read only).  budget_bytes: device bytes one range may use (0 = half

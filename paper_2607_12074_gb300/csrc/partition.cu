@@ -860,6 +860,10 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
         stats->cut_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
         stats->tri_ms = sum.tri_ms;
         stats->wedge_ms = sum.wedge_ms;
+        stats->tri_blocks = (int64_t)tri.size();
+        stats->wedge_blocks = (int64_t)wedge.size();
+        stats->wedge_sliced = 0;
+        for (const WedgeBlock& b : wedge) stats->wedge_sliced += (b.xlo > 0 || b.xhi < n) ? 1 : 0;
     }
     return HARP_OK;
 }

@@ -78,7 +78,8 @@ class harp_partition_stats(ctypes.Structure):
     _fields_ = [("partitions", ctypes.c_int64), ("m", ctypes.c_int64), ("halo_arcs", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_uint64), ("device_peak_bytes", ctypes.c_uint64), ("host_ms", ctypes.c_double),
                 ("transfer_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("graph_ms", ctypes.c_double),
-                ("cut_ms", ctypes.c_double), ("tri_ms", ctypes.c_double), ("wedge_ms", ctypes.c_double)]
+                ("cut_ms", ctypes.c_double), ("tri_ms", ctypes.c_double), ("wedge_ms", ctypes.c_double),
+                ("tri_blocks", ctypes.c_int64), ("wedge_blocks", ctypes.c_int64), ("wedge_sliced", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -197,3 +197,16 @@ def test_async_entry_point_and_launch_count(harp):
     got = out.cpu().numpy().view(np.uint64)[:6]
     csr.close()
     assert got.tolist() == O.count4_esu(g.n, g.src, g.dst).tolist()
+
+
+def test_large_grid_boundary_table(harp):
+    """A grid of more than 15 windows per row keeps every 2^s-th boundary and finds the rest by a
+    galloping search: 2e6 vertices of degree >= 2 span about 30 windows of 48 KiB (and about 15 of
+    100 KiB); both agree with the oracle."""
+    g = graphgen.chung_lu(2_000_000, 2.1, 3000, 4, 5)
+    want = O.count4_combo(g.n, g.src, g.dst).tolist()
+    for bytes_ in (0, 49152):
+        p = harp.harp_plan()
+        p.version = harp.HARP_ABI_VERSION
+        p.c4_window_bytes = bytes_
+        assert harp.count4_edges(g.n, g.src, g.dst, p).tolist() == want, bytes_

@@ -89,3 +89,30 @@ def test_chung_lu_subsample_under_a_cap(harp):
     assert st["partitions"] > 2 and st["device_peak_bytes"] <= budget
     assert st["transfer_ms"] >= 0 and st["device_ms"] > 0
     assert got.tolist() == whole.tolist() == want.tolist()
+
+
+def test_wedge_blocks_cut_into_x_slices(harp):
+    """A budget that holds the roots' lists but not the rows of their lower neighbours forces the
+    wedge blocks of a hub-heavy graph into x-slices; the counts stay exact."""
+    g = graphgen.chung_lu(60000, 2.1, 3000, 16, 21)
+    want = O.count4_combo(g.n, g.src, g.dst)
+    whole, st1 = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=1 << 34)
+    assert st1["wedge_sliced"] == 0 and st1["tri_blocks"] == 1 and st1["wedge_blocks"] == 1
+    lo, hi = 0, st1["device_peak_bytes"]
+    got = None
+    for _ in range(24):  # the largest budget below the whole footprint that slices
+        mid = (lo + hi) // 2
+        try:
+            c, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=mid)
+        except harp.HarpError as e:
+            assert e.status == harp.HARP_ENOMEM
+            lo = mid
+            continue
+        if st["wedge_sliced"] > 0:
+            got = (c, st)
+            break
+        hi = mid
+    assert got is not None, "no budget produced x-sliced wedge blocks"
+    c, st = got
+    assert st["wedge_blocks"] == st["partitions"] - st["tri_blocks"] and st["device_peak_bytes"] <= mid
+    assert c.tolist() == whole.tolist() == want.tolist()
