@@ -11,9 +11,9 @@
 // cnt(x) <= d-(u).  Rank order sorts each graph's vertices by degree, so inside a graph's rank range
 //   * x of degree 1 never complete a cycle: x runs over [n1, u) with n1 the graph's first rank of
 //     degree >= 2, and every row's segment starts at fpos[w] (its first neighbour of degree >= 2);
-//   * a dense counter for x fits 8 bits while d(x) <= 255 and 16 bits while d(x) <= 65535, so the
-//     x-range splits into the bands [n1, r256), [r256, r64k), [r64k, end) with 8-, 16- and 32-bit
-//     counters.  The bands cut into windows of 48-100 KiB of counters form a fixed grid per graph, so the
+//   * a dense counter for x fits 4 bits while d(x) <= 15, 8 bits while d(x) <= 255 and 16 bits
+//     while d(x) <= 65535, so the x-range splits into the bands [n1, r16), [r16, r256),
+//     [r256, r64k), [r64k, end) with 4-, 8-, 16- and 32-bit counters.  The bands cut into windows of 48-100 KiB of counters form a fixed grid per graph, so the
 //     row position of every grid boundary is computed once per row (bpos) instead of being searched
 //     for every (root, lower neighbour, window).
 // pos_w(u) itself is computed once per lower arc (rev) by a fully parallel pass.
@@ -54,7 +54,11 @@ constexpr int kChunk = 1024;                 // elements per split chunk
 // ---------------------------------------------------------------------------------------------
 // The window size is a template parameter (WORDS 32-bit words of counters) of every kernel that
 // computes window geometry, so each size is its own compiled instance with constant spans.
-enum : int { GI_LO = 0, GI_HI, GI_N1, GI_B1, GI_B2, GI_NWIN };
+// The x-range [n1, hi) splits into four bands by degree, each with the narrowest counter that is
+// exact there (cnt(x) <= d(x)): d <= 15 takes 4 bits, d <= 255 8 bits, d <= 65535 16 bits, else 32.
+// GI_B0, GI_B1 and GI_B2 are the starts of the 8-, 16- and 32-bit bands.
+enum : int { GI_B0 = 0, GI_HI, GI_N1, GI_B1, GI_B2, GI_NWIN };
+constexpr int kBands = 4;
 
 __device__ __forceinline__ int64_t first_above_in(const int32_t* __restrict__ deg, int64_t lo, int64_t hi, int32_t t) {
     while (lo < hi) {
@@ -76,16 +80,16 @@ struct Band {
 
 __device__ __forceinline__ Band band_of(const int64_t* gi, int b) {
     Band r;
-    r.start = b == 0 ? gi[GI_N1] : (b == 1 ? gi[GI_B1] : gi[GI_B2]);
-    r.end = b == 0 ? gi[GI_B1] : (b == 1 ? gi[GI_B2] : gi[GI_HI]);
-    r.width = b == 0 ? 8 : (b == 1 ? 16 : 32);
+    r.start = b == 0 ? gi[GI_N1] : (b == 1 ? gi[GI_B0] : (b == 2 ? gi[GI_B1] : gi[GI_B2]));
+    r.end = b == 0 ? gi[GI_B0] : (b == 1 ? gi[GI_B1] : (b == 2 ? gi[GI_B2] : gi[GI_HI]));
+    r.width = 4 << b;
     return r;
 }
 
 // window j of the graph's grid: [xlo, xhi) and counter width; false if j is past the grid
 template <int WORDS>
 __device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_t& xlo, int64_t& xhi, int& width) {
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < kBands; ++b) {
         const Band B = band_of(gi, b);
         if (B.end <= B.start) continue;
         const int64_t S = span_of<WORDS>(B.width);
@@ -105,7 +109,7 @@ __device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_
 template <int WORDS>
 __device__ __forceinline__ int64_t windows_below(const int64_t* gi, int64_t u) {
     int64_t total = 0;
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < kBands; ++b) {
         const Band B = band_of(gi, b);
         const int64_t e = B.end < u ? B.end : u;
         if (e <= B.start) continue;
@@ -124,18 +128,20 @@ __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int
         const int64_t lo = gbase ? gbase[g] : 0;
         int64_t hi = gbase ? gbase[g + 1] : n;
         int64_t n1 = first_above_in(deg, lo, hi, 1);
+        int64_t r16 = first_above_in(deg, lo, hi, 15);
         int64_t r256 = first_above_in(deg, lo, hi, 255);
         int64_t r64k = first_above_in(deg, lo, hi, 65535);
         auto clamp = [&](int64_t v) { return v < x_lo ? x_lo : (v > x_hi ? x_hi : v); };
         hi = hi < x_hi ? hi : x_hi;
         n1 = clamp(n1);
         n1 = n1 < hi ? n1 : hi;
+        r16 = clamp(r16);
         r256 = clamp(r256);
         r64k = clamp(r64k);
         int64_t* gi = ginfo + g * kGInfo;
-        gi[GI_LO] = lo;
         gi[GI_HI] = hi;
         gi[GI_N1] = n1;
+        gi[GI_B0] = r16 > n1 ? (r16 < hi ? r16 : hi) : n1;
         gi[GI_B1] = r256 > n1 ? (r256 < hi ? r256 : hi) : n1;
         gi[GI_B2] = r64k > n1 ? (r64k < hi ? r64k : hi) : n1;
         gi[GI_NWIN] = windows_below<WORDS>(gi, hi);
@@ -469,12 +475,15 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
 // ---------------------------------------------------------------------------------------------
 // Windowed CTA mode: one block per (root, grid window); dense packed counters in shared memory.
 // ---------------------------------------------------------------------------------------------
-// Packed counters: 8-bit counters four to a word, 16-bit two to a word.  (A byte-plane layout that
+// Packed counters: 4-bit counters eight to a word, 8-bit four, 16-bit two.  (A byte-plane layout that
 // puts consecutive x in consecutive banks was measured no faster: the kernel is bound by load
 // latency and the end-of-item barrier, not by shared-memory bank conflicts.)
 template <int WIDTH, int WORDS>
 __device__ __forceinline__ uint32_t counter_add(uint32_t* cw, uint32_t r) {
-    if (WIDTH == 8) {
+    if (WIDTH == 4) {
+        const uint32_t sh = (r & 7u) << 2;
+        return (atomicAdd(&cw[r >> 3], 1u << sh) >> sh) & 0xfu;
+    } else if (WIDTH == 8) {
         const uint32_t sh = (r & 3u) << 3;
         return (atomicAdd(&cw[r >> 2], 1u << sh) >> sh) & 0xffu;
     } else if (WIDTH == 16) {
@@ -676,7 +685,10 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
             resolve_item<WORDS>(s_next, (int64_t)atomicAdd(ticket, 1ull), total, nroots, win_prefix, q_win, gid,
                                 ginfo, deg, dplus, loff);
         uint64_t a_c4 = 0;
-        if (width == 8)
+        if (width == 4)
+            window_pass<4, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
+                           sh, a_c4, acc);
+        else if (width == 8)
             window_pass<8, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
                            sh, a_c4, acc);
         else if (width == 16)
@@ -697,7 +709,8 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
                 sh.split_pre[ns] = run;
             }
             __syncthreads();
-            if (width == 8) split_pass<8, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
+            if (width == 4) split_pass<4, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
+            else if (width == 8) split_pass<8, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
             else if (width == 16) split_pass<16, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
             else split_pass<32, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
             __syncthreads();

@@ -102,6 +102,7 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
     ru, rw = rows[down], cols[down]
     rev = np.searchsorted(rows * n + cols, rw * n + ru)
     n1 = int(np.searchsorted(deg, 2))                 # first rank of degree >= 2
+    r16 = int(np.searchsorted(deg, 16))
     r256 = int(np.searchsorted(deg, 256))
     r64k = int(np.searchsorted(deg, 65536))
     fpos = np.bincount(rows[cols < n1], minlength=n)  # neighbours of degree <= 1 lead every row
@@ -113,8 +114,8 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
     words = WIN_WORDS[2 if c4_window_bytes >= 4 * WIN_WORDS[2] else (3 if c4_window_bytes >= 4 * WIN_WORDS[3] else 4)]
     u_ids = np.arange(n, dtype=np.int64)
     nwin = np.zeros(n, np.int64)
-    bounds = [n1, max(r256, n1), max(r64k, n1), n]     # x bands by the degree of x: 8-, 16-, 32-bit counters
-    for band, width_x in enumerate((8, 16, 32)):
+    bounds = [n1, max(r16, n1), max(r256, n1), max(r64k, n1), n]  # x bands by d(x): 4-, 8-, 16-, 32-bit counters
+    for band, width_x in enumerate((4, 8, 16, 32)):
         lo = np.minimum(bounds[band], u_ids)
         hi = np.maximum(np.minimum(bounds[band + 1], u_ids), lo)
         span = words * (32 // width_x)
