@@ -11,11 +11,11 @@
 // cnt(x) <= d-(u).  Rank order sorts each graph's vertices by degree, so inside a graph's rank range
 //   * x of degree 1 never complete a cycle: x runs over [n1, u) with n1 the graph's first rank of
 //     degree >= 2, and every row's segment starts at fpos[w] (its first neighbour of degree >= 2);
-//   * a dense counter for x fits 4 bits while d(x) <= 15, 8 bits while d(x) <= 255 and 16 bits
-//     while d(x) <= 65535, so the x-range splits into the bands [n1, r16), [r16, r256),
-//     [r256, r64k), [r64k, end) with 4-, 8-, 16- and 32-bit counters.  The bands cut into windows of 48-100 KiB of counters form a fixed grid per graph, so the
-//     row position of every grid boundary is computed once per row (bpos) instead of being searched
-//     for every (root, lower neighbour, window).
+//   * a dense counter for x needs only as many bits as d(x) has, so the x-range splits into bands
+//     by degree (d <= 7, 15, 31, 63, 255, 65535, larger) with 3-, 4-, 5-, 6-, 8-, 16- and 32-bit
+//     counters packed floor(32 / bits) to a word.  The bands cut into windows of 48-100 KiB of
+//     counters form a fixed grid per graph, so the row position of every grid boundary is computed
+//     once per row (bpos) instead of being searched for every (root, lower neighbour, window).
 // pos_w(u) itself is computed once per lower arc (rev) by a fully parallel pass.
 //
 // The frontier (the set of x) is not an induced class: whether u ~ x or w1 ~ w2 holds decides
@@ -28,6 +28,8 @@
 //                   (CTA mode); lower neighbours are handed to warps in groups of 32, heaviest first,
 //                   and segments of 2048+ elements are split across all warps of the block.  The
 //                   window (100, 64 or 48 KiB) sets how many blocks share an SM (2, 3 or 4).
+#include <type_traits>
+
 #include "harp_internal.cuh"
 
 namespace harp {
@@ -54,11 +56,22 @@ constexpr int kChunk = 1024;                 // elements per split chunk
 // ---------------------------------------------------------------------------------------------
 // The window size is a template parameter (WORDS 32-bit words of counters) of every kernel that
 // computes window geometry, so each size is its own compiled instance with constant spans.
-// The x-range [n1, hi) splits into four bands by degree, each with the narrowest counter that is
-// exact there (cnt(x) <= d(x)): d <= 15 takes 4 bits, d <= 255 8 bits, d <= 65535 16 bits, else 32.
-// GI_B0, GI_B1 and GI_B2 are the starts of the 8-, 16- and 32-bit bands.
-enum : int { GI_B0 = 0, GI_HI, GI_N1, GI_B1, GI_B2, GI_NWIN };
-constexpr int kBands = 4;
+// The x-range [n1, hi) splits into bands by degree, each with the narrowest counter that is exact
+// there (cnt(x) <= d(x) < 2^width): a band of width b packs floor(32 / b) counters into a word.
+// ginfo slots: GI_HI, GI_NWIN, then the band starts GI_BAND + b (b = 0 .. kBands - 1; band b
+// ends where band b + 1 starts, the last band at GI_HI).  GI_N1 = GI_BAND: the first band starts at n1.
+constexpr int kBands = 7;
+enum : int { GI_HI = 0, GI_NWIN = 1, GI_BAND = 2, GI_N1 = GI_BAND };
+static_assert(GI_BAND + kBands <= kGInfo, "ginfo slots");
+
+// counter bits of band b and the largest degree the band holds
+__host__ __device__ constexpr int band_width(int b) {
+    return b == 0 ? 3 : (b == 1 ? 4 : (b == 2 ? 5 : (b == 3 ? 6 : (b == 4 ? 8 : (b == 5 ? 16 : 32)))));
+}
+__host__ __device__ constexpr int band_per_word(int b) { return 32 / band_width(b); }
+__host__ __device__ constexpr int32_t band_max_degree(int b) {
+    return band_width(b) >= 31 ? INT32_MAX : (int32_t)((1u << band_width(b)) - 1u);
+}
 
 __device__ __forceinline__ int64_t first_above_in(const int32_t* __restrict__ deg, int64_t lo, int64_t hi, int32_t t) {
     while (lo < hi) {
@@ -69,35 +82,28 @@ __device__ __forceinline__ int64_t first_above_in(const int32_t* __restrict__ de
     return lo;
 }
 
-// x-values one window covers at a counter width: the window's words times counters per word
+// x-values one window of band b covers: the window's words times counters per word
 template <int WORDS>
-__device__ __forceinline__ int64_t span_of(int width) { return (int64_t)WORDS * (32 / width); }
+__device__ __forceinline__ int64_t span_of(int b) { return (int64_t)WORDS * band_per_word(b); }
 
-struct Band {
-    int64_t start, end;
-    int width;
-};
-
-__device__ __forceinline__ Band band_of(const int64_t* gi, int b) {
-    Band r;
-    r.start = b == 0 ? gi[GI_N1] : (b == 1 ? gi[GI_B0] : (b == 2 ? gi[GI_B1] : gi[GI_B2]));
-    r.end = b == 0 ? gi[GI_B0] : (b == 1 ? gi[GI_B1] : (b == 2 ? gi[GI_B2] : gi[GI_HI]));
-    r.width = 4 << b;
-    return r;
+__device__ __forceinline__ int64_t band_end(const int64_t* gi, int b) {
+    return b + 1 < kBands ? gi[GI_BAND + b + 1] : gi[GI_HI];
 }
 
-// window j of the graph's grid: [xlo, xhi) and counter width; false if j is past the grid
+// window j of the graph's grid: [xlo, xhi) and its band; false if j is past the grid.  The band loops
+// are unrolled, so every span is a compile-time constant.
 template <int WORDS>
-__device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_t& xlo, int64_t& xhi, int& width) {
+__device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_t& xlo, int64_t& xhi, int& band) {
+#pragma unroll
     for (int b = 0; b < kBands; ++b) {
-        const Band B = band_of(gi, b);
-        if (B.end <= B.start) continue;
-        const int64_t S = span_of<WORDS>(B.width);
-        const int64_t nb = (B.end - B.start + S - 1) / S;
+        const int64_t bs = gi[GI_BAND + b], be = band_end(gi, b);
+        if (be <= bs) continue;
+        const int64_t S = span_of<WORDS>(b);
+        const int64_t nb = (be - bs + S - 1) / S;
         if (j < nb) {
-            xlo = B.start + j * S;
-            xhi = xlo + S < B.end ? xlo + S : B.end;
-            width = B.width;
+            xlo = bs + j * S;
+            xhi = xlo + S < be ? xlo + S : be;
+            band = b;
             return true;
         }
         j -= nb;
@@ -109,42 +115,96 @@ __device__ __forceinline__ bool grid_window(const int64_t* gi, int64_t j, int64_
 template <int WORDS>
 __device__ __forceinline__ int64_t windows_below(const int64_t* gi, int64_t u) {
     int64_t total = 0;
+#pragma unroll
     for (int b = 0; b < kBands; ++b) {
-        const Band B = band_of(gi, b);
-        const int64_t e = B.end < u ? B.end : u;
-        if (e <= B.start) continue;
-        const int64_t S = span_of<WORDS>(B.width);
-        total += (e - B.start + S - 1) / S;
+        const int64_t bs = gi[GI_BAND + b], be = band_end(gi, b);
+        const int64_t e = be < u ? be : u;
+        if (e <= bs) continue;
+        const int64_t S = span_of<WORDS>(b);
+        total += (e - bs + S - 1) / S;
     }
     return total;
 }
 
-// The x-range of a graph's grid is [n1, hi) intersected with [x_lo, x_hi) (a partitioned wedge
-// block owns only the opposite vertices in that slice; a whole graph passes [0, INT64_MAX)).
+// Windows intersecting [n1, u) when bands are merged upwards by mask (bit b set: band b joins band
+// b + 1 and takes its wider counters).  st[0 .. kBands] are the unmerged band starts and hi.
+template <int WORDS>
+__device__ __forceinline__ int64_t merged_windows(const int64_t* st, unsigned mask, int64_t u) {
+    int64_t total = 0, gs = st[0];
+#pragma unroll
+    for (int b = 0; b < kBands; ++b) {
+        if (b + 1 < kBands && ((mask >> b) & 1u)) continue;  // the group goes on into band b + 1
+        const int64_t e = st[b + 1] < u ? st[b + 1] : u;
+        const int64_t S = span_of<WORDS>(b);
+        if (e > gs) total += (e - gs + S - 1) / S;
+        gs = st[b + 1];
+    }
+    return total;
+}
+
+constexpr int kMergeMasks = 1 << (kBands - 1);
+constexpr int kMergeSamples = 64;
+
+// One warp per graph.  The x-range of a graph's grid is [n1, hi) intersected with [x_lo, x_hi) (a
+// partitioned wedge block owns only the opposite vertices in that slice; a whole graph passes
+// [0, INT64_MAX)).  A narrow band holding few vertices costs a partly filled window for every root
+// that reaches past it, so bands may merge into the next wider one: each lane scores merge masks by
+// the windows of kMergeSamples roots spread evenly over the graph's ranks of degree >= 64 (the roots
+// that take the windowed mode), each weighted by its degree; the cheapest mask (lowest on a tie) wins.
 template <int WORDS>
 __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int64_t* __restrict__ gbase,
                            int64_t G, int64_t x_lo, int64_t x_hi, int64_t* __restrict__ ginfo) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lo = gbase ? gbase[g] : 0;
-        int64_t hi = gbase ? gbase[g + 1] : n;
-        int64_t n1 = first_above_in(deg, lo, hi, 1);
-        int64_t r16 = first_above_in(deg, lo, hi, 15);
-        int64_t r256 = first_above_in(deg, lo, hi, 255);
-        int64_t r64k = first_above_in(deg, lo, hi, 65535);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += warps) {
+        const int64_t lo = gbase ? gbase[g] : 0, gend = gbase ? gbase[g + 1] : n;
         auto clamp = [&](int64_t v) { return v < x_lo ? x_lo : (v > x_hi ? x_hi : v); };
-        hi = hi < x_hi ? hi : x_hi;
-        n1 = clamp(n1);
+        const int64_t hi = gend < x_hi ? gend : x_hi;
+        int64_t n1 = clamp(first_above_in(deg, lo, gend, 1));
         n1 = n1 < hi ? n1 : hi;
-        r16 = clamp(r16);
-        r256 = clamp(r256);
-        r64k = clamp(r64k);
-        int64_t* gi = ginfo + g * kGInfo;
-        gi[GI_HI] = hi;
-        gi[GI_N1] = n1;
-        gi[GI_B0] = r16 > n1 ? (r16 < hi ? r16 : hi) : n1;
-        gi[GI_B1] = r256 > n1 ? (r256 < hi ? r256 : hi) : n1;
-        gi[GI_B2] = r64k > n1 ? (r64k < hi ? r64k : hi) : n1;
-        gi[GI_NWIN] = windows_below<WORDS>(gi, hi);
+        int64_t st[kBands + 1];
+        st[0] = n1;
+        st[kBands] = hi;
+#pragma unroll
+        for (int b = 1; b < kBands; ++b) {  // band b starts at the first rank above band b - 1's degrees
+            const int64_t r = clamp(first_above_in(deg, lo, gend, band_max_degree(b - 1)));
+            st[b] = r > n1 ? (r < hi ? r : hi) : n1;
+        }
+        int64_t s0 = first_above_in(deg, lo, gend, 63);
+        if (s0 >= gend) s0 = lo;
+        const int64_t span = gend - s0;  // samples u lie in [s0, gend); none for an empty graph
+        unsigned best_mask = 0;
+        double best = 0.0;
+        for (int m = lane; m < kMergeMasks; m += 32) {
+            double c = 0.0;
+            for (int k = 0; span > 0 && k < kMergeSamples; ++k) {
+                const int64_t u = s0 + (span * (2 * k + 1)) / (2 * kMergeSamples);
+                c += (double)deg[u] * (double)merged_windows<WORDS>(st, (unsigned)m, u);
+            }
+            if (m == lane || c < best) {
+                best = c;
+                best_mask = (unsigned)m;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oc = __shfl_xor_sync(0xffffffffu, best, o);
+            const unsigned om = __shfl_xor_sync(0xffffffffu, best_mask, o);
+            if (oc < best || (oc == best && om < best_mask)) {
+                best = oc;
+                best_mask = om;
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int b = 0; b + 1 < kBands; ++b)
+                if ((best_mask >> b) & 1u) st[b + 1] = st[b];  // band b becomes empty, b + 1 starts at its start
+            int64_t* gi = ginfo + g * kGInfo;
+            gi[GI_HI] = hi;
+#pragma unroll
+            for (int b = 0; b < kBands; ++b) gi[GI_BAND + b] = st[b];
+            gi[GI_NWIN] = windows_below<WORDS>(gi, hi);
+        }
     }
 }
 
@@ -245,8 +305,8 @@ __global__ void k_c4_bpos(const int64_t* __restrict__ off, const int32_t* __rest
         int64_t bound = gi[GI_HI];
         if (i < nwin) {
             int64_t xhi;
-            int width;
-            grid_window<WORDS>(gi, i, bound, xhi, width);
+            int band;
+            grid_window<WORDS>(gi, i, bound, xhi, band);
         }
         const int64_t wb = off[w];
         bpos[t] = (int32_t)lower_bound_i32(cols + wb, off[w + 1] - wb, (int32_t)bound);
@@ -475,24 +535,37 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
 // ---------------------------------------------------------------------------------------------
 // Windowed CTA mode: one block per (root, grid window); dense packed counters in shared memory.
 // ---------------------------------------------------------------------------------------------
-// Packed counters: 4-bit counters eight to a word, 8-bit four, 16-bit two.  (A byte-plane layout that
+// Packed counters: a band of width b packs floor(32 / b) counters into a word (3-bit ten, 4-bit
+// eight, 5-bit six, 6-bit five, 8-bit four, 16-bit two).  (A byte-plane layout that
 // puts consecutive x in consecutive banks was measured no faster: the kernel is bound by load
 // latency and the end-of-item barrier, not by shared-memory bank conflicts.)
 template <int WIDTH, int WORDS>
 __device__ __forceinline__ uint32_t counter_add(uint32_t* cw, uint32_t r) {
-    if (WIDTH == 4) {
-        const uint32_t sh = (r & 7u) << 2;
-        return (atomicAdd(&cw[r >> 3], 1u << sh) >> sh) & 0xfu;
-    } else if (WIDTH == 8) {
-        const uint32_t sh = (r & 3u) << 3;
-        return (atomicAdd(&cw[r >> 2], 1u << sh) >> sh) & 0xffu;
-    } else if (WIDTH == 16) {
-        const uint32_t sh = (r & 1u) << 4;
-        return (atomicAdd(&cw[r >> 1], 1u << sh) >> sh) & 0xffffu;
-    } else {
+    constexpr uint32_t K = 32 / WIDTH;  // counters per word
+    if constexpr (K == 1) {
         return atomicAdd(&cw[r], 1u);
+    } else {
+        const uint32_t q = r / K;  // a constant divisor: a multiply and a shift
+        const uint32_t sh = (r - q * K) * WIDTH;
+        return (atomicAdd(&cw[q], 1u << sh) >> sh) & ((1u << WIDTH) - 1u);
     }
 }
+
+// Calls f(std::integral_constant<int, width>) for band b's counter width, so each width is its own
+// compiled instance of the window and split passes.
+template <typename F>
+__device__ __forceinline__ void with_band(int b, F&& f) {
+    switch (b) {
+        case 0: f(std::integral_constant<int, band_width(0)>{}); break;
+        case 1: f(std::integral_constant<int, band_width(1)>{}); break;
+        case 2: f(std::integral_constant<int, band_width(2)>{}); break;
+        case 3: f(std::integral_constant<int, band_width(3)>{}); break;
+        case 4: f(std::integral_constant<int, band_width(4)>{}); break;
+        case 5: f(std::integral_constant<int, band_width(5)>{}); break;
+        default: f(std::integral_constant<int, band_width(6)>{}); break;
+    }
+}
+static_assert(kBands == 7, "with_band covers every band");
 
 struct WinShared {
     int group;                 // next group of 32 lower neighbours
@@ -599,7 +672,7 @@ struct WinItem {
     int64_t t;  // ticket; >= the item total: no more items
     int64_t j, xlo, xhi, nwin, dm, ub;
     int32_t u;
-    int width, sl, first, last;
+    int band, sl, first, last;
 };
 
 template <int WORDS>
@@ -620,15 +693,15 @@ __device__ __forceinline__ void resolve_item(WinItem& it, int64_t t, int64_t tot
     const int64_t j = t - win_prefix[lo];
     const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
     int64_t xlo = 0, xhi = 0;
-    int width = 32;
-    grid_window<WORDS>(gi, j, xlo, xhi, width);
+    int band = kBands - 1;
+    grid_window<WORDS>(gi, j, xlo, xhi, band);
     it.last = xhi >= (int64_t)u;
     it.xhi = it.last ? u : xhi;
     it.xlo = xlo;
     it.first = j == 0;
     it.j = j;
     it.u = u;
-    it.width = width;
+    it.band = band;
     it.nwin = gi[GI_NWIN];
     it.sl = table_shift(it.nwin);
     it.dm = (int64_t)deg[u] - dplus[u];
@@ -670,33 +743,28 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
         if (it.t >= total) break;
         const int32_t u = it.u;
         const int64_t j = it.j, xlo = it.xlo, xhi = it.xhi, nwin = it.nwin, dm = it.dm, ub = it.ub;
-        const int width = it.width, sl = it.sl;
+        const int band = it.band, sl = it.sl;
         const bool first = it.first, last = it.last;
         if (threadIdx.x == 0) {
             sh.group = 0;
             sh.nsplit = 0;
             sh.chunk = 0;
         }
-        const int per = 32 / width;
-        const int words = (int)((xhi - xlo + per - 1) / per);
+        int words = 0;
+        with_band(band, [&](auto wc) {
+            constexpr int per = 32 / decltype(wc)::value;
+            words = (int)((xhi - xlo + per - 1) / per);
+        });
         for (int i = threadIdx.x; i < words; i += kWinThreads) cw[i] = 0;
         __syncthreads();  // every thread holds this item; counters and work counters are reset
         if (threadIdx.x == 0)  // the next item, resolved while the block walks this one
             resolve_item<WORDS>(s_next, (int64_t)atomicAdd(ticket, 1ull), total, nroots, win_prefix, q_win, gid,
                                 ginfo, deg, dplus, loff);
         uint64_t a_c4 = 0;
-        if (width == 4)
-            window_pass<4, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                           sh, a_c4, acc);
-        else if (width == 8)
-            window_pass<8, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                           sh, a_c4, acc);
-        else if (width == 16)
-            window_pass<16, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                            sh, a_c4, acc);
-        else
-            window_pass<32, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm, (int32_t)xlo, (int32_t)xhi, first, last, cw,
-                            sh, a_c4, acc);
+        with_band(band, [&](auto wc) {
+            window_pass<decltype(wc)::value, WORDS>(off, cols, lcols, fpos, rev, bpos, table, sl, nwin, j, ub, dm,
+                                                    (int32_t)xlo, (int32_t)xhi, first, last, cw, sh, a_c4, acc);
+        });
         __syncthreads();
         if (sh.nsplit > 0) {
             if (threadIdx.x == 0) {
@@ -709,10 +777,7 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
                 sh.split_pre[ns] = run;
             }
             __syncthreads();
-            if (width == 4) split_pass<4, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else if (width == 8) split_pass<8, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else if (width == 16) split_pass<16, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
-            else split_pass<32, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4);
+            with_band(band, [&](auto wc) { split_pass<decltype(wc)::value, WORDS>(cols, (int32_t)xlo, cw, sh, a_c4); });
             __syncthreads();
         }
         if (sink.batch()) {
@@ -743,7 +808,7 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, cuda
     const Sink sink{ws.acc, ws.gid, ws.accG};
     int32_t* wcount = ws.q_win + n;
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
-    k_c4_ginfo<WORDS><<<grid_cap(G, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.x_lo, ws.x_hi, ws.ginfo);
+    k_c4_ginfo<WORDS><<<grid_cap(G * 32, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.x_lo, ws.x_hi, ws.ginfo);
     HARP_LAUNCHED();
     // the roots' lower lists: row prefixes of a whole graph, or their own CSR in a partitioned block
     const bool lists = ws.loff != nullptr;

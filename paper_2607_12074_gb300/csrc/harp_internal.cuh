@@ -84,7 +84,7 @@ enum : int {
 
 // Per-graph accumulator slots (batch mode), kGStride per graph.
 constexpr int kGStride = 8;
-constexpr int kGInfo = 8;      // int64 per graph of wedge-window geometry
+constexpr int kGInfo = 16;     // int64 per graph of wedge-window geometry
 constexpr int kGridCap = 16;   // grid boundaries kept per row
 enum : int { G_T = 0, G_K4, G_C4, G_S, G_PW, G_PAWSUM, G_D };
 

@@ -58,6 +58,21 @@ def rank_space(n, src, dst):
             "split": split, "dplus": deg - split}
 
 
+def _merged_windows(bounds, widths, mask, u, words):
+    """Grid windows that intersect [n1, u) per root u when band b merges into band b + 1 (and takes
+    its wider counters) for every bit b set in mask; bounds = band starts followed by n."""
+    total = np.zeros(len(u), np.int64)
+    gs = bounds[0]
+    for b, width in enumerate(widths):
+        if b + 1 < len(widths) and (mask >> b) & 1:
+            continue
+        e = np.minimum(bounds[b + 1], u)
+        span = words * (32 // width)
+        total += np.where(e > gs, (e - gs + span - 1) // span, 0)
+        gs = bounds[b + 1]
+    return total
+
+
 def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
     """Per-kernel work and algorithmic bytes (dict of dicts) under the given wedge plan fields."""
     G = rank_space(n, src, dst)
@@ -102,9 +117,8 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
     ru, rw = rows[down], cols[down]
     rev = np.searchsorted(rows * n + cols, rw * n + ru)
     n1 = int(np.searchsorted(deg, 2))                 # first rank of degree >= 2
-    r16 = int(np.searchsorted(deg, 16))
-    r256 = int(np.searchsorted(deg, 256))
-    r64k = int(np.searchsorted(deg, 65536))
+    band_widths = (3, 4, 5, 6, 8, 16, 32)              # x bands by d(x): d < 2^width
+    band_starts = [n1] + [max(int(np.searchsorted(deg, 1 << w)), n1) for w in band_widths[:-1]]
     fpos = np.bincount(rows[cols < n1], minlength=n)  # neighbours of degree <= 1 lead every row
     seg = np.maximum(pos[rev] - fpos[rw], 0)
     W = np.bincount(ru, weights=seg, minlength=n).astype(np.int64)
@@ -112,14 +126,17 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
     # warp-local hash mode for W <= c4_warp_max, windowed counters above (no middle tier)
     tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= min(c4_warp_max, 512), 0, 2))
     words = WIN_WORDS[2 if c4_window_bytes >= 4 * WIN_WORDS[2] else (3 if c4_window_bytes >= 4 * WIN_WORDS[3] else 4)]
-    u_ids = np.arange(n, dtype=np.int64)
-    nwin = np.zeros(n, np.int64)
-    bounds = [n1, max(r16, n1), max(r256, n1), max(r64k, n1), n]  # x bands by d(x): 4-, 8-, 16-, 32-bit counters
-    for band, width_x in enumerate((4, 8, 16, 32)):
-        lo = np.minimum(bounds[band], u_ids)
-        hi = np.maximum(np.minimum(bounds[band + 1], u_ids), lo)
-        span = words * (32 // width_x)
-        nwin += (hi - lo + span - 1) // span            # grid windows of the band that intersect [n1, u)
+    bounds = band_starts + [n]
+    # narrow bands may merge into the next wider one: the mask with the fewest degree-weighted windows
+    # over 64 roots spread evenly over the ranks of degree >= 64 (lowest mask on a tie)
+    s0 = int(np.searchsorted(deg, 64))
+    s0 = 0 if s0 >= n else s0
+    samples = s0 + ((n - s0) * (2 * np.arange(64, dtype=np.int64) + 1)) // 128
+    weights = deg[samples].astype(np.float64) if n > s0 else np.zeros(0)
+    costs = [float((weights * _merged_windows(bounds, band_widths, mask, samples, words)).sum())
+             for mask in range(1 << (len(band_widths) - 1))]
+    best = int(np.argmin(costs))
+    nwin = _merged_windows(bounds, band_widths, best, np.arange(n, dtype=np.int64), words)
     nwin = np.where(tier == 2, nwin, 1)
     for t, name in ((0, "c4_small"), (1, "c4_mid"), (2, "c4_window")):
         sel = tier == t
