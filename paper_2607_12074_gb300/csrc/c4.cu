@@ -62,7 +62,7 @@ constexpr int kChunk = 1024;                 // elements per split chunk
 // ends where band b + 1 starts, the last band at GI_HI).  GI_N1 = GI_BAND: the first band starts at n1.
 constexpr int kBands = 7;
 enum : int { GI_HI = 0, GI_NWIN = 1, GI_BAND = 2, GI_N1 = GI_BAND };
-static_assert(GI_BAND + kBands <= kGInfo, "ginfo slots");
+static_assert(GI_BAND + kBands <= kGInfo && kBands < 32, "ginfo slots; one search per lane");
 
 // counter bits of band b and the largest degree the band holds
 __host__ __device__ constexpr int band_width(int b) {
@@ -135,8 +135,8 @@ __device__ __forceinline__ int64_t merged_windows(const int64_t* st, unsigned ma
     for (int b = 0; b < kBands; ++b) {
         if (b + 1 < kBands && ((mask >> b) & 1u)) continue;  // the group goes on into band b + 1
         const int64_t e = st[b + 1] < u ? st[b + 1] : u;
-        const int64_t S = span_of<WORDS>(b);
-        if (e > gs) total += (e - gs + S - 1) / S;
+        const uint32_t S = (uint32_t)WORDS * (uint32_t)band_per_word(b);  // constant once unrolled
+        if (e > gs) total += ((uint32_t)(e - gs) + (S - 1u)) / S;  // ranks and spans fit 31 bits
         gs = st[b + 1];
     }
     return total;
@@ -160,26 +160,39 @@ __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int
         const int64_t lo = gbase ? gbase[g] : 0, gend = gbase ? gbase[g + 1] : n;
         auto clamp = [&](int64_t v) { return v < x_lo ? x_lo : (v > x_hi ? x_hi : v); };
         const int64_t hi = gend < x_hi ? gend : x_hi;
-        int64_t n1 = clamp(first_above_in(deg, lo, gend, 1));
+        // lane 0: n1 (first rank of degree >= 2); lane b < kBands: the first rank above band b - 1's
+        // degrees (band b's start); lane kBands: the first rank of degree >= 64.  One search each.
+        const int32_t t = lane == 0 ? 1 : (lane < kBands ? band_max_degree(lane - 1) : 63);
+        const int64_t r_lane = lane <= kBands ? first_above_in(deg, lo, gend, t) : gend;
+        int64_t n1 = clamp(__shfl_sync(0xffffffffu, r_lane, 0));
         n1 = n1 < hi ? n1 : hi;
         int64_t st[kBands + 1];
         st[0] = n1;
         st[kBands] = hi;
 #pragma unroll
-        for (int b = 1; b < kBands; ++b) {  // band b starts at the first rank above band b - 1's degrees
-            const int64_t r = clamp(first_above_in(deg, lo, gend, band_max_degree(b - 1)));
+        for (int b = 1; b < kBands; ++b) {
+            const int64_t r = clamp(__shfl_sync(0xffffffffu, r_lane, b));
             st[b] = r > n1 ? (r < hi ? r : hi) : n1;
         }
-        int64_t s0 = first_above_in(deg, lo, gend, 63);
+        int64_t s0 = __shfl_sync(0xffffffffu, r_lane, kBands);
         if (s0 >= gend) s0 = lo;
         const int64_t span = gend - s0;  // samples u lie in [s0, gend); none for an empty graph
+        static_assert(kMergeSamples == 64 && kMergeMasks == 64, "two samples and two masks per lane");
+        int64_t us[2];
+        double ws[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // lane holds samples lane and lane + 32 (loads issued together)
+            us[h] = s0 + (span * (2 * (lane + 32 * h) + 1)) / (2 * kMergeSamples);
+            ws[h] = span > 0 ? (double)deg[us[h]] : 0.0;
+        }
         unsigned best_mask = 0;
         double best = 0.0;
         for (int m = lane; m < kMergeMasks; m += 32) {
             double c = 0.0;
-            for (int k = 0; span > 0 && k < kMergeSamples; ++k) {
-                const int64_t u = s0 + (span * (2 * k + 1)) / (2 * kMergeSamples);
-                c += (double)deg[u] * (double)merged_windows<WORDS>(st, (unsigned)m, u);
+            for (int k = 0; k < kMergeSamples; ++k) {  // uniform over the warp: every lane shuffles
+                const int64_t u = __shfl_sync(0xffffffffu, k < 32 ? us[0] : us[1], k & 31);
+                const double w = __shfl_sync(0xffffffffu, k < 32 ? ws[0] : ws[1], k & 31);
+                c += w * (double)merged_windows<WORDS>(st, (unsigned)m, u);
             }
             if (m == lane || c < best) {
                 best = c;
