@@ -115,6 +115,10 @@ harp_status harp_csr_arrays(const harp_csr* g, const int64_t** offsets, const in
 #define HARP_PLAN_NO_REUSE 2u  /* flags: signature reuse off: every 4-clique extension recomputes  */
                                /* |N+(w) n S_uv| from N+(w) instead of reading the staged frontier */
                                /* of (u, w) (Section III-C); the counts are identical              */
+#define HARP_PLAN_NO_BAND_MERGE 4u /* flags: keep every wedge counter width (3, 4, 5, 6, 8, 16, 32  */
+                                   /* bits by the degree of x) as its own band of windows instead of */
+                                   /* merging narrow bands that would cost more windows; the counts  */
+                                   /* are identical                                                  */
 
 typedef struct harp_plan {
     uint32_t version;            /* HARP_ABI_VERSION                                               */

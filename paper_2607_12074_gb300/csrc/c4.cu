@@ -151,9 +151,10 @@ constexpr int kMergeSamples = 64;
 // that reaches past it, so bands may merge into the next wider one: each lane scores merge masks by
 // the windows of kMergeSamples roots spread evenly over the graph's ranks of degree >= 64 (the roots
 // that take the windowed mode), each weighted by its degree; the cheapest mask (lowest on a tie) wins.
+// merge = false keeps every band separate (mask 0).
 template <int WORDS>
 __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int64_t* __restrict__ gbase,
-                           int64_t G, int64_t x_lo, int64_t x_hi, int64_t* __restrict__ ginfo) {
+                           int64_t G, int64_t x_lo, int64_t x_hi, bool merge, int64_t* __restrict__ ginfo) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += warps) {
@@ -185,27 +186,29 @@ __global__ void k_c4_ginfo(const int32_t* __restrict__ deg, int64_t n, const int
             us[h] = s0 + (span * (2 * (lane + 32 * h) + 1)) / (2 * kMergeSamples);
             ws[h] = span > 0 ? (double)deg[us[h]] : 0.0;
         }
-        unsigned best_mask = 0;
-        double best = 0.0;
-        for (int m = lane; m < kMergeMasks; m += 32) {
-            double c = 0.0;
-            for (int k = 0; k < kMergeSamples; ++k) {  // uniform over the warp: every lane shuffles
-                const int64_t u = __shfl_sync(0xffffffffu, k < 32 ? us[0] : us[1], k & 31);
-                const double w = __shfl_sync(0xffffffffu, k < 32 ? ws[0] : ws[1], k & 31);
-                c += w * (double)merged_windows<WORDS>(st, (unsigned)m, u);
+        unsigned best_mask = 0;  // mask 0: every band separate
+        if (merge) {             // uniform over the warp (a kernel argument)
+            double best = 0.0;
+            for (int m = lane; m < kMergeMasks; m += 32) {
+                double c = 0.0;
+                for (int k = 0; k < kMergeSamples; ++k) {  // uniform over the warp: every lane shuffles
+                    const int64_t u = __shfl_sync(0xffffffffu, k < 32 ? us[0] : us[1], k & 31);
+                    const double w = __shfl_sync(0xffffffffu, k < 32 ? ws[0] : ws[1], k & 31);
+                    c += w * (double)merged_windows<WORDS>(st, (unsigned)m, u);
+                }
+                if (m == lane || c < best) {
+                    best = c;
+                    best_mask = (unsigned)m;
+                }
             }
-            if (m == lane || c < best) {
-                best = c;
-                best_mask = (unsigned)m;
-            }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double oc = __shfl_xor_sync(0xffffffffu, best, o);
-            const unsigned om = __shfl_xor_sync(0xffffffffu, best_mask, o);
-            if (oc < best || (oc == best && om < best_mask)) {
-                best = oc;
-                best_mask = om;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double oc = __shfl_xor_sync(0xffffffffu, best, o);
+                const unsigned om = __shfl_xor_sync(0xffffffffu, best_mask, o);
+                if (oc < best || (oc == best && om < best_mask)) {
+                    best = oc;
+                    best_mask = om;
+                }
             }
         }
         if (lane == 0) {
@@ -814,14 +817,15 @@ unsigned grid_cap(int64_t work, int threads, int64_t cap) {
 
 // The whole wedge pass for one window size (MINB resident window blocks per SM).
 template <int MINB>
-harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, cudaStream_t s) {
+harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool merge, cudaStream_t s) {
     constexpr int WORDS = win_words(MINB);
     const int64_t n = g->n;
     const int64_t G = ws.G > 0 ? ws.G : 1;
     const Sink sink{ws.acc, ws.gid, ws.accG};
     int32_t* wcount = ws.q_win + n;
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
-    k_c4_ginfo<WORDS><<<grid_cap(G * 32, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.x_lo, ws.x_hi, ws.ginfo);
+    k_c4_ginfo<WORDS><<<grid_cap(G * 32, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.x_lo, ws.x_hi, merge,
+                                                                  ws.ginfo);
     HARP_LAUNCHED();
     // the roots' lower lists: row prefixes of a whole graph, or their own CSR in a partitioned block
     const bool lists = ws.loff != nullptr;
@@ -871,9 +875,10 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     uint32_t warp_max = plan.c4_warp_max_work ? plan.c4_warp_max_work : 512;
     if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
     // window size: the largest of the three that fits plan.c4_window_bytes (at least the smallest)
-    if (plan.c4_window_bytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, s);
-    if (plan.c4_window_bytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, s);
-    return wedge_pass<4>(g, ws, warp_max, s);
+    const bool merge = !(plan.flags & HARP_PLAN_NO_BAND_MERGE);
+    if (plan.c4_window_bytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, merge, s);
+    if (plan.c4_window_bytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, merge, s);
+    return wedge_pass<4>(g, ws, warp_max, merge, s);
 }
 
 }  // namespace harp

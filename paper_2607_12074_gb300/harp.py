@@ -22,7 +22,7 @@ HARP_PTR_HOST, HARP_PTR_DEVICE = 0, 1
 HARP_ABI_VERSION = 1
 HARP_BASIS_TRIANGLE_WEDGE = 0
 HARP_PROBE_HASH, HARP_PROBE_BSEARCH = 1, 2
-HARP_PLAN_NO_GRAPH, HARP_PLAN_NO_REUSE = 1, 2
+HARP_PLAN_NO_GRAPH, HARP_PLAN_NO_REUSE, HARP_PLAN_NO_BAND_MERGE = 1, 2, 4
 
 MOTIFS = ("star3", "path4", "paw", "cycle4", "diamond", "clique4")
 STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")

@@ -6,6 +6,7 @@ and the warp / CTA-hash / windowed wedge modes; plus the full R-MAT scale-20 wor
 stored oracle counts.
 """
 import json
+import math
 import os
 import sys
 
@@ -17,7 +18,7 @@ import oracle as O
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
-from graph_families import closed_forms, complete, edges_of  # noqa: E402
+from graph_families import closed_forms, complete, edges_of, kbip  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -210,3 +211,37 @@ def test_large_grid_boundary_table(harp):
         p.version = harp.HARP_ABI_VERSION
         p.c4_window_bytes = bytes_
         assert harp.count4_edges(g.n, g.src, g.dst, p).tolist() == want, bytes_
+
+
+def test_counter_widths_at_their_limits(harp):
+    """Wedge counters are 3, 4, 5, 6, 8, 16 or 32 bits wide by the degree of x (cnt(x) <= d(x)).  In
+    K_{k,k} (ranks = ids, all degrees k) the top root u has every vertex of the other side as a lower
+    neighbour, so every x on u's side below u reaches cnt(x) = d(x) = k: k = 2^b - 1 fills a b-bit
+    counter exactly and k = 2^b moves x into the next band.  K_{2,k} does the same for the 16-bit
+    band's limit and the 32-bit band.  c4_warp_max_work = 1 sends every root with wedge work to the
+    windowed counters; with and without band merging the counts are the closed forms."""
+    cases = [(k, k) for k in (7, 8, 15, 16, 31, 32, 63, 64, 255, 256)] + [(2, 65535), (2, 65536)]
+    for a, b in cases:
+        s, d = kbip(a, b)
+        want = [a * math.comb(b, 3) + b * math.comb(a, 3), 0, 0, math.comb(a, 2) * math.comb(b, 2), 0, 0]
+        for flags in (0, harp.HARP_PLAN_NO_BAND_MERGE):
+            p = harp.harp_plan()
+            p.version = harp.HARP_ABI_VERSION
+            p.c4_warp_max_work = 1
+            p.flags = flags
+            got, _ = gpu_count(harp, a + b, s, d, plan=p)
+            assert got.tolist() == want, (a, b, flags)
+
+
+def test_band_merging_never_changes_counts(harp):
+    """A heavy-tailed graph whose x-range has every counter band: merged or separate bands, and the
+    windowed or the warp-hash mode for small roots, all give the oracle's counts."""
+    g = graphgen.chung_lu(100_000, 2.1, 2000, 6, 11)
+    want = O.count4_combo(g.n, g.src, g.dst).tolist()
+    for wm in (0, 1):
+        for flags in (0, harp.HARP_PLAN_NO_BAND_MERGE):
+            p = harp.harp_plan()
+            p.version = harp.HARP_ABI_VERSION
+            p.c4_warp_max_work = wm
+            p.flags = flags
+            assert harp.count4_edges(g.n, g.src, g.dst, p).tolist() == want, (wm, flags)
