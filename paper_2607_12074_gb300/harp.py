@@ -23,6 +23,7 @@ HARP_ABI_VERSION = 1
 HARP_BASIS_TRIANGLE_WEDGE = 0
 HARP_PROBE_HASH, HARP_PROBE_BSEARCH = 1, 2
 HARP_PLAN_NO_GRAPH, HARP_PLAN_NO_REUSE, HARP_PLAN_NO_BAND_MERGE = 1, 2, 4
+HARP_NSEGMENTS = 9
 
 MOTIFS = ("star3", "path4", "paw", "cycle4", "diamond", "clique4")
 STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")
@@ -449,7 +450,7 @@ def harp_set_profiling(enable: bool) -> None:
 
 
 def harp_last_stage_times() -> tuple[list[float], int]:
-    ms = (ctypes.c_float * 9)()
+    ms = (ctypes.c_float * HARP_NSEGMENTS)()
     launches = ctypes.c_int64()
     _check(lib().harp_last_stage_times(ms, ctypes.byref(launches)), "harp_last_stage_times")
     return list(ms), launches.value

@@ -69,3 +69,56 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(harp, "_lib", None)
     with pytest.raises(harp.HarpUnavailable):
         harp.lib()
+
+
+def _c_layouts(tmp_path, structs):
+    """sizeof and every field's offset of each struct, as gcc lays out include/harp.h."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "harp.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'    printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = {}
+    for row in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = row.split()
+        out[(s, f)] = int(v)
+    return out
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the header's size and field offsets."""
+    from paper_2607_12074_gb300 import harp
+    classes = {name: getattr(harp, name) for name in
+               ("harp_plan", "harp_select_opts", "harp_partition_stats", "harp_server_opts", "harp_server_stats")}
+    structs = {name: [f for f, _ in cls._fields_] for name, cls in classes.items()}
+    c = _c_layouts(tmp_path, structs)
+    for name, cls in classes.items():
+        assert c[(name, "size")] == ctypes.sizeof(cls), name
+        for f in structs[name]:
+            assert c[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def test_binding_constants_match_the_header():
+    """Every HARP_* constant the binding defines has the header's value (#define or enum)."""
+    from paper_2607_12074_gb300 import harp
+    values = {}
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^#define\s+(HARP_\w+)\s+\(?(-?\d+)[uUlL]*\)?\s*$", text, flags=re.M):
+            values[m.group(1)] = int(m.group(2))
+        for body in re.findall(r"enum\s*\w*\s*\{(.*?)\}", text, flags=re.S):
+            for m in re.finditer(r"(HARP_\w+)\s*=\s*(-?\d+)", body):
+                values[m.group(1)] = int(m.group(2))
+    bound = {k: v for k, v in vars(harp).items() if k.startswith("HARP_") and isinstance(v, int)}
+    assert bound, "the binding defines no constants"
+    missing = sorted(k for k in bound if k not in values)
+    assert not missing, missing
+    wrong = {k: (v, values[k]) for k, v in bound.items() if values[k] != v}
+    assert not wrong, wrong
+    # the binding's motif order is the header's HARP_<MOTIF> index order
+    assert [values["HARP_" + name.upper()] for name in harp.MOTIFS] == list(range(6))
