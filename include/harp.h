@@ -270,6 +270,22 @@ harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const int32_t* src,
                                     uint64_t budget_bytes, int32_t parts, uint64_t counts_out[6],
                                     harp_partition_stats* stats);
 
+/* Host-only dry run of harp_count4_partitioned: builds the same rank-order graph and cuts the same
+ * triangle ranges and wedge blocks under the same budget and parts rules, and counts nothing.  Lets a
+ * caller see how many device passes a graph needs and the largest device allocation before it runs.
+ * Ranges are in rank order (vertices sorted by (degree, id)), half-open.
+ * stats (required) receives partitions, m, device_peak_bytes, tri_blocks, wedge_blocks, wedge_sliced,
+ * graph_ms, cut_ms and host_ms (= graph_ms + cut_ms); the device and transfer fields are zero.
+ * tri_out: HOST int64[2 * cap], the first cap triangle ranges as (lo, hi).  wedge_out: HOST
+ * int64[4 * cap], the first cap wedge blocks as (root lo, root hi, x lo, x hi).  Both may be NULL when
+ * cap = 0; compare stats->tri_blocks / wedge_blocks with cap to see whether all were written.
+ * budget_bytes = 0 asks the device for half of its free memory, as the count does (HARP_ECUDA
+ * without a device); with a budget > 0 no CUDA call is made.
+ * Errors: HARP_EINVAL, HARP_EOVERFLOW, HARP_ENOMEM (as harp_count4_partitioned), HARP_ECUDA. */
+harp_status harp_partition_plan(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                                uint64_t budget_bytes, int32_t parts, harp_partition_stats* stats,
+                                int64_t* tri_out, int64_t* wedge_out, int64_t cap);
+
 /* ------------------------------------------------------------------------------------------------
  * Serving with continuous batching.  Requests are admitted in arrival order while the device bytes
  * held by admitted requests stay within the HBM budget; their edge lists are copied and their CSRs

@@ -532,6 +532,15 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
     return HARP_OK;
 }
 
+// Scratch the triangle kernels of a block allocate: the fallback's per-warp frontier buffers (sized
+// for the largest out-degree a graph of m edges can have, sqrt(2m)) and the global-staged tier's rows
+// (4096 x 4096 bits per block, one block per SM).
+int64_t tri_scratch_bytes(int64_t m) {
+    int64_t dmax = 1;
+    while (dmax * dmax < 2 * m) ++dmax;
+    return 152 * 8 * (dmax + 32) * 4 + (dmax > 1024 ? (int64_t)152 * 4096 * 128 * 4 : 0);
+}
+
 // The device results of all blocks, and where the time went.
 struct PartSums {
     uint64_t T = 0, K4 = 0, C4 = 0, PAWSUM = 0;
@@ -778,11 +787,7 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
         HARP_CK(cudaMemGetInfo(&fr, &tot));
         budget_bytes = fr / 2;
     }
-    int64_t dmax = 1;
-    while (dmax * dmax < 2 * g.m) ++dmax;
-    // scratch the triangle kernels allocate: the fallback's per-warp frontier buffers and the
-    // global-staged tier's rows (4096 x 4096 bits per block, one block per SM)
-    const int64_t fb = 152 * 8 * (dmax + 32) * 4 + (dmax > 1024 ? (int64_t)152 * 4096 * 128 * 4 : 0);
+    const int64_t fb = tri_scratch_bytes(g.m);
     std::vector<TriBlock> tri;
     std::vector<WedgeBlock> wedge;
     uint64_t device_peak = 0, h2d = 0, halo_arcs = 0;
@@ -864,6 +869,51 @@ extern "C" harp_status harp_count4_partitioned(int64_t n, int64_t m_in, const in
         stats->wedge_blocks = (int64_t)wedge.size();
         stats->wedge_sliced = 0;
         for (const WedgeBlock& b : wedge) stats->wedge_sliced += (b.xlo > 0 || b.xhi < n) ? 1 : 0;
+    }
+    return HARP_OK;
+}
+
+extern "C" harp_status harp_partition_plan(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                                           uint64_t budget_bytes, int32_t parts, harp_partition_stats* stats,
+                                           int64_t* tri_out, int64_t* wedge_out, int64_t cap) {
+    if (!stats || n < 0 || m_in < 0 || (m_in > 0 && (!src || !dst)) || parts < 0 || cap < 0 ||
+        (cap > 0 && (!tri_out || !wedge_out)))
+        return HARP_EINVAL;
+    if (n > 2147483647LL || m_in > 2147483647LL) return HARP_EOVERFLOW;
+    const auto t0 = std::chrono::steady_clock::now();
+    RankGraph g;
+    HARP_TRY(build_rank_graph(n, m_in, src, dst, g));
+    const auto t1 = std::chrono::steady_clock::now();
+    if (budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        HARP_CK(cudaMemGetInfo(&fr, &tot));
+        budget_bytes = fr / 2;
+    }
+    std::vector<TriBlock> tri;
+    std::vector<WedgeBlock> wedge;
+    uint64_t device_peak = 0;
+    HARP_TRY(cut_triangle_ranges(g, budget_bytes, parts, tri_scratch_bytes(g.m), tri, device_peak));
+    HARP_TRY(cut_wedge_blocks(g, budget_bytes, parts, wedge, device_peak));
+    const auto t2 = std::chrono::steady_clock::now();
+    *stats = harp_partition_stats{};
+    stats->partitions = (int64_t)(tri.size() + wedge.size());
+    stats->m = g.m;
+    stats->device_peak_bytes = device_peak;
+    stats->graph_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    stats->cut_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    stats->host_ms = stats->graph_ms + stats->cut_ms;
+    stats->tri_blocks = (int64_t)tri.size();
+    stats->wedge_blocks = (int64_t)wedge.size();
+    for (const WedgeBlock& b : wedge) stats->wedge_sliced += (b.xlo > 0 || b.xhi < n) ? 1 : 0;
+    for (size_t k = 0; k < tri.size() && (int64_t)k < cap; ++k) {
+        tri_out[2 * k] = tri[k].lo;
+        tri_out[2 * k + 1] = tri[k].hi;
+    }
+    for (size_t k = 0; k < wedge.size() && (int64_t)k < cap; ++k) {
+        wedge_out[4 * k] = wedge[k].lo;
+        wedge_out[4 * k + 1] = wedge[k].hi;
+        wedge_out[4 * k + 2] = wedge[k].xlo;
+        wedge_out[4 * k + 3] = wedge[k].xhi;
     }
     return HARP_OK;
 }

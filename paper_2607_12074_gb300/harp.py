@@ -144,6 +144,8 @@ def lib():
             getattr(L, name).restype = i32
         L.harp_count4_partitioned.argtypes = [i64, i64, vp, vp, ctypes.c_uint64, ctypes.c_int32, pu64,
                                               ctypes.POINTER(harp_partition_stats)]
+        L.harp_partition_plan.argtypes = [i64, i64, vp, vp, ctypes.c_uint64, ctypes.c_int32,
+                                          ctypes.POINTER(harp_partition_stats), pi64, pi64, i64]
         L.harp_server_create.argtypes = [ctypes.POINTER(harp_server_opts), ctypes.POINTER(vp)]
         L.harp_submit.argtypes = [vp, i64, i64, vp, vp, pu64]
         L.harp_poll.argtypes = [vp, ctypes.c_uint64, pu64, ctypes.POINTER(ctypes.c_int)]
@@ -151,7 +153,7 @@ def lib():
         L.harp_server_get_stats.argtypes = [vp, ctypes.POINTER(harp_server_stats)]
         L.harp_server_destroy.argtypes = [vp]
         L.harp_server_destroy.restype = None
-        for name in ("harp_count4_partitioned", "harp_server_create", "harp_submit", "harp_poll", "harp_wait",
+        for name in ("harp_count4_partitioned", "harp_partition_plan", "harp_server_create", "harp_submit", "harp_poll", "harp_wait",
                      "harp_server_get_stats"):
             getattr(L, name).restype = i32
         L.harp_set_profiling.argtypes = [i32]
@@ -393,6 +395,26 @@ def harp_count4_partitioned(n: int, src, dst, budget_bytes: int = 0, parts: int 
                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(st)),
            "harp_count4_partitioned")
     return out, st.as_dict()
+
+
+def harp_partition_plan(n: int, src, dst, budget_bytes: int, parts: int = 0):
+    """Host-only dry run of harp_count4_partitioned (no device work).
+
+    Returns (stats dict, triangle ranges int64[k, 2], wedge blocks int64[w, 4]) in rank order."""
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+    d = np.ascontiguousarray(np.asarray(dst, dtype=np.int32))
+    cap = 1024
+    while True:
+        st = harp_partition_stats()
+        tri = np.zeros((cap, 2), np.int64)
+        wedge = np.zeros((cap, 4), np.int64)
+        _check(lib().harp_partition_plan(int(n), s.size, s.ctypes.data, d.ctypes.data, int(budget_bytes), int(parts),
+                                         ctypes.byref(st), tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         wedge.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap),
+               "harp_partition_plan")
+        if st.tri_blocks <= cap and st.wedge_blocks <= cap:
+            return st.as_dict(), tri[:st.tri_blocks].copy(), wedge[:st.wedge_blocks].copy()
+        cap = max(st.tri_blocks, st.wedge_blocks)
 
 
 class Server:
