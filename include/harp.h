@@ -286,6 +286,17 @@ harp_status harp_partition_plan(int64_t n, int64_t m_in, const int32_t* src, con
                                 uint64_t budget_bytes, int32_t parts, harp_partition_stats* stats,
                                 int64_t* tri_out, int64_t* wedge_out, int64_t cap);
 
+/* Host-only: the simple graph of a host edge list in global rank order, as the partitioned count
+ * builds it on the host (Section III-D ordering): self-loops and duplicate edges dropped, vertices
+ * sorted by (degree, id), every row of the symmetric CSR sorted ascending by rank.
+ * m_out (required): undirected simple edges m.  rank_out: NULL or HOST int32[n], rank_out[v] = the
+ * rank of input vertex v.  off_out: NULL or HOST int64[n+1], row offsets by rank.  cols_out: NULL or
+ * HOST int32[cols_cap], the rows' ranks, written only when 2m <= cols_cap (call once with NULL to
+ * learn m).  Errors: HARP_EINVAL (ids outside [0, n), negative sizes), HARP_EOVERFLOW, HARP_ENOMEM. */
+harp_status harp_rank_csr_host(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                               int64_t* m_out, int32_t* rank_out, int64_t* off_out, int32_t* cols_out,
+                               int64_t cols_cap);
+
 /* ------------------------------------------------------------------------------------------------
  * Serving with continuous batching.  Requests are admitted in arrival order while the device bytes
  * held by admitted requests stay within the HBM budget; their edge lists are copied and their CSRs

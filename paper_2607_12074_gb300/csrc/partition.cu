@@ -77,6 +77,7 @@ struct RankGraph {
     std::vector<int32_t> deg, dplus;  // by rank
     std::vector<int64_t> offp;        // global out-arc numbering: N+(r) holds out-arcs offp[r] ..
     int64_t n1 = 0;                   // first rank of degree >= 2
+    std::vector<int32_t> rank;        // rank[v] of input vertex v
 };
 
 // f(lo, hi) over chunks of [0, n) taken from a shared counter by every host thread (rows of very
@@ -245,6 +246,7 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
             g.dplus[(size_t)r] = (int32_t)(z - a - split);
         }
     });
+    g.rank.swap(rank);
     g.offp.assign((size_t)n + 1, 0);
     g.n1 = n;
     for (int64_t r = 0; r < n; ++r) {
@@ -315,12 +317,14 @@ inline int32_t out_nbr(const RankGraph& g, int64_t r, int64_t k) {
 // Exact out-arcs of the triangle halo of [lo, hi) (distinct out-lists of R and N+(R)), on all host
 // cores: each vertex is claimed once through its mark byte.  mark is all zero on entry and on return.
 int64_t tri_extent(const RankGraph& g, int64_t lo, int64_t hi, std::vector<uint8_t>& mark) {
+    if (lo == 0 && hi == g.n) return g.offp[(size_t)g.n];  // every vertex is in the halo: all out-arcs
     std::vector<int64_t> part(host_threads(), 0);
     std::vector<std::vector<int32_t>> claimed(host_threads());
     parallel_for(hi - lo, [&](int64_t a, int64_t b, unsigned t) {
         int64_t outs = 0;
-        auto add = [&](int32_t v) {
-            if (__atomic_exchange_n(&mark[(size_t)v], (uint8_t)1, __ATOMIC_RELAXED) == 0) {
+        auto add = [&](int32_t v) {  // a plain load first: hub marks are read by every thread
+            if (__atomic_load_n(&mark[(size_t)v], __ATOMIC_RELAXED) == 0 &&
+                __atomic_exchange_n(&mark[(size_t)v], (uint8_t)1, __ATOMIC_RELAXED) == 0) {
                 claimed[t].push_back(v);
                 outs += g.dplus[(size_t)v];
             }
@@ -461,7 +465,9 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
                 const int64_t dm = list_arcs_of(g, u);
                 for (int64_t a = 0; a < dm; ++a) {
                     const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
-                    if (__atomic_exchange_n(&mark[(size_t)w], (uint8_t)1, __ATOMIC_RELAXED) == 0) lower[t].push_back(w);
+                    if (__atomic_load_n(&mark[(size_t)w], __ATOMIC_RELAXED) == 0 &&
+                        __atomic_exchange_n(&mark[(size_t)w], (uint8_t)1, __ATOMIC_RELAXED) == 0)
+                        lower[t].push_back(w);
                 }
             }
         });
@@ -915,5 +921,19 @@ extern "C" harp_status harp_partition_plan(int64_t n, int64_t m_in, const int32_
         wedge_out[4 * k + 2] = wedge[k].xlo;
         wedge_out[4 * k + 3] = wedge[k].xhi;
     }
+    return HARP_OK;
+}
+
+extern "C" harp_status harp_rank_csr_host(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst,
+                                          int64_t* m_out, int32_t* rank_out, int64_t* off_out, int32_t* cols_out,
+                                          int64_t cols_cap) {
+    if (!m_out || n < 0 || m_in < 0 || (m_in > 0 && (!src || !dst)) || cols_cap < 0) return HARP_EINVAL;
+    if (n > 2147483647LL || m_in > 2147483647LL) return HARP_EOVERFLOW;
+    RankGraph g;
+    HARP_TRY(build_rank_graph(n, m_in, src, dst, g));
+    *m_out = g.m;
+    if (rank_out) std::copy(g.rank.begin(), g.rank.end(), rank_out);
+    if (off_out) std::copy(g.off.begin(), g.off.end(), off_out);
+    if (cols_out && 2 * g.m <= cols_cap) std::copy(g.cols.begin(), g.cols.end(), cols_out);
     return HARP_OK;
 }

@@ -146,6 +146,8 @@ def lib():
                                               ctypes.POINTER(harp_partition_stats)]
         L.harp_partition_plan.argtypes = [i64, i64, vp, vp, ctypes.c_uint64, ctypes.c_int32,
                                           ctypes.POINTER(harp_partition_stats), pi64, pi64, i64]
+        L.harp_rank_csr_host.argtypes = [i64, i64, vp, vp, pi64, ctypes.POINTER(ctypes.c_int32), pi64,
+                                         ctypes.POINTER(ctypes.c_int32), i64]
         L.harp_server_create.argtypes = [ctypes.POINTER(harp_server_opts), ctypes.POINTER(vp)]
         L.harp_submit.argtypes = [vp, i64, i64, vp, vp, pu64]
         L.harp_poll.argtypes = [vp, ctypes.c_uint64, pu64, ctypes.POINTER(ctypes.c_int)]
@@ -153,7 +155,7 @@ def lib():
         L.harp_server_get_stats.argtypes = [vp, ctypes.POINTER(harp_server_stats)]
         L.harp_server_destroy.argtypes = [vp]
         L.harp_server_destroy.restype = None
-        for name in ("harp_count4_partitioned", "harp_partition_plan", "harp_server_create", "harp_submit", "harp_poll", "harp_wait",
+        for name in ("harp_count4_partitioned", "harp_partition_plan", "harp_rank_csr_host", "harp_server_create", "harp_submit", "harp_poll", "harp_wait",
                      "harp_server_get_stats"):
             getattr(L, name).restype = i32
         L.harp_set_profiling.argtypes = [i32]
@@ -415,6 +417,23 @@ def harp_partition_plan(n: int, src, dst, budget_bytes: int, parts: int = 0):
         if st.tri_blocks <= cap and st.wedge_blocks <= cap:
             return st.as_dict(), tri[:st.tri_blocks].copy(), wedge[:st.wedge_blocks].copy()
         cap = max(st.tri_blocks, st.wedge_blocks)
+
+
+def harp_rank_csr_host(n: int, src, dst):
+    """The host rank-order graph of the partitioned path: (rank int32[n], offsets int64[n+1], cols int32[2m])."""
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+    d = np.ascontiguousarray(np.asarray(dst, dtype=np.int32))
+    m = ctypes.c_int64()
+    _check(lib().harp_rank_csr_host(int(n), s.size, s.ctypes.data, d.ctypes.data, ctypes.byref(m), None, None, None, 0),
+           "harp_rank_csr_host")
+    rank = np.zeros(n, np.int32)
+    off = np.zeros(n + 1, np.int64)
+    cols = np.zeros(max(2 * m.value, 1), np.int32)
+    p32 = ctypes.POINTER(ctypes.c_int32)
+    _check(lib().harp_rank_csr_host(int(n), s.size, s.ctypes.data, d.ctypes.data, ctypes.byref(m),
+                                    rank.ctypes.data_as(p32), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    cols.ctypes.data_as(p32), cols.size), "harp_rank_csr_host")
+    return rank, off, cols[:2 * m.value]
 
 
 class Server:

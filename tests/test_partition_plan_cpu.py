@@ -138,3 +138,63 @@ def test_zero_budget_needs_a_device(lib):
     with pytest.raises(lib.HarpError) as ei:
         lib.harp_partition_plan(g.n, g.src, g.dst, 0)
     assert ei.value.status == lib.HARP_ECUDA
+
+
+def rank_graph_reference(n, src, dst):
+    """Definition of the rank-order simple graph: drop self-loops and duplicates, rank = position of
+    (degree, id) in lexicographic order, rows of the symmetric CSR sorted by rank."""
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    keep = s != d
+    lo, hi = np.minimum(s, d)[keep], np.maximum(s, d)[keep]
+    key = np.unique(lo * max(n, 1) + hi)
+    a, b = key // max(n, 1), key % max(n, 1)
+    deg = np.bincount(np.concatenate([a, b]), minlength=n)
+    order = np.lexsort((np.arange(n), deg))
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    ru, rv = rank[np.concatenate([a, b])], rank[np.concatenate([b, a])]
+    srt = np.lexsort((rv, ru))
+    off = np.concatenate([[0], np.cumsum(np.bincount(ru, minlength=n))])
+    return rank, off, rv[srt]
+
+
+def _messy_graph(n, m, seed):
+    """Uniform random pairs with repeated edges (both orientations), self-loops and isolated vertices."""
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, n, m)
+    d = rng.integers(0, n, m)
+    rep = rng.integers(0, m, m // 4)
+    s = np.concatenate([s, d[rep], s[: m // 10]])
+    d = np.concatenate([d, s[rep], s[: m // 10]])  # reversed repeats and self-loops
+    return s.astype(np.int32), d.astype(np.int32)
+
+
+@pytest.mark.parametrize("case", ["messy_small", "messy_mid", "ba", "chung_lu", "rmat", "empty", "edgeless"])
+def test_host_rank_graph_is_the_definition(lib, case):
+    if case == "messy_small":
+        n, (s, d) = 50, _messy_graph(50, 300, 1)
+    elif case == "messy_mid":
+        n, (s, d) = 30_000, _messy_graph(30_000, 400_000, 2)
+    elif case == "empty":
+        n, s, d = 0, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    elif case == "edgeless":
+        n, s, d = 17, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    else:
+        g = {"ba": lambda: graphgen.ba(20_000, 6, 4), "chung_lu": lambda: graphgen.chung_lu(80_000, 2.1, 5000, 8, 9),
+             "rmat": lambda: graphgen.rmat(15, 16, seed=3)}[case]()
+        n, s, d = g.n, g.src, g.dst
+    rank, off, cols = lib.harp_rank_csr_host(n, s, d)
+    want_rank, want_off, want_cols = rank_graph_reference(n, s, d)
+    assert np.array_equal(rank, want_rank)
+    assert np.array_equal(off, want_off)
+    assert np.array_equal(cols, want_cols)
+
+
+def test_host_rank_graph_rejects_bad_ids(lib):
+    with pytest.raises(lib.HarpError) as ei:
+        lib.harp_rank_csr_host(4, np.array([0, 4], np.int32), np.array([1, 2], np.int32))
+    assert ei.value.status == lib.HARP_EINVAL
+    with pytest.raises(lib.HarpError) as ei:
+        lib.harp_rank_csr_host(4, np.array([0, -1], np.int32), np.array([1, 2], np.int32))
+    assert ei.value.status == lib.HARP_EINVAL
