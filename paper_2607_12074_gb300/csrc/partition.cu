@@ -102,10 +102,93 @@ void parallel_dynamic(int64_t n, int64_t chunk, F&& f) {
     for (auto& x : th) x.join();
 }
 
-// The rank-order CSR without atomics: arcs are partitioned by source-id bucket (per-thread histograms
-// and thread-private cursors), each bucket - a few thousand rows - is turned into its rows locally,
-// every row is sorted and deduplicated, the rank order (degree, id) is a counting sort by degree, and
-// the rows are copied to their ranks with relabelled entries and sorted again.
+// Stable regrouping of a symmetric arc multiset by its other endpoint.  Sources i = 0 .. N - 1 are
+// visited in increasing order; source i's entries are row(i) = [begin, end) of `cols`.  Entry c of
+// source i goes to destination row dest(c) with value i, so every destination row receives its
+// values in increasing order (sorted rows without a sort).  out_off[0 .. n_dest] are the destination
+// rows' offsets; because the arcs are symmetric they are also the prefix of the sources' entry counts
+// in visit order, which balances the sources over the host threads.  With dedup, a value equal to the
+// one placed before it in its row is dropped and kept[d] receives the number placed in row d (rows
+// keep their full extent, the tail unused).  scratch holds out_off[n_dest] packed (row, value) pairs.
+// done(d0, d1) runs on destination rows [d0, d1) right after they are filled (while they are in cache).
+constexpr int64_t kRegroupBuckets = 4096;
+template <typename RowOf, typename DestOf, typename Done>
+void regroup_by_destination(int64_t N, RowOf row, DestOf dest, int64_t n_dest, const int64_t* out_off, int32_t* out,
+                            uint64_t* scratch, bool dedup, int32_t* kept, Done&& done) {
+    int sh = 0;  // destination bucket: d >> sh, about kRegroupBuckets buckets
+    while ((n_dest >> sh) > kRegroupBuckets) ++sh;
+    const int64_t nb = (n_dest >> sh) + 1;
+    const int64_t total = out_off[n_dest];
+    const unsigned nt = total < (1 << 16) ? 1 : host_threads();
+    std::vector<int64_t> cut((size_t)nt + 1, N);  // thread t visits sources [cut[t], cut[t+1])
+    cut[0] = 0;
+    for (unsigned t = 1; t < nt; ++t)
+        cut[t] = std::upper_bound(out_off, out_off + N + 1, total * (int64_t)t / (int64_t)nt) - out_off - 1;
+    for (unsigned t = 1; t <= nt; ++t) cut[t] = std::max(cut[t], cut[t - 1]);
+    std::vector<std::vector<int64_t>> cnt(nt, std::vector<int64_t>((size_t)nb, 0));
+    auto each_thread = [&](auto&& f) {
+        if (nt == 1) {
+            f(0u);
+            return;
+        }
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t) th.emplace_back([&, t] { f(t); });
+        for (auto& x : th) x.join();
+    };
+    each_thread([&](unsigned t) {
+        std::vector<int64_t>& c = cnt[t];
+        for (int64_t i = cut[t]; i < cut[t + 1]; ++i) {
+            const auto r = row(i);
+            for (const int32_t* p = r.first; p != r.second; ++p) c[(size_t)(dest(*p) >> sh)]++;
+        }
+    });
+    std::vector<int64_t> bstart((size_t)nb + 1, 0);
+    for (int64_t k = 0; k < nb; ++k) {  // bucket k, thread t's part after those of threads < t
+        int64_t run = bstart[(size_t)k];
+        for (unsigned t = 0; t < nt; ++t) {
+            const int64_t c = cnt[t][(size_t)k];
+            cnt[t][(size_t)k] = run;
+            run += c;
+        }
+        bstart[(size_t)k + 1] = run;
+    }
+    each_thread([&](unsigned t) {
+        std::vector<int64_t>& cur = cnt[t];
+        for (int64_t i = cut[t]; i < cut[t + 1]; ++i) {
+            const auto r = row(i);
+            for (const int32_t* p = r.first; p != r.second; ++p) {
+                const int64_t d = dest(*p);
+                scratch[(size_t)cur[(size_t)(d >> sh)]++] = ((uint64_t)d << 32) | (uint32_t)i;
+            }
+        }
+    });
+    parallel_dynamic(nb, 1, [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t d0 = k << sh, d1 = std::min<int64_t>((k + 1) << sh, n_dest);
+            if (d0 >= d1) continue;
+            std::vector<int64_t> pos((size_t)(d1 - d0));
+            for (int64_t d = d0; d < d1; ++d) pos[(size_t)(d - d0)] = out_off[d];
+            for (int64_t e = bstart[(size_t)k]; e < bstart[(size_t)k + 1]; ++e) {
+                const uint64_t pr = scratch[(size_t)e];
+                const int64_t d = (int64_t)(pr >> 32);
+                const int32_t v = (int32_t)(uint32_t)pr;
+                int64_t& at = pos[(size_t)(d - d0)];
+                if (dedup && at > out_off[d] && out[at - 1] == v) continue;
+                out[at++] = v;
+            }
+            if (kept)
+                for (int64_t d = d0; d < d1; ++d) kept[d] = (int32_t)(pos[(size_t)(d - d0)] - out_off[d]);
+            done(d0, d1);
+        }
+    });
+}
+
+// The rank-order CSR without atomics and without sorting rows: arcs are partitioned by source-id
+// bucket (per-thread histograms and thread-private cursors) and each bucket is turned into its rows
+// (unsorted); regrouping those rows by their other endpoint, visited in id order, sorts every row by
+// id and puts duplicates side by side, where they are dropped; the rank order (degree, id) is a
+// counting sort by degree; regrouping once more, visiting vertices in rank order and relabelling the
+// other endpoint, gives rows sorted by rank.
 harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst, RankGraph& g) {
     int sh = 0;  // bucket of a vertex: v >> sh, about 1024 buckets
     while ((n >> sh) > 1024) ++sh;
@@ -150,9 +233,12 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
         bstart[(size_t)k + 1] = run;
     }
     const int64_t A = bstart[(size_t)nb];
-    buf<uint64_t> pairs;  // (row << 32) | column, in bucket order
+    buf<uint64_t> pairs;  // (row << 32) | column, in bucket order; later the regrouping scratch
+    buf<int32_t> cu, c0;  // rows by id: unsorted with duplicates, then sorted without
     try {
         pairs.resize((size_t)(A > 0 ? A : 1));
+        cu.resize((size_t)(A > 0 ? A : 1));
+        c0.resize((size_t)(A > 0 ? A : 1));
     } catch (...) {
         return HARP_ENOMEM;
     }
@@ -175,13 +261,6 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     std::vector<std::vector<int64_t>>().swap(hist);
     // each bucket into its rows (positions of the id-order CSR are the bucket's own range)
     std::vector<int64_t> off0((size_t)n + 1, 0);
-    buf<int32_t> c0;
-    try {
-        c0.resize((size_t)(A > 0 ? A : 1));
-    } catch (...) {
-        return HARP_ENOMEM;
-    }
-    std::vector<int32_t> deg0((size_t)n, 0);
     parallel_dynamic(nb, 1, [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t r0 = k << sh, r1 = std::min<int64_t>((k + 1) << sh, n);
@@ -193,18 +272,18 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
             for (int64_t r = r0; r < r1; ++r) off0[(size_t)r] = bstart[(size_t)k] + pos[(size_t)(r - r0)];
             for (int64_t i = bstart[(size_t)k]; i < bstart[(size_t)k + 1]; ++i) {
                 const uint64_t pr = pairs[(size_t)i];
-                c0[(size_t)(bstart[(size_t)k] + pos[(size_t)((int64_t)(pr >> 32) - r0)]++)] = (int32_t)(uint32_t)pr;
-            }
-            for (int64_t r = r0; r < r1; ++r) {  // after the scatter pos[r - r0] is the start of row r + 1
-                auto b = c0.begin() + off0[(size_t)r];
-                auto e = c0.begin() + bstart[(size_t)k] + pos[(size_t)(r - r0)];
-                std::sort(b, e);
-                deg0[(size_t)r] = (int32_t)(std::unique(b, e) - b);
+                cu[(size_t)(bstart[(size_t)k] + pos[(size_t)((int64_t)(pr >> 32) - r0)]++)] = (int32_t)(uint32_t)pr;
             }
         }
     });
     off0[(size_t)n] = A;
-    buf<uint64_t>().swap(pairs);
+    // rows sorted by id, duplicates dropped: row v keeps deg0[v] entries from off0[v]
+    std::vector<int32_t> deg0((size_t)n, 0);
+    regroup_by_destination(
+        n, [&](int64_t u) { return std::make_pair(cu.data() + off0[(size_t)u], cu.data() + off0[(size_t)u + 1]); },
+        [](int32_t v) { return (int64_t)v; }, n, off0.data(), c0.data(), pairs.data(), true, deg0.data(),
+        [](int64_t, int64_t) {});
+    buf<int32_t>().swap(cu);
     // rank = (degree, id): counting sort by degree, ids ascending inside a degree
     int32_t maxd = 0;
     for (int32_t d : deg0) maxd = d > maxd ? d : maxd;
@@ -221,31 +300,38 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     g.off.assign((size_t)n + 1, 0);
     for (int64_t r = 0; r < n; ++r) g.off[(size_t)r + 1] = g.off[(size_t)r] + deg0[(size_t)order[(size_t)r]];
     g.m = g.off[(size_t)n] / 2;
+    g.deg.resize((size_t)n);
+    g.dplus.resize((size_t)n);
     try {
         g.cols.resize((size_t)g.off[(size_t)n]);
     } catch (...) {
         return HARP_ENOMEM;
     }
-    parallel_dynamic(n, 1024, [&](int64_t lo, int64_t hi) {
-        for (int64_t r = lo; r < hi; ++r) {
+    // rows by rank, sorted: the other endpoints relabelled in place (one gather each), then vertices
+    // visited in rank order
+    parallel_dynamic(n, 4096, [&](int64_t lo, int64_t hi) {
+        for (int64_t v = lo; v < hi; ++v)
+            for (int64_t k = off0[(size_t)v]; k < off0[(size_t)v] + deg0[(size_t)v]; ++k)
+                c0[(size_t)k] = rank[(size_t)c0[(size_t)k]];
+    });
+    regroup_by_destination(
+        n,
+        [&](int64_t r) {
             const int32_t v = order[(size_t)r];
-            const int64_t b0 = off0[(size_t)v], d = deg0[(size_t)v], b = g.off[(size_t)r];
-            for (int64_t k = 0; k < d; ++k) g.cols[(size_t)(b + k)] = rank[(size_t)c0[(size_t)(b0 + k)]];
-            std::sort(g.cols.begin() + b, g.cols.begin() + b + d);
-        }
-    });
+            return std::make_pair(c0.data() + off0[(size_t)v], c0.data() + off0[(size_t)v] + deg0[(size_t)v]);
+        },
+        [](int32_t c) { return (int64_t)c; }, n, g.off.data(), g.cols.data(), pairs.data(), false, nullptr,
+        [&](int64_t r0, int64_t r1) {  // degree and out-degree (entries above r) of the rows just filled
+            for (int64_t r = r0; r < r1; ++r) {
+                const int64_t a = g.off[(size_t)r], z = g.off[(size_t)r + 1];
+                g.deg[(size_t)r] = (int32_t)(z - a);
+                const int64_t split =
+                    std::upper_bound(g.cols.begin() + a, g.cols.begin() + z, (int32_t)r) - (g.cols.begin() + a);
+                g.dplus[(size_t)r] = (int32_t)(z - a - split);
+            }
+        });
     buf<int32_t>().swap(c0);
-    g.deg.resize((size_t)n);
-    g.dplus.resize((size_t)n);
-    parallel_for(n, [&](int64_t lo, int64_t hi, unsigned) {
-        for (int64_t r = lo; r < hi; ++r) {
-            const int64_t a = g.off[(size_t)r], z = g.off[(size_t)r + 1];
-            g.deg[(size_t)r] = (int32_t)(z - a);
-            const int64_t split =
-                std::upper_bound(g.cols.begin() + a, g.cols.begin() + z, (int32_t)r) - (g.cols.begin() + a);
-            g.dplus[(size_t)r] = (int32_t)(z - a - split);
-        }
-    });
+    buf<uint64_t>().swap(pairs);
     g.rank.swap(rank);
     g.offp.assign((size_t)n + 1, 0);
     g.n1 = n;
