@@ -528,6 +528,35 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
             lo = hi;
         }
     }
+    // One range over the whole graph: its rows are those of every w that is a lower neighbour of a
+    // root with two or more lower neighbours, i.e. some u in N+(w) has d-(u) >= 2; each holds its
+    // elements x >= n1.  Counted per w without marks; when that block fits, no slicing is needed.
+    if (ranges.size() == 1 && ranges[0].first == 0 && ranges[0].second == n && n > 0) {
+        std::vector<int64_t> prow(host_threads(), 0), pla(host_threads(), 0);
+        parallel_for(n, [&](int64_t lo, int64_t hi, unsigned t) {
+            int64_t rows = 0, la = 0;
+            for (int64_t w = lo; w < hi; ++w) {
+                la += list_arcs_of(g, w);
+                const int64_t b = g.off[(size_t)w], e = g.off[(size_t)w + 1];
+                bool lower = false;
+                for (int64_t k = e - g.dplus[(size_t)w]; k < e && !lower; ++k) lower = list_arcs_of(g, g.cols[(size_t)k]) > 0;
+                if (lower)
+                    rows += e - (std::lower_bound(g.cols.begin() + b, g.cols.begin() + e, (int32_t)g.n1) - g.cols.begin());
+            }
+            prow[t] += rows;
+            pla[t] += la;
+        });
+        int64_t rows_total = 0, la = 0;
+        for (size_t t = 0; t < prow.size(); ++t) {
+            rows_total += prow[t];
+            la += pla[t];
+        }
+        if (parts > 0 || g.n1 >= n || wedge_block_bytes(n, rows_total, la) <= budget) {
+            peak = std::max<uint64_t>(peak, wedge_block_bytes(n, rows_total, la));
+            out.push_back({0, n, 0, n});
+            return HARP_OK;
+        }
+    }
     // x-slices per root range, cut from a histogram of the row elements the block would hold, counted
     // per x-bucket (at most 65,536 buckets, per-thread counts, no atomics); slices end on bucket
     // boundaries, and a bucket that cannot fit alone is cut exactly, per x.
