@@ -566,7 +566,6 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
     const unsigned nt = host_threads();
     std::vector<std::vector<int64_t>> hist(nt, std::vector<int64_t>((size_t)nbk, 0));
     std::vector<int64_t> hsum((size_t)nbk, 0);
-    std::vector<uint8_t> mark((size_t)n, 0);
     std::vector<std::vector<int32_t>> lower(nt);
     std::vector<int32_t> all;
     for (const auto& r : ranges) {
@@ -574,42 +573,47 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
         if (lo >= hi) continue;
         int64_t la = 0;
         for (int64_t u = lo; u < hi; ++u) la += list_arcs_of(g, u);
+        // the block's rows are those of every w < hi with a root u in N+(w) n [lo, hi) that has two or
+        // more lower neighbours; one pass over w (chunks taken dynamically: hub rows sit at the top)
+        // finds them and counts their elements x in [n1, hi) per x-bucket
         for (auto& l : lower) l.clear();
-        parallel_for(hi - lo, [&](int64_t a0, int64_t b0, unsigned t) {
-            for (int64_t u = lo + a0; u < lo + b0; ++u) {
-                const int64_t dm = list_arcs_of(g, u);
-                for (int64_t a = 0; a < dm; ++a) {
-                    const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
-                    if (__atomic_load_n(&mark[(size_t)w], __ATOMIC_RELAXED) == 0 &&
-                        __atomic_exchange_n(&mark[(size_t)w], (uint8_t)1, __ATOMIC_RELAXED) == 0)
-                        lower[t].push_back(w);
-                }
-            }
-        });
-        all.clear();
-        for (auto& l : lower) all.insert(all.end(), l.begin(), l.end());
         const int64_t xa = g.n1, xb = hi;  // opposite vertices of degree >= 2, below the range's end
         auto seg = [&](int32_t w, int64_t x0, int64_t x1, auto&& visit) {  // row w's elements in [x0, x1)
             const auto b = g.cols.begin() + g.off[(size_t)w], e = g.cols.begin() + g.off[(size_t)w + 1];
             for (auto it = std::lower_bound(b, e, (int32_t)x0); it != e && *it < x1; ++it) visit(*it);
         };
         {
+            std::atomic<int64_t> next{0};
             std::vector<std::thread> th;
             for (unsigned t = 0; t < nt; ++t)
                 th.emplace_back([&, t] {
                     std::vector<int64_t>& h = hist[t];
                     std::fill(h.begin(), h.end(), 0);
-                    const size_t a0 = all.size() * t / nt, b0 = all.size() * (t + 1) / nt;
-                    for (size_t k = a0; k < b0; ++k) seg(all[k], xa, xb, [&](int32_t x) { h[(size_t)(x >> bs)]++; });
+                    for (;;) {
+                        const int64_t w0 = next.fetch_add(256);
+                        if (w0 >= hi) break;
+                        for (int64_t w = w0; w < std::min<int64_t>(w0 + 256, hi); ++w) {
+                            const auto e = g.cols.begin() + g.off[(size_t)w + 1];
+                            bool root = false;
+                            for (auto it = std::lower_bound(g.cols.begin() + g.off[(size_t)w], e,
+                                                            (int32_t)std::max<int64_t>(lo, w + 1));
+                                 it != e && *it < hi && !root; ++it)
+                                root = list_arcs_of(g, *it) > 0;
+                            if (!root) continue;
+                            lower[t].push_back((int32_t)w);
+                            seg((int32_t)w, xa, xb, [&](int32_t x) { h[(size_t)(x >> bs)]++; });
+                        }
+                    }
                 });
             for (auto& x : th) x.join();
         }
+        all.clear();
+        for (auto& l : lower) all.insert(all.end(), l.begin(), l.end());
         for (int64_t k = 0; k < nbk; ++k) {
             int64_t c = 0;
             for (unsigned t = 0; t < nt; ++t) c += hist[t][(size_t)k];
             hsum[(size_t)k] = c;
         }
-        for (int32_t w : all) mark[(size_t)w] = 0;
         int64_t rows_total = 0;
         for (int64_t k = 0; k < nbk; ++k) rows_total += hsum[(size_t)k];
         if (parts > 0 || xa >= xb || wedge_block_bytes(n, rows_total, la) <= budget) {
