@@ -695,12 +695,15 @@ harp_status check_cuda(cudaError_t e) {
 harp_status run_triangle_block(const RankGraph& g, const TriBlock& blk, int dev, int64_t fb, cudaStream_t s,
                                PartSums& sum, uint64_t& h2d, uint64_t& halo_arcs) {
     const int64_t n = g.n;
-    // halo: out-lists of R and N+(R), local numbering in rank order
+    // halo: out-lists of R and N+(R), local numbering in rank order (flags set on all host cores)
     std::vector<uint8_t> in((size_t)n, 0);
-    for (int64_t u = blk.lo; u < blk.hi; ++u) {
-        in[(size_t)u] = 1;
-        for (int64_t k = 0; k < g.dplus[(size_t)u]; ++k) in[(size_t)out_nbr(g, u, k)] = 1;
-    }
+    parallel_for(blk.hi - blk.lo, [&](int64_t a, int64_t b, unsigned) {
+        for (int64_t u = blk.lo + a; u < blk.lo + b; ++u) {
+            __atomic_store_n(&in[(size_t)u], (uint8_t)1, __ATOMIC_RELAXED);
+            for (int64_t k = 0; k < g.dplus[(size_t)u]; ++k)
+                __atomic_store_n(&in[(size_t)out_nbr(g, u, k)], (uint8_t)1, __ATOMIC_RELAXED);
+        }
+    });
     std::vector<int64_t> offp((size_t)n + 1, 0);
     for (int64_t v = 0; v < n; ++v) offp[(size_t)v + 1] = offp[(size_t)v] + (in[(size_t)v] ? g.dplus[(size_t)v] : 0);
     const int64_t outs = offp[(size_t)n];
@@ -788,14 +791,16 @@ harp_status run_wedge_block(const RankGraph& g, const WedgeBlock& blk, int dev, 
     const int64_t la = loff[(size_t)n];
     buf<int32_t> lcols((size_t)(la > 0 ? la : 1));
     std::vector<uint8_t> in((size_t)n, 0);
-    for (int64_t u = blk.lo; u < blk.hi; ++u) {
-        const int64_t len = loff[(size_t)u + 1] - loff[(size_t)u];
-        for (int64_t a = 0; a < len; ++a) {
-            const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
-            lcols[(size_t)(loff[(size_t)u] + a)] = w;
-            in[(size_t)w] = 1;
+    parallel_for(blk.hi - blk.lo, [&](int64_t a0, int64_t b0, unsigned) {  // on all host cores
+        for (int64_t u = blk.lo + a0; u < blk.lo + b0; ++u) {
+            const int64_t len = loff[(size_t)u + 1] - loff[(size_t)u];
+            for (int64_t a = 0; a < len; ++a) {
+                const int32_t w = g.cols[(size_t)(g.off[(size_t)u] + a)];
+                lcols[(size_t)(loff[(size_t)u] + a)] = w;
+                __atomic_store_n(&in[(size_t)w], (uint8_t)1, __ATOMIC_RELAXED);
+            }
         }
-    }
+    });
     // rows of the lower neighbours, restricted to the slice [xa, xb) of opposite vertices
     const int64_t xa = std::max<int64_t>(blk.xlo, g.n1), xb = std::min<int64_t>(blk.xhi, blk.hi);
     std::vector<int64_t> off((size_t)n + 1, 0), rb((size_t)n, 0);
