@@ -337,6 +337,49 @@ def run_partitioned(args):
     return 0
 
 
+def run_whole(args):
+    """The same heavy-tailed family as the partitioned workload, counted whole on the device: the CSR is
+    built from device-resident edges, then each step is one harp_count4 with per-segment CUDA-event
+    times (the CSR, well above L2, is read from HBM every step)."""
+    import torch
+
+    import graphgen
+    from paper_2607_12074_gb300 import _build, harp
+
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    _build.build()
+    harp.lib()
+    t0 = time.perf_counter()
+    g = graphgen.chung_lu_large(args.n)
+    t_gen = time.perf_counter() - t0
+    csr = harp.harp_build_csr(g.n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda())
+    m = csr.info()["m"]
+    harp.harp_set_profiling(True)
+    runs = []
+    for k in range(args.warmup + args.steps):
+        with ClockSampler(local) as clocks:
+            counts = harp.harp_count4(csr)
+            ms, _ = harp.harp_last_stage_times()
+        if k >= args.warmup:
+            runs.append((sum(ms), ms, clocks.summary()))
+    harp.harp_set_profiling(False)
+    csr.close()
+    total, ms, clk = min(runs, key=lambda r: r[0])
+    line = {"metric": METRIC, "value": m / (total / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"chung_lu(n={g.n}, gamma=2.1, max expected degree {1e6 * g.n / 5e7:g}, "
+                                   f"mean degree 48, seed 1), whole graph on the device",
+                       "n": g.n, "m": m, "parallelism": "single", "l2": "inputs larger than L2"},
+            "segments_ms": {k: v for k, v in zip(SEGMENTS, ms)}, "generate_s": t_gen, "clocks": clk,
+            "counts": [int(x) for x in counts]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,14 +391,18 @@ def main():
     ap.add_argument("--no-meter", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
-    ap.add_argument("--workload", default="plain", choices=("plain", "partitioned"))
-    ap.add_argument("--n", type=int, default=50_000_000, help="vertices of the partitioned workload")
+    ap.add_argument("--workload", default="plain", choices=("plain", "partitioned", "whole"),
+                    help="plain: the R-MAT bench; partitioned / whole: the Chung-Lu family of --n vertices, "
+                         "partitioned under --cap-gib or counted whole on the device")
+    ap.add_argument("--n", type=int, default=50_000_000, help="vertices of the Chung-Lu workloads")
     ap.add_argument("--cap-gib", type=float, default=24.0, help="device cap of the partitioned workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "partitioned":
         return run_partitioned(args)
+    if args.workload == "whole":
+        return run_whole(args)
     args.warmup = max(args.warmup, 3)
 
     world, rank, local = dist_env()
