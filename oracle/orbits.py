@@ -24,9 +24,14 @@ other, which for the six 4-vertex motifs is decided by the vertex's degree insid
 ``out[v, o]`` = number of induced occurrences S with v in S playing orbit o.  Summed over v, orbit o
 gives its motif's count times the number of its vertices in that orbit (the last column).
 
+Functions: :func:`orbits4_brute` (every 4-subset), :func:`orbits4_esu` (each connected 4-set once) and
+:func:`orbits4_combo` (eleven non-induced statistics per vertex and a unit upper-triangular
+containment inversion, the per-vertex analogue of the global closure of Section III-F).
+
 Parity status: pinned in ``tests/test_oracle_orbits.py`` (brute force over every 4-subset, closed forms
-of complete, star, cycle, path, complete bipartite and wheel graphs, and the global counts of the C
-oracle); nothing is pinned to a value printed in the paper, which prints no count.
+of complete, star, cycle, path, complete bipartite and wheel graphs, each motif graph alone, and the
+global counts of the C oracle); nothing is pinned to a value printed in the paper, which prints no
+count.
 """
 from __future__ import annotations
 
@@ -108,4 +113,90 @@ def orbits4_esu(n, src, dst):
 
     for v in range(n):
         extend([v], [y for y in adj[v] if y > v], v)
+    return out
+
+
+# ---------------------------------------------------------------------------------------------------
+# Per-vertex closure: eleven non-induced statistics per vertex and their containment system.
+# ---------------------------------------------------------------------------------------------------
+# N[i] counts (not necessarily induced) copies of a pattern in which v plays role i; every induced
+# occurrence S that contains v contributes the number of such copies inside G[S].  Row i lists the
+# contribution of each induced orbit o (columns in ORBITS order); the matrix is unit upper triangular,
+# so the orbits follow by back-substitution from the 4-clique up, without division.
+#   N0  stars centred at v                         C(d_v, 3)
+#   N1  stars with v a leaf                        sum_{c in N(v)} C(d_c - 1, 2)
+#   N2  3-edge paths with v an end                 sum_{a in N(v)} sum_{b in N(a), b != v} (d_b - 1 - [b ~ v])
+#   N3  3-edge paths with v inner                  sum_{b in N(v)} sum_{a in N(v), a != b} (d_b - 1 - [a ~ b])
+#   N4  paws with v the pendant                    sum_{h in N(v)} (t_h - t_vh)
+#   N5  paws with v the degree-3 vertex            t_v (d_v - 2)
+#   N6  paws with v a degree-2 triangle vertex     sum_{h in N(v)} t_vh (d_h - 2)
+#   N7  4-cycles through v                         sum_{x != v} C(|N(v) n N(x)|, 2)
+#   N8  diamonds with v on the shared edge         sum_{s in N(v)} C(t_vs, 2)
+#   N9  diamonds with v a degree-2 vertex          sum_{triangles {v, a, b}} (t_ab - 1)
+#   N10 4-cliques through v
+# with t_e = triangles on edge e and t_v = triangles on vertex v.
+CONTAINMENT = np.array([
+    # o0 o1 o2 o3 o4 o5 o6 o7 o8 o9 o10
+    [1, 0, 0, 0, 0, 1, 0, 0, 1, 0, 1],   # N0: v of degree 3 in G[S]
+    [0, 1, 0, 0, 1, 0, 1, 0, 1, 2, 3],   # N1: neighbours of v of degree 3 in G[S]
+    [0, 0, 1, 0, 2, 0, 1, 2, 2, 4, 6],   # N2: Hamiltonian paths of G[S] ending at v
+    [0, 0, 0, 1, 0, 2, 1, 2, 4, 2, 6],   # N3: Hamiltonian paths of G[S] through v
+    [0, 0, 0, 0, 1, 0, 0, 0, 0, 2, 3],   # N4
+    [0, 0, 0, 0, 0, 1, 0, 0, 2, 0, 3],   # N5
+    [0, 0, 0, 0, 0, 0, 1, 0, 2, 2, 6],   # N6
+    [0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 3],   # N7
+    [0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 3],   # N8
+    [0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 3],   # N9
+    [0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1],   # N10
+], dtype=np.int64)
+
+
+def noninduced_per_vertex(n, src, dst):
+    """The eleven statistics N0..N10 of every vertex, by plain loops over the simple graph."""
+    adj = _adjacency(n, src, dst)
+    deg = [len(a) for a in adj]
+    t_e = {}
+    for u in range(n):
+        for v in adj[u]:
+            if u < v:
+                t_e[(u, v)] = len(adj[u] & adj[v])
+
+    def te(a, b):
+        return t_e[(a, b) if a < b else (b, a)]
+
+    t_v = [sum(te(v, h) for h in adj[v]) // 2 for v in range(n)]
+    out = np.zeros((n, 11), np.uint64)
+    for v in range(n):
+        d = deg[v]
+        N = [0] * 11
+        N[0] = d * (d - 1) * (d - 2) // 6
+        N[1] = sum((deg[c] - 1) * (deg[c] - 2) // 2 for c in adj[v])
+        N[2] = sum(deg[b] - 1 - (b in adj[v]) for a in adj[v] for b in adj[a] if b != v)
+        N[3] = sum(deg[b] - 1 - (a in adj[b]) for b in adj[v] for a in adj[v] if a != b)
+        N[4] = sum(t_v[h] - te(v, h) for h in adj[v])
+        N[5] = t_v[v] * (d - 2) if d >= 2 else 0
+        N[6] = sum(te(v, h) * (deg[h] - 2) for h in adj[v])
+        common = {}
+        for a in adj[v]:
+            for x in adj[a]:
+                if x != v:
+                    common[x] = common.get(x, 0) + 1
+        N[7] = sum(c * (c - 1) // 2 for c in common.values())
+        N[8] = sum(te(v, s) * (te(v, s) - 1) // 2 for s in adj[v])
+        N[9] = sum(te(a, b) - 1 for a in adj[v] for b in adj[v] if a < b and b in adj[a])
+        N[10] = sum(1 for a in adj[v] for b in adj[v] for c in adj[v]
+                    if a < b < c and b in adj[a] and c in adj[a] and c in adj[b])
+        out[v] = N
+    return out
+
+
+def orbits4_combo(n, src, dst):
+    """Orbit counts by back-substitution in the per-vertex containment system (mod 2^64)."""
+    N = noninduced_per_vertex(n, src, dst).astype(object)
+    out = np.zeros((n, 11), np.uint64)
+    for v in range(n):
+        o = [0] * 11
+        for i in range(10, -1, -1):
+            o[i] = int(N[v, i]) - sum(int(CONTAINMENT[i, j]) * o[j] for j in range(i + 1, 11))
+        out[v] = [x % (1 << 64) for x in o]
     return out

@@ -150,3 +150,41 @@ def test_each_motif_graph_alone(name):
     want = expect(4, {perm[v]: {r: 1} for v, r in roles.items()})
     for f in (R.orbits4_brute, R.orbits4_esu):
         assert np.array_equal(f(4, s, d), want)
+
+
+def test_containment_system_is_unit_upper_triangular():
+    M = R.CONTAINMENT
+    assert M.shape == (11, 11)
+    assert np.array_equal(np.diag(M), np.ones(11, np.int64))
+    assert not np.tril(M, -1).any()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_per_vertex_closure_equals_the_definition(seed):
+    """Eleven non-induced statistics per vertex and the containment inversion give every orbit count
+    exactly (random graphs of varied density, including isolated vertices and pendant paths)."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(6, 16))
+    p = float(rng.uniform(0.1, 0.85))
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+    s = np.array([a for a, _ in pairs], np.int32)
+    d = np.array([b for _, b in pairs], np.int32)
+    assert np.array_equal(R.orbits4_combo(n, s, d), R.orbits4_brute(n, s, d))
+
+
+@pytest.mark.parametrize("name,make", [("ba", lambda: graphgen.ba(150, 4, 5)), ("rgg", lambda: graphgen.rgg(150, 7.0, 6)),
+                                       ("rmat", lambda: graphgen.rmat(7, 8, seed=4))])
+def test_per_vertex_closure_on_larger_graphs(name, make):
+    g = make()
+    assert np.array_equal(R.orbits4_combo(g.n, g.src, g.dst), R.orbits4_esu(g.n, g.src, g.dst))
+
+
+def test_containment_rows_from_the_motif_graphs():
+    """Each motif graph alone: the non-induced statistics of each vertex are the containment column
+    of its role (the matrix read off the six drawings, independently of the inversion)."""
+    for name, (pairs, roles) in MOTIF_GRAPHS.items():
+        s = np.array([a for a, _ in pairs], np.int32)
+        d = np.array([b for _, b in pairs], np.int32)
+        N = R.noninduced_per_vertex(4, s, d)
+        for v, role in roles.items():
+            assert N[v].tolist() == R.CONTAINMENT[:, IDX[role]].tolist(), (name, v, role)
