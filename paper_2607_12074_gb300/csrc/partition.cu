@@ -234,10 +234,11 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     }
     const int64_t A = bstart[(size_t)nb];
     buf<uint64_t> pairs;  // (row << 32) | column, in bucket order; later the regrouping scratch
-    buf<int32_t> cu, c0;  // rows by id: unsorted with duplicates, then sorted without
+    // The rows, in one buffer throughout (each regrouping reads its input rows before it places a
+    // value): by id unsorted with duplicates, by id sorted without, relabelled, then by rank.
+    buf<int32_t> c0;
     try {
         pairs.resize((size_t)(A > 0 ? A : 1));
-        cu.resize((size_t)(A > 0 ? A : 1));
         c0.resize((size_t)(A > 0 ? A : 1));
     } catch (...) {
         return HARP_ENOMEM;
@@ -272,7 +273,7 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
             for (int64_t r = r0; r < r1; ++r) off0[(size_t)r] = bstart[(size_t)k] + pos[(size_t)(r - r0)];
             for (int64_t i = bstart[(size_t)k]; i < bstart[(size_t)k + 1]; ++i) {
                 const uint64_t pr = pairs[(size_t)i];
-                cu[(size_t)(bstart[(size_t)k] + pos[(size_t)((int64_t)(pr >> 32) - r0)]++)] = (int32_t)(uint32_t)pr;
+                c0[(size_t)(bstart[(size_t)k] + pos[(size_t)((int64_t)(pr >> 32) - r0)]++)] = (int32_t)(uint32_t)pr;
             }
         }
     });
@@ -280,10 +281,9 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     // rows sorted by id, duplicates dropped: row v keeps deg0[v] entries from off0[v]
     std::vector<int32_t> deg0((size_t)n, 0);
     regroup_by_destination(
-        n, [&](int64_t u) { return std::make_pair(cu.data() + off0[(size_t)u], cu.data() + off0[(size_t)u + 1]); },
+        n, [&](int64_t u) { return std::make_pair(c0.data() + off0[(size_t)u], c0.data() + off0[(size_t)u + 1]); },
         [](int32_t v) { return (int64_t)v; }, n, off0.data(), c0.data(), pairs.data(), true, deg0.data(),
         [](int64_t, int64_t) {});
-    buf<int32_t>().swap(cu);
     // rank = (degree, id): counting sort by degree, ids ascending inside a degree
     int32_t maxd = 0;
     for (int32_t d : deg0) maxd = d > maxd ? d : maxd;
@@ -302,11 +302,6 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     g.m = g.off[(size_t)n] / 2;
     g.deg.resize((size_t)n);
     g.dplus.resize((size_t)n);
-    try {
-        g.cols.resize((size_t)g.off[(size_t)n]);
-    } catch (...) {
-        return HARP_ENOMEM;
-    }
     // rows by rank, sorted: the other endpoints relabelled in place (one gather each), then vertices
     // visited in rank order
     parallel_dynamic(n, 4096, [&](int64_t lo, int64_t hi) {
@@ -320,18 +315,18 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
             const int32_t v = order[(size_t)r];
             return std::make_pair(c0.data() + off0[(size_t)v], c0.data() + off0[(size_t)v] + deg0[(size_t)v]);
         },
-        [](int32_t c) { return (int64_t)c; }, n, g.off.data(), g.cols.data(), pairs.data(), false, nullptr,
+        [](int32_t c) { return (int64_t)c; }, n, g.off.data(), c0.data(), pairs.data(), false, nullptr,
         [&](int64_t r0, int64_t r1) {  // degree and out-degree (entries above r) of the rows just filled
             for (int64_t r = r0; r < r1; ++r) {
                 const int64_t a = g.off[(size_t)r], z = g.off[(size_t)r + 1];
                 g.deg[(size_t)r] = (int32_t)(z - a);
-                const int64_t split =
-                    std::upper_bound(g.cols.begin() + a, g.cols.begin() + z, (int32_t)r) - (g.cols.begin() + a);
+                const int64_t split = std::upper_bound(c0.begin() + a, c0.begin() + z, (int32_t)r) - (c0.begin() + a);
                 g.dplus[(size_t)r] = (int32_t)(z - a - split);
             }
         });
-    buf<int32_t>().swap(c0);
     buf<uint64_t>().swap(pairs);
+    c0.resize((size_t)g.off[(size_t)n]);
+    g.cols.swap(c0);
     g.rank.swap(rank);
     g.offp.assign((size_t)n + 1, 0);
     g.n1 = n;
