@@ -31,9 +31,11 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -65,9 +67,20 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples: kept in HARP_CLOCKS_DIR when it is set, else a temporary file (the JSON line
+        # carries the summary)
+        keep = os.environ.get("HARP_CLOCKS_DIR")
+        self.keep = bool(keep)
+        self.path = None
+        if keep:
+            self.path = os.path.join(keep, f"clocks_bench_{os.getpid()}.csv")
+        elif shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(prefix="harp_clocks_", suffix=".csv")
+            os.close(fd)
 
     def __enter__(self):
+        if self.path is None:
+            return self
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -89,6 +102,8 @@ class ClockSampler:
 
     def summary(self):
         if not self.proc:
+            if not self.keep and self.path and os.path.exists(self.path):
+                os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
         with open(self.path) as f:
@@ -96,6 +111,8 @@ class ClockSampler:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) >= 9:
                     rows.append(parts)
+        if not self.keep:
+            os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

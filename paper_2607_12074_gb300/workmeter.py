@@ -2,9 +2,9 @@
 
 "Algorithmic bytes" are the bytes an ideal implementation of each step must move between the SMs
 and memory (every needed list element, offset and statistic read or written once), independent of
-how many of them the L2 serves.  They are the numerators of the roofline figures; the same per-unit
-figures are stated in the design doc.  This module is plain numpy on the host and is not on the counting
-path (bench.py uses it to turn kernel times into bandwidth).
+how many of them the L2 serves.  They are the numerators of the roofline figures (per unit below).
+This module is plain numpy on the host and is not on the counting path (bench.py uses it to turn
+kernel times into bandwidth).
 
 Per unit (int32 ids and counters = 4 B, int64 offsets = 8 B):
   orientation   read offsets + cols + perm gather, write relabelled cols and offsets, out-CSR copy:
