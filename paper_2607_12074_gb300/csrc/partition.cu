@@ -107,14 +107,14 @@ void parallel_dynamic(int64_t n, int64_t chunk, F&& f) {
 // source i goes to destination row dest(c) with value i, so every destination row receives its
 // values in increasing order (sorted rows without a sort).  out_off[0 .. n_dest] are the destination
 // rows' offsets; because the arcs are symmetric they are also the prefix of the sources' entry counts
-// in visit order, which balances the sources over the host threads.  With dedup, a value equal to the
-// one placed before it in its row is dropped and kept[d] receives the number placed in row d (rows
-// keep their full extent, the tail unused).  scratch holds out_off[n_dest] packed (row, value) pairs.
+// in visit order, which balances the sources over the host threads.  scratch holds out_off[n_dest]
+// packed (row, value) pairs.  Every source row is read before the first value is placed, so `out`
+// may be the buffer the source rows live in.
 // done(d0, d1) runs on destination rows [d0, d1) right after they are filled (while they are in cache).
 constexpr int64_t kRegroupBuckets = 4096;
 template <typename RowOf, typename DestOf, typename Done>
 void regroup_by_destination(int64_t N, RowOf row, DestOf dest, int64_t n_dest, const int64_t* out_off, int32_t* out,
-                            uint64_t* scratch, bool dedup, int32_t* kept, Done&& done) {
+                            uint64_t* scratch, Done&& done) {
     int sh = 0;  // destination bucket: d >> sh, about kRegroupBuckets buckets
     while ((n_dest >> sh) > kRegroupBuckets) ++sh;
     const int64_t nb = (n_dest >> sh) + 1;
@@ -171,24 +171,18 @@ void regroup_by_destination(int64_t N, RowOf row, DestOf dest, int64_t n_dest, c
             for (int64_t e = bstart[(size_t)k]; e < bstart[(size_t)k + 1]; ++e) {
                 const uint64_t pr = scratch[(size_t)e];
                 const int64_t d = (int64_t)(pr >> 32);
-                const int32_t v = (int32_t)(uint32_t)pr;
-                int64_t& at = pos[(size_t)(d - d0)];
-                if (dedup && at > out_off[d] && out[at - 1] == v) continue;
-                out[at++] = v;
+                out[pos[(size_t)(d - d0)]++] = (int32_t)(uint32_t)pr;
             }
-            if (kept)
-                for (int64_t d = d0; d < d1; ++d) kept[d] = (int32_t)(pos[(size_t)(d - d0)] - out_off[d]);
             done(d0, d1);
         }
     });
 }
 
 // The rank-order CSR without atomics and without sorting rows: arcs are partitioned by source-id
-// bucket (per-thread histograms and thread-private cursors) and each bucket is turned into its rows
-// (unsorted); regrouping those rows by their other endpoint, visited in id order, sorts every row by
-// id and puts duplicates side by side, where they are dropped; the rank order (degree, id) is a
-// counting sort by degree; regrouping once more, visiting vertices in rank order and relabelling the
-// other endpoint, gives rows sorted by rank.
+// bucket (per-thread histograms and thread-private cursors), each bucket is turned into its rows and
+// each row's duplicates are dropped through a hash table; the rank order (degree, id) is a counting
+// sort by degree; regrouping the rows by their other endpoint, relabelled, with vertices visited in
+// rank order, gives rows sorted by rank.
 harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const int32_t* dst, RankGraph& g) {
     int sh = 0;  // bucket of a vertex: v >> sh, about 1024 buckets
     while ((n >> sh) > 1024) ++sh;
@@ -234,8 +228,8 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
     }
     const int64_t A = bstart[(size_t)nb];
     buf<uint64_t> pairs;  // (row << 32) | column, in bucket order; later the regrouping scratch
-    // The rows, in one buffer throughout (each regrouping reads its input rows before it places a
-    // value): by id unsorted with duplicates, by id sorted without, relabelled, then by rank.
+    // The rows, in one buffer throughout: by id with duplicates, by id without, relabelled, then by
+    // rank (the regrouping reads its input rows before it places a value).
     buf<int32_t> c0;
     try {
         pairs.resize((size_t)(A > 0 ? A : 1));
@@ -260,9 +254,13 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
         for (auto& x : th) x.join();
     }
     std::vector<std::vector<int64_t>>().swap(hist);
-    // each bucket into its rows (positions of the id-order CSR are the bucket's own range)
+    // each bucket into its rows (positions of the id-order CSR are the bucket's own range), then each
+    // row's duplicates dropped in place through a small hash table (stamped by row, so it is never
+    // cleared): row v keeps deg0[v] entries from off0[v], in first-seen order
     std::vector<int64_t> off0((size_t)n + 1, 0);
+    std::vector<int32_t> deg0((size_t)n, 0);
     parallel_dynamic(nb, 1, [&](int64_t k0, int64_t k1) {
+        thread_local std::vector<uint64_t> table;
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t r0 = k << sh, r1 = std::min<int64_t>((k + 1) << sh, n);
             if (r0 >= r1) continue;
@@ -275,15 +273,36 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
                 const uint64_t pr = pairs[(size_t)i];
                 c0[(size_t)(bstart[(size_t)k] + pos[(size_t)((int64_t)(pr >> 32) - r0)]++)] = (int32_t)(uint32_t)pr;
             }
+            for (int64_t r = r0; r < r1; ++r) {  // after the scatter pos[r - r0] is the end of row r
+                const int64_t beg = off0[(size_t)r], end = bstart[(size_t)k] + pos[(size_t)(r - r0)];
+                if (end - beg <= 1) {
+                    deg0[(size_t)r] = (int32_t)(end - beg);
+                    continue;
+                }
+                int lg = 1;
+                while (((int64_t)1 << lg) < 2 * (end - beg)) ++lg;
+                if (table.size() < ((size_t)1 << lg)) table.assign((size_t)1 << lg, 0);  // stamp 0: empty
+                const uint64_t stamp = (uint64_t)(r + 1) << 32, mask = ((uint64_t)1 << lg) - 1;
+                int64_t w = beg;
+                for (int64_t i = beg; i < end; ++i) {
+                    const uint32_t v = (uint32_t)c0[(size_t)i];
+                    uint64_t h = ((uint64_t)v * 0x9E3779B97F4A7C15ull) >> (64 - lg);
+                    for (;;) {
+                        const uint64_t e = table[(size_t)h];
+                        if ((e & ~0xffffffffull) != stamp) {  // a slot of another row: free here
+                            table[(size_t)h] = stamp | v;
+                            c0[(size_t)w++] = (int32_t)v;
+                            break;
+                        }
+                        if ((uint32_t)e == v) break;  // a duplicate
+                        h = (h + 1) & mask;
+                    }
+                }
+                deg0[(size_t)r] = (int32_t)(w - beg);
+            }
         }
     });
     off0[(size_t)n] = A;
-    // rows sorted by id, duplicates dropped: row v keeps deg0[v] entries from off0[v]
-    std::vector<int32_t> deg0((size_t)n, 0);
-    regroup_by_destination(
-        n, [&](int64_t u) { return std::make_pair(c0.data() + off0[(size_t)u], c0.data() + off0[(size_t)u + 1]); },
-        [](int32_t v) { return (int64_t)v; }, n, off0.data(), c0.data(), pairs.data(), true, deg0.data(),
-        [](int64_t, int64_t) {});
     // rank = (degree, id): counting sort by degree, ids ascending inside a degree
     int32_t maxd = 0;
     for (int32_t d : deg0) maxd = d > maxd ? d : maxd;
@@ -315,7 +334,7 @@ harp_status build_rank_graph(int64_t n, int64_t m_in, const int32_t* src, const 
             const int32_t v = order[(size_t)r];
             return std::make_pair(c0.data() + off0[(size_t)v], c0.data() + off0[(size_t)v] + deg0[(size_t)v]);
         },
-        [](int32_t c) { return (int64_t)c; }, n, g.off.data(), c0.data(), pairs.data(), false, nullptr,
+        [](int32_t c) { return (int64_t)c; }, n, g.off.data(), c0.data(), pairs.data(),
         [&](int64_t r0, int64_t r1) {  // degree and out-degree (entries above r) of the rows just filled
             for (int64_t r = r0; r < r1; ++r) {
                 const int64_t a = g.off[(size_t)r], z = g.off[(size_t)r + 1];

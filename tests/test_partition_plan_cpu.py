@@ -170,12 +170,18 @@ def _messy_graph(n, m, seed):
     return s.astype(np.int32), d.astype(np.int32)
 
 
-@pytest.mark.parametrize("case", ["messy_small", "messy_mid", "ba", "chung_lu", "rmat", "empty", "edgeless"])
+@pytest.mark.parametrize("case", ["messy_small", "messy_mid", "messy_dense", "hub_repeats", "ba", "chung_lu", "rmat",
+                                  "empty", "edgeless"])
 def test_host_rank_graph_is_the_definition(lib, case):
     if case == "messy_small":
         n, (s, d) = 50, _messy_graph(50, 300, 1)
     elif case == "messy_mid":
         n, (s, d) = 30_000, _messy_graph(30_000, 400_000, 2)
+    elif case == "messy_dense":  # about 400 repeats per simple edge
+        n, (s, d) = 300, _messy_graph(300, 2_000_000, 3)
+    elif case == "hub_repeats":  # one row of 300,000 arcs with 1,000 distinct neighbours, both orientations
+        x = (np.arange(300_000, dtype=np.int32) % 1000 + 1).astype(np.int32)
+        n, s, d = 1001, np.concatenate([np.zeros_like(x), x]), np.concatenate([x, np.zeros_like(x)])
     elif case == "empty":
         n, s, d = 0, np.zeros(0, np.int32), np.zeros(0, np.int32)
     elif case == "edgeless":
