@@ -23,6 +23,10 @@ the degrees of its two endpoints inside G[S]:
 edge is in orbit o; edges are numbered as :func:`edge_list` returns them.  Summed over edges, orbit o
 gives its motif's count times its number of edges (the last column).
 
+Functions: :func:`edge_orbits4_brute` (every 4-subset), :func:`edge_orbits4_esu` (each connected 4-set
+once) and :func:`edge_orbits4_combo` (ten non-induced statistics per edge and a unit upper-triangular
+containment inversion).
+
 Parity status: pinned in ``tests/test_oracle_edge_orbits.py`` (each motif graph alone, closed forms of
 complete, star, cycle, path and complete bipartite graphs, ESU against brute force, edge-orbit sums
 against the C oracle's global counts, and the vertex orbits of ``oracle.orbits``); nothing is pinned
@@ -136,4 +140,79 @@ def edge_orbits4_esu(n, src, dst):
 
     for v in range(n):
         extend([v], [y for y in adj[v] if y > v], v)
+    return out
+
+
+# ---------------------------------------------------------------------------------------------------
+# Per-edge closure: ten non-induced statistics per edge e = (a, b) and their containment system.
+# ---------------------------------------------------------------------------------------------------
+# E[i] counts (not necessarily induced) copies of a pattern that contain e in role i; an induced
+# occurrence S containing e contributes the number of such copies inside G[S].  Row i gives that
+# number for each edge orbit (columns in EDGE_ORBITS order); the matrix is unit upper triangular.
+#   E0  stars containing e                           C(d_a - 1, 2) + C(d_b - 1, 2)
+#   E1  3-edge paths with e at an end                sum over the two orientations (a end, b inner) of
+#                                                    sum_{c in N(b), c != a} (d_c - 1) - t_ab
+#   E2  3-edge paths with e in the middle            (d_a - 1)(d_b - 1) - t_ab
+#   E3  paws with e the pendant edge                 (t_a - t_ab) + (t_b - t_ab)
+#   E4  paws with e a triangle edge at the hub       t_ab (d_a + d_b - 4)
+#   E5  paws with e the triangle edge facing the hub sum_{h in N(a) n N(b)} (d_h - 2)
+#   E6  4-cycles through e                           sum_{x in N(a), x != b} (|N(x) n N(b)| - 1)
+#   E7  diamonds with e the shared edge              C(t_ab, 2)
+#   E8  diamonds with e an outer edge                sum_{s in N(a) n N(b)} (t_as - 1) + (t_bs - 1)
+#   E9  4-cliques through e                          edges of G[N(a) n N(b)]
+# with t_e = triangles on edge e and t_v = triangles on vertex v.
+EDGE_CONTAINMENT = np.array([
+    # o0 o1 o2 o3 o4 o5 o6 o7 o8 o9
+    [1, 0, 0, 1, 1, 0, 0, 2, 1, 2],   # E0: endpoints of e of degree 3 in G[S]
+    [0, 1, 0, 2, 0, 2, 2, 0, 3, 4],   # E1: Hamiltonian paths of G[S] ending with e
+    [0, 0, 1, 0, 1, 0, 1, 2, 1, 2],   # E2: Hamiltonian paths of G[S] with e in the middle
+    [0, 0, 0, 1, 0, 0, 0, 0, 1, 2],   # E3
+    [0, 0, 0, 0, 1, 0, 0, 4, 1, 4],   # E4
+    [0, 0, 0, 0, 0, 1, 0, 0, 1, 2],   # E5
+    [0, 0, 0, 0, 0, 0, 1, 0, 1, 2],   # E6
+    [0, 0, 0, 0, 0, 0, 0, 1, 0, 1],   # E7
+    [0, 0, 0, 0, 0, 0, 0, 0, 1, 4],   # E8
+    [0, 0, 0, 0, 0, 0, 0, 0, 0, 1],   # E9
+], dtype=np.int64)
+
+
+def noninduced_per_edge(n, src, dst):
+    """The ten statistics E0..E9 of every edge (in edge_list order), by plain loops."""
+    edges = edge_list(n, src, dst)
+    adj = _adjacency(n, edges)
+    deg = [len(x) for x in adj]
+    t = {e: len(adj[e[0]] & adj[e[1]]) for e in edges}
+
+    def te(x, y):
+        return t[(x, y) if x < y else (y, x)]
+
+    t_v = [sum(te(v, h) for h in adj[v]) // 2 for v in range(n)]
+    out = np.zeros((len(edges), 10), np.uint64)
+    for k, (a, b) in enumerate(edges):
+        common = adj[a] & adj[b]
+        tab = len(common)
+        E = [0] * 10
+        E[0] = (deg[a] - 1) * (deg[a] - 2) // 2 + (deg[b] - 1) * (deg[b] - 2) // 2
+        E[1] = sum(sum(deg[c] - 1 for c in adj[y] if c != x) - tab for x, y in ((a, b), (b, a)))
+        E[2] = (deg[a] - 1) * (deg[b] - 1) - tab
+        E[3] = (t_v[a] - tab) + (t_v[b] - tab)
+        E[4] = tab * (deg[a] + deg[b] - 4)
+        E[5] = sum(deg[h] - 2 for h in common)
+        E[6] = sum(len(adj[x] & adj[b]) - 1 for x in adj[a] if x != b)
+        E[7] = tab * (tab - 1) // 2
+        E[8] = sum((te(a, s) - 1) + (te(b, s) - 1) for s in common)
+        E[9] = sum(1 for x in common for y in common if x < y and y in adj[x])
+        out[k] = E
+    return out
+
+
+def edge_orbits4_combo(n, src, dst):
+    """Edge-orbit counts by back-substitution in the per-edge containment system (mod 2^64)."""
+    N = noninduced_per_edge(n, src, dst)
+    out = np.zeros(N.shape, np.uint64)
+    for k in range(N.shape[0]):
+        o = [0] * 10
+        for i in range(9, -1, -1):
+            o[i] = int(N[k, i]) - sum(int(EDGE_CONTAINMENT[i, j]) * o[j] for j in range(i + 1, 10))
+        out[k] = [x % (1 << 64) for x in o]
     return out

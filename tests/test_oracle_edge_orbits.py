@@ -148,3 +148,38 @@ def test_edgeless_and_bad_ids():
     assert E.edge_orbits4_esu(6, e, e).shape == (0, 10)
     with pytest.raises(ValueError):
         E.edge_orbits4_brute(3, np.array([0], np.int32), np.array([5], np.int32))
+
+
+def test_edge_containment_is_unit_upper_triangular():
+    M = E.EDGE_CONTAINMENT
+    assert M.shape == (10, 10)
+    assert np.array_equal(np.diag(M), np.ones(10, np.int64))
+    assert not np.tril(M, -1).any()
+
+
+def test_edge_containment_columns_from_the_motif_graphs():
+    """Each motif graph alone: each edge's non-induced statistics are the column of its class."""
+    for name, roles in MOTIF_GRAPHS.items():
+        s = np.array([a for a, _ in roles], np.int32)
+        d = np.array([b for _, b in roles], np.int32)
+        N = E.noninduced_per_edge(4, s, d)
+        for k, e in enumerate(E.edge_list(4, s, d)):
+            assert N[k].tolist() == E.EDGE_CONTAINMENT[:, IDX[roles[e]]].tolist(), (name, e, roles[e])
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_per_edge_closure_equals_the_definition(seed):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(6, 15))
+    p = float(rng.uniform(0.1, 0.85))
+    pairs = [(x, y) for x in range(n) for y in range(x + 1, n) if rng.random() < p]
+    s = np.array([x for x, _ in pairs], np.int32)
+    d = np.array([y for _, y in pairs], np.int32)
+    assert np.array_equal(E.edge_orbits4_combo(n, s, d), E.edge_orbits4_brute(n, s, d))
+
+
+@pytest.mark.parametrize("name,make", [("ba", lambda: graphgen.ba(150, 4, 5)), ("rgg", lambda: graphgen.rgg(150, 7.0, 6)),
+                                       ("rmat", lambda: graphgen.rmat(7, 8, seed=4))])
+def test_per_edge_closure_on_larger_graphs(name, make):
+    g = make()
+    assert np.array_equal(E.edge_orbits4_combo(g.n, g.src, g.dst), E.edge_orbits4_esu(g.n, g.src, g.dst))
