@@ -12,6 +12,9 @@ order [3-star, 4-path, tailed triangle, 4-cycle, diamond, 4-clique]):
 * :func:`count4_literal` - the closure equations of Section III-F taken literally.
 * :func:`count4_combo`   - plain non-induced counts (:func:`noninduced`) and the containment inversion.
 
+Submodules (plain Python, pinned in their own tests): ``oracle.orbits`` (per-vertex orbit counts),
+``oracle.edge_orbits`` (per-edge orbit counts) and ``oracle.motifs5`` (connected 5-vertex motifs).
+
 Parity status: every function is pinned in ``tests/test_oracle_*.py`` against closed forms, brute force
 and exact integer matrix identities; the paper prints no motif count, so nothing is pinned to a value
 printed in the paper itself.
