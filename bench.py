@@ -9,7 +9,8 @@ reduction and closure, counts copied to the host.  L2 is flushed (256 MiB write)
 `value` = m / (device time per step).  `e2e` = the same metric through the public API from pinned
 host edge lists: harp_build_csr (H2D + device CSR build) + harp_count4 (D2H of the counts) per step.
 `roofline` = the dominant kernel's algorithmic bytes (host work meter) / its CUDA-event time, against
-the measured HBM copy bandwidth.  `cpu_baseline` = the CPU oracle on a bounded R-MAT sample.
+the measured HBM copy bandwidth (`segment_rooflines`: the same for every segment).  `cpu_baseline` =
+the CPU oracle (OpenMP, all host cores) on the bench graph itself.
 
 `batched`: the batched workload (4,096 graphs: ER / BA / RGG, n log-uniform in [50, 20000], mean degree
 in [4, 32], seeds 0..4095) counted as one captured CUDA graph under the autotuned plan, against the plain
@@ -123,17 +124,42 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample_rate(scale: int, threads: int = 0):
-    """Time the CPU oracle on an R-MAT sample in a fresh process (OpenMP on all host cores)."""
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu on Arm, /proc/cpuinfo on x86), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample_rate(scale: int, threads: int = 0, counts: bool = False):
+    """Time the CPU oracle on an R-MAT graph of the bench family in a fresh process (OpenMP on all
+    host cores).  counts=True also returns the oracle's counts (as a check against the GPU's)."""
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
         "import graphgen, oracle, os\n"
         "g = graphgen.rmat(%d, 16, 0.57, 0.19, 0.19, seed=1)\n"
         "m, _ = oracle.graph_summary(g.n, g.src, g.dst)\n"
         "t = time.perf_counter(); c = oracle.count4_combo(g.n, g.src, g.dst, %d); t = time.perf_counter() - t\n"
-        "print(json.dumps({'m': m, 'seconds': t, 'cores': os.cpu_count()}))\n" % (ROOT, scale, threads))
+        "print(json.dumps({'m': m, 'seconds': t, 'cores': os.cpu_count(), 'counts': [int(x) for x in c]}))\n"
+        % (ROOT, scale, threads))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    if not counts:
+        r.pop("counts", None)
+    return r
 
 
 def max_over_ranks(value: float, world: int, device: str) -> float:
@@ -508,8 +534,21 @@ def main():
     seg_avg = {k: (sum(v) / len(v) if v else 0.0) for k, v in seg_ms.items()}
     roofline = None
     meter = None
+    segment_rooflines = None
     if not args.no_meter:
         meter = workmeter.meter(g.n, g.src, g.dst)
+        # every segment against the HBM roofline: its algorithmic bytes (work meter) over its CUDA-event
+        # time; the windowed wedge kernel's per-window re-reads are listed apart as overhead
+        segment_rooflines = {}
+        for k in SEGMENTS:
+            t_ms = seg_avg[k]
+            alg_k = meter[k]["bytes"] if k in meter else 0
+            if t_ms <= 0 or alg_k <= 0:
+                continue
+            ach = alg_k / (t_ms / 1000) / 1e9
+            segment_rooflines[k] = {"ms": t_ms, "algorithmic_bytes": alg_k, "achieved_gbs": ach, "frac": ach / peak}
+            if meter[k].get("overhead_bytes"):
+                segment_rooflines[k]["overhead_bytes"] = meter[k]["overhead_bytes"]
         kernel_segments = [k for k in SEGMENTS if k != "orient"]
         dom = max(kernel_segments, key=lambda k: seg_avg[k])
         alg = meter[dom]["bytes"]
@@ -527,13 +566,18 @@ def main():
                         traffic = rec[dom]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                    "algorithmic_bytes": alg, "kernel_ms": seg_avg[dom]}
+                    "algorithmic_bytes": alg, "kernel_ms": seg_avg[dom],
+                    "overhead_bytes": meter[dom].get("overhead_bytes", 0)}
     cpu = None
     if not args.no_cpu_baseline:
-        r = oracle_sample_rate(18)
+        # the oracle on the bench graph itself (R-MAT scale 20, the same generator call), all host cores
+        r = oracle_sample_rate(args.scale, counts=True)
         cpu = {"value": r["m"] / r["seconds"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-               "sample": f"R-MAT scale 18 (same a,b,c, ef 16, seed 1; m={r['m']}), oracle count4_combo, "
-                         f"{r['seconds']:.1f} s"}
+               "cpu_model": host_cpu_model(),
+               "sample": f"the whole bench graph: R-MAT scale {args.scale} (a,b,c = 0.57,0.19,0.19, ef 16, "
+                         f"seed 1; m={r['m']}), oracle count4_combo (non-induced counts + inversion, OpenMP), "
+                         f"one run of {r['seconds']:.1f} s",
+               "counts_equal_gpu": [int(x) for x in counts] == r["counts"]}
     value = replica_throughput(m, world, t_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -546,6 +590,7 @@ def main():
         "e2e": {"value": world * m / (t_e2e / 1000), "unit": UNIT, "h2d_bytes_per_step": 8 * g.m_in,
                 "d2h_bytes_per_step": 72, "ms_per_step": t_e2e},
         "roofline": roofline,
+        "segment_rooflines": segment_rooflines,
         "cpu_baseline": cpu,
         "gpu_launches": launches,
         "clocks": clocks.summary(),

@@ -171,8 +171,10 @@ harp_status harp_count4_stats(const harp_csr* g, const harp_plan* plan, uint64_t
                               uint64_t stats_out[8]);
 
 /* Asynchronous form: enqueue the whole count on `stream` and return.  d_out is DEVICE memory of at
- * least 16 uint64: [0..5] the counts, [6..7] reserved, [8..15] the statistics.  It is written when
- * the stream reaches that point.  The handle's workspace is in use until then: do not start
+ * least 16 uint64: [0..5] the counts, [6] the device self-check word (0 = fine; nonzero = a kernel's
+ * consistency check fired and the counts are not valid, the case in which the blocking calls return
+ * HARP_EDEVICE), [7] reserved, [8..15] the statistics.  It is written when the stream reaches that
+ * point.  The handle's workspace is in use until then: do not start
  * another count on the same handle on a different stream before it completes. */
 harp_status harp_count4_async(const harp_csr* g, const harp_plan* plan, uint64_t* d_out, void* stream);
 
@@ -357,16 +359,24 @@ void harp_server_destroy(harp_server* srv);
  *
  * harp_count4_noalloc counts the six induced motifs of a caller-owned, device-resident CSR:
  *   n, m       vertices and undirected simple edges; n <= 262,144 and m <= 524,288, larger sizes
- *              return HARP_ENOMEM (they do not fit the fixed scratch)
+ *              return HARP_ENOMEM (they do not fit the fixed scratch).  m must equal
+ *              d_offsets[n] / 2.
  *   d_offsets  device int64[n+1], d_cols device int32[2m]: a symmetric CSR with every row sorted
  *              ascending, no self-loops, no duplicates (e.g. the arrays of harp_csr_arrays);
- *              read only.  A malformed CSR gives undefined results.
- *   d_out      device uint64[16]: [0..5] counts, [8..15] statistics (HARP_STAT_* order), written
- *              when `stream` reaches the end of the work
+ *              read only.  The device checks d_offsets[0] = 0, d_offsets[n] = 2m, non-decreasing
+ *              offsets with degrees <= n - 1 and column ids in [0, n) before anything else; a CSR
+ *              that fails is counted as edgeless and d_out[6] is nonzero.  Self-loops, duplicates
+ *              or an asymmetric CSR pass that check and give wrong counts.
+ *   d_out      device uint64[16]: [0..5] counts, [6] the device self-check word (0 = fine; nonzero =
+ *              the CSR check or a kernel's consistency check fired and the counts are not valid),
+ *              [7] reserved, [8..15] statistics (HARP_STAT_* order), written when `stream` reaches
+ *              the end of the work
  *   stream     cudaStream_t; the call only enqueues work and returns
  * Scratch lives in one file-scope static device array of 64 MiB that every GPU used by the process
  * holds until exit.  The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream capture.  All calls
+ * device, with the device current) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point again on a device after a
+ * cudaDeviceReset of it.  All calls
  * share the array and clear what must start at zero themselves: calls whose work overlaps on the
  * GPU (different streams or threads) race on it, so serialise them.  No cudaMalloc, cudaFree or
  * allocating library routine is called. */

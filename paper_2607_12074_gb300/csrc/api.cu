@@ -27,6 +27,17 @@ void record_cuda_error(cudaError_t e) {
 }
 void note_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+int num_sms() {
+    static std::atomic<int> cached[64];  // 0 = not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
+    cached[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 cudaError_t prof_mark(cudaStream_t s, int seg) {
     if (!g_profiling.load(std::memory_order_relaxed) || !t_marks[0]) return cudaSuccess;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -289,6 +300,7 @@ harp_status harp_count4_async(const harp_csr* gc, const harp_plan* plan, uint64_
     HARP_CK(cudaSetDevice(g->device));
     HARP_TRY(enqueue_count(g, plan, s));
     HARP_CK(cudaMemcpyAsync(d_out, g->ws.acc, 16 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    HARP_CK(cudaMemcpyAsync(d_out + OUT_ERR, g->ws.acc + ACC_ERR, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     return HARP_OK;
 }
 

@@ -633,11 +633,11 @@ __device__ __forceinline__ void window_pass(const int64_t* __restrict__ off, con
             else if (table) p1 = gallop_i32(cols + wb, p0 < 0 ? 0 : p0, rowlen, xhi);
             else p1 = lower_bound_i32(cols + wb, rowlen, xhi);
             if (p0 < 0 || p1 > rowlen) {
-                flag_error(acc, 2ull);
+                flag_error(acc, kErrRow);
                 p0 = p1 = 0;
             }
             if (p1 > p0 && (cols[wb + p0] < xlo || cols[wb + p1 - 1] >= xhi)) {
-                flag_error(acc, 1ull);
+                flag_error(acc, kErrSegment);
                 p1 = p0;
             }
             base = wb + p0;
@@ -822,6 +822,7 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool
     const int64_t n = g->n;
     const int64_t G = ws.G > 0 ? ws.G : 1;
     const Sink sink{ws.acc, ws.gid, ws.accG};
+    const int sms = num_sms();
     int32_t* wcount = ws.q_win + n;
     HARP_CK(cudaMemsetAsync(wcount, 0, (size_t)n * sizeof(int32_t), s));
     k_c4_ginfo<WORDS><<<grid_cap(G * 32, 128, 1024), 128, 0, s>>>(ws.deg, n, ws.gbase, G, ws.x_lo, ws.x_hi, merge,
@@ -833,24 +834,24 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool
     const int32_t* lcols = lists ? ws.lcols : ws.cols;
     if (lists) {
         const int64_t la = ws.lower_arcs;  // == loff[n]
-        k_c4_rev<true><<<grid_cap((la + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
+        k_c4_rev<true><<<grid_cap((la + kRevRun - 1) / kRevRun, 256, (int64_t)sms * 64), 256, 0, s>>>(
             ws.loff, ws.lcols, ws.off, ws.cols, ws.deg, ws.dplus, n, la, ws.rev);
     } else {
         const int64_t arcs = ws.arcs >= 0 ? ws.arcs : 2 * g->m;  // must equal off[n]
-        k_c4_rev<false><<<grid_cap((arcs + kRevRun - 1) / kRevRun, 256, 152 * 64), 256, 0, s>>>(
+        k_c4_rev<false><<<grid_cap((arcs + kRevRun - 1) / kRevRun, 256, (int64_t)sms * 64), 256, 0, s>>>(
             ws.off, ws.cols, ws.offp, ws.colsp, ws.deg, ws.dplus, n, arcs, ws.rev);
     }
     HARP_LAUNCHED();
-    k_c4_bpos<WORDS><<<grid_cap(n * kGridCap, 256, 152 * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n,
+    k_c4_bpos<WORDS><<<grid_cap(n * kGridCap, 256, (int64_t)sms * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n,
                                                                              ws.fpos, ws.bpos);
     HARP_LAUNCHED();
-    k_c4_classify<WORDS><<<grid_cap(n * 32, 256, 152 * 32), 256, 0, s>>>(
+    k_c4_classify<WORDS><<<grid_cap(n * 32, 256, (int64_t)sms * 32), 256, 0, s>>>(
         loff, lcols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
         ws.q_mid, ws.q_win, wcount, ws.acc);
     HARP_LAUNCHED();
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
     HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
-    k_c4_small<<<152 * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus, ws.fpos,
+    k_c4_small<<<sms * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus, ws.fpos,
                                                           ws.rev, ws.q_mid,
                                                           n, ws.acc, sink);
     HARP_LAUNCHED();
@@ -859,7 +860,7 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
     const size_t win_smem = (size_t)WORDS * sizeof(uint32_t);
     HARP_CK(cudaFuncSetAttribute(k_c4_window<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
-    k_c4_window<MINB><<<152 * MINB, kWinThreads, win_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus,
+    k_c4_window<MINB><<<sms * MINB, kWinThreads, win_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus,
                                                                 ws.fpos, ws.rev,
                                                                 ws.bpos, ws.gid, ws.ginfo, ws.q_win, ws.win_prefix,
                                                                 ws.acc, sink);

@@ -86,7 +86,7 @@ __global__ void k_max_degree(const int64_t* __restrict__ off, int64_t n, unsigne
 unsigned grid_for(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > (int64_t)num_sms() * 32) b = (int64_t)num_sms() * 32;
     return (unsigned)b;
 }
 

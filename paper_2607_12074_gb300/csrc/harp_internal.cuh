@@ -15,6 +15,9 @@ namespace harp {
 
 void record_cuda_error(cudaError_t e);
 void note_launch(int64_t k = 1);   // counts kernel launches (harp_launch_count)
+// Streaming multiprocessors of the current device (queried once per device, then cached); every
+// persistent grid and per-block scratch is sized from it.
+int num_sms();
 // Profiling: records an event closing segment `seg` (0..HARP_NSEGMENTS-1) on stream s when enabled.
 enum : int { SEG_ORIENT = 0, SEG_TRI_WARP, SEG_TRI_CTA_S, SEG_TRI_CTA_L, SEG_TRI_FALLBACK, SEG_C4_SMALL,
              SEG_C4_MID, SEG_C4_WINDOW, SEG_REDUCE };
@@ -61,7 +64,7 @@ enum : int {
     ACC_PAWSUM = 21,       // sum over triangles of (d_a + d_b + d_c)
     ACC_D = 22,            // sum_e C(t_e, 2)
     ACC_M = 23,            // m
-    ACC_ERR = 24,          // device-side consistency flags (0 = fine)
+    ACC_ERR = 24,          // device-side consistency flags (0 = fine; kErr* bits)
     ACC_DONE = 25,         // last-block counter of the reduction kernel
     Q_TRI_WARP = 26,       // queue lengths
     Q_TRI_CTA = 27,
@@ -81,6 +84,14 @@ enum : int {
     T_TRI_BIG = 42,        // its ticket
     kOutLen = 48
 };
+
+// Bits of acc[ACC_ERR].  Any set bit makes a blocking count return HARP_EDEVICE; the asynchronous
+// entry points copy the word to d_out[OUT_ERR].
+constexpr uint64_t kErrSegment = 1;     // a wedge segment outside its window (skipped)
+constexpr uint64_t kErrRow = 2;         // a wedge segment outside its row (skipped)
+constexpr uint64_t kErrBadCsr = 256;    // a caller-built CSR failed its size/id check (nothing counted)
+constexpr uint64_t kErrLitDiv = 512;    // a literal-closure sum was not divisible by its divisor
+constexpr int OUT_ERR = 6;              // slot of d_out that receives acc[ACC_ERR]
 
 // Per-graph accumulator slots (batch mode), kGStride per graph.
 constexpr int kGStride = 8;

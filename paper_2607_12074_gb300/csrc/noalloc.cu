@@ -28,6 +28,45 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device
 
+// The caller's CSR must match the sizes it passes: off[0] = 0, off[n] = 2m, offsets non-decreasing
+// with every degree at most n - 1, and every column id in [0, n).  The offsets are checked first;
+// the columns are read only when the offsets passed (so no read goes past off[n] = 2m).  A failure
+// sets kErrBadCsr in acc[ACC_ERR]; the orientation pass then treats the graph as edgeless, so no
+// kernel indexes past the scratch laid out for (n, m).
+__global__ void k_check_offsets(const int64_t* __restrict__ off, int64_t n, int64_t m, uint64_t* __restrict__ acc) {
+    bool bad = false;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = off[v];
+        if (v == 0 && o != 0) bad = true;
+        if (v == n && o != 2 * m) bad = true;
+        if (v < n) {
+            const int64_t d = off[v + 1] - o;
+            if (d < 0 || d > n - 1) bad = true;
+        }
+    }
+    if (__any_sync(kFull, bad) && lane_id() == 0) atomicOr((unsigned long long*)&acc[ACC_ERR], (unsigned long long)kErrBadCsr);
+}
+
+__global__ void k_check_cols(const int32_t* __restrict__ cols, int64_t n, int64_t m, uint64_t* __restrict__ acc) {
+    // offsets failed: off[n] may not bound the columns.  Lane 0 reads the flag for its warp, so the
+    // warp leaves (or stays) as a whole even while other warps set the same bit.
+    const uint64_t flag = __shfl_sync(kFull, lane_id() == 0 ? acc[ACC_ERR] : 0ull, 0);
+    if (flag & kErrBadCsr) return;
+    bool bad = false;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < 2 * m; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cols[a];
+        if (c < 0 || (int64_t)c >= n) bad = true;
+    }
+    if (__any_sync(kFull, bad) && lane_id() == 0) atomicOr((unsigned long long*)&acc[ACC_ERR], (unsigned long long)kErrBadCsr);
+}
+
+unsigned check_grid(int64_t work) {
+    int64_t b = (work + 255) / 256;
+    if (b < 1) b = 1;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    return (unsigned)(b > cap ? cap : b);
+}
+
 // Lay out a Workspace for (n, m) inside [base, base + cap) with the library's one layout; returns
 // the bytes used, or 0 if it does not fit.
 size_t carve(unsigned char* base, size_t cap, int64_t n, int64_t m, Workspace& ws) {
@@ -37,7 +76,9 @@ size_t carve(unsigned char* base, size_t cap, int64_t n, int64_t m, Workspace& w
     return ws_layout(ws, base, n, m);
 }
 
-// Device address of the static array for the current device (looked up once per device).
+// Device address of the static array for the current device (looked up once per device and kept
+// for the life of the process: a device reset invalidates it, so the entry point must not be used
+// across cudaDeviceReset).
 harp_status scratch_address(unsigned char** out) {
     int dev = 0;
     HARP_CK(cudaGetDevice(&dev));
@@ -84,6 +125,12 @@ extern "C" harp_status harp_count4_noalloc(int64_t n, int64_t m, const int64_t* 
     // every accumulator, queue counter and ticket starts at zero; the kernels clear t_e and the
     // window counts themselves
     HARP_CK(cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s));
+    k_check_offsets<<<check_grid(n + 1), 256, 0, s>>>(d_offsets, n, m, ws.acc);
+    HARP_LAUNCHED();
+    if (m > 0) {
+        k_check_cols<<<check_grid(2 * m), 256, 0, s>>>(d_cols, n, m, ws.acc);
+        HARP_LAUNCHED();
+    }
     if (n > 0) {
         HARP_TRY(orient(&g, ws, s));
         HARP_TRY(count_triangles_k4(&g, ws, plan, s));
@@ -91,5 +138,6 @@ extern "C" harp_status harp_count4_noalloc(int64_t n, int64_t m, const int64_t* 
     }
     HARP_TRY(reduce_and_close(&g, ws, s));
     HARP_CK(cudaMemcpyAsync(d_out, ws.acc, 16 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    HARP_CK(cudaMemcpyAsync(d_out + OUT_ERR, ws.acc + ACC_ERR, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     return HARP_OK;
 }

@@ -26,7 +26,8 @@ int bits_for(int64_t x) {
     return b < 1 ? 1 : b;
 }
 
-unsigned grid_for(int64_t work, int threads, int64_t cap = 152 * 64) {
+unsigned grid_for(int64_t work, int threads, int64_t cap = -1) {
+    if (cap < 0) cap = (int64_t)num_sms() * 64;
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > cap) b = cap;
@@ -37,9 +38,12 @@ __global__ void k_vertex_keys(const int64_t* __restrict__ off, int64_t n, int b,
                               uint64_t* __restrict__ keys, uint64_t* __restrict__ acc,
                               const int32_t* __restrict__ gid_in, uint64_t* __restrict__ accG) {
     uint64_t s3 = 0;
+    // a caller-built CSR that failed its check (harp_count4_noalloc) is counted as edgeless: every
+    // later kernel then stays inside the arrays sized for its (n, m)
+    const bool bad_csr = (acc[ACC_ERR] & kErrBadCsr) != 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+        uint64_t d = bad_csr ? 0 : (uint64_t)(off[v + 1] - off[v]);
         const uint64_t g = gid_in ? (uint64_t)gid_in[v] : 0;
         keys[v] = (g << (bd + b)) | (d << b) | (uint64_t)v;
         const uint64_t c3 = choose3_u64(d);
@@ -342,11 +346,11 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
         k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
                                                                 ws.off, n, ws.cols, ws.dplus);
         HARP_LAUNCHED();
-        k_sort_rows_block<<<152 * 4, 512, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n,
+        k_sort_rows_block<<<num_sms() * 4, 512, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n,
                                                    ws.cols, ws.dplus, ws.q_tri, qsort);
         HARP_LAUNCHED();
         // the out-CSR columns + t_e region (2m int32) is free until k_out_csr: hub sort ping-pong
-        k_sort_rows_hub<<<152, kHubThreads, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n, b,
+        k_sort_rows_hub<<<num_sms(), kHubThreads, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n, b,
                                                      ws.cols, ws.colsp, ws.dplus, ws.q_tri, qsort);
         HARP_LAUNCHED();
     } else {

@@ -677,7 +677,8 @@ harp_status cut_wedge_blocks(const RankGraph& g, uint64_t budget, int32_t parts,
 int64_t tri_scratch_bytes(int64_t m) {
     int64_t dmax = 1;
     while (dmax * dmax < 2 * m) ++dmax;
-    return 152 * 8 * (dmax + 32) * 4 + (dmax > 1024 ? (int64_t)152 * 4096 * 128 * 4 : 0);
+    const int64_t sms = num_sms();
+    return sms * 8 * (dmax + 32) * 4 + (dmax > 1024 ? sms * 4096 * 128 * 4 : 0);
 }
 
 // The device results of all blocks, and where the time went.

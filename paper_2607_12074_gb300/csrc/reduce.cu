@@ -117,7 +117,7 @@ harp_status reduce_and_close_batch(const harp_csr* g, Workspace& ws, int64_t G, 
     const Sink sink{ws.acc, ws.gid, ws.accG};
     int64_t blocks = (g->n * 32 + 255) / 256;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (g->m > 0) {
         k_reduce_rows_batch<<<(unsigned)blocks, 256, 0, s>>>(ws.offp, ws.te, g->n, sink);
         HARP_LAUNCHED();
@@ -132,7 +132,7 @@ harp_status reduce_and_close_batch(const harp_csr* g, Workspace& ws, int64_t G, 
 harp_status reduce_and_close(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     int64_t blocks = (g->m + 255) / 256;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
     k_reduce_close<<<(unsigned)blocks, 256, 0, s>>>(ws.te, g->m, ws.acc);
     HARP_LAUNCHED();
     return HARP_OK;

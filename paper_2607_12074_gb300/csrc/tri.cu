@@ -779,7 +779,7 @@ harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slo
     const size_t smem = sizeof(CtaSmem<DMAX>);
     HARP_CK(cudaFuncSetAttribute(k_tri_cta<DMAX, THREADS, MINB, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    k_tri_cta<DMAX, THREADS, MINB, BS><<<152 * MINB, THREADS, smem, s>>>(
+    k_tri_cta<DMAX, THREADS, MINB, BS><<<num_sms() * MINB, THREADS, smem, s>>>(
         ws.offp, ws.colsp, ws.deg, ws.q_tri, g->n, cls, wmax, cmax, bmax, reuse,
         (const unsigned long long*)&ws.acc[Q_TRI_WARP], (unsigned long long*)&ws.acc[ticket_slot], ws.te,
         Sink{ws.acc, ws.gid, ws.accG});
@@ -791,7 +791,7 @@ template <bool BS>
 harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, int bmax, bool reuse,
                          cudaStream_t s) {
     const Sink sink{ws.acc, ws.gid, ws.accG};
-    k_tri_warp<BS><<<152 * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri,
+    k_tri_warp<BS><<<num_sms() * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri,
                                                    (const unsigned long long*)&ws.acc[Q_TRI_WARP], reuse, ws.te, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_TRI_WARP));
@@ -816,7 +816,7 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     const bool reuse = !(plan.flags & HARP_PLAN_NO_REUSE);
     unsigned long long* cnt = (unsigned long long*)&ws.acc[Q_TRI_WARP];
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     unsigned long long* cnt_fb = (unsigned long long*)&ws.acc[Q_TRI_FB];
     unsigned long long* cnt_big = (unsigned long long*)&ws.acc[Q_TRI_BIG];
     k_tri_classify<<<(unsigned)blocks, 256, 0, s>>>(ws.dplus, n, ws.own_lo, ws.own_hi, wmax, cmax, bmax, ws.q_tri,
@@ -830,13 +830,13 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     while (dmax * dmax < 2 * g->m) ++dmax;
     if (dmax > g->max_deg) dmax = g->max_deg;
     if (dmax > cmax && bmax > cmax) {  // global-staged tier: one block per SM, scratch of kBigMax rows
-        const size_t bytes = (size_t)152 * kBigMax * kBigWords * sizeof(uint32_t);
+        const size_t bytes = (size_t)num_sms() * kBigMax * kBigWords * sizeof(uint32_t);
         uint32_t* scratch = nullptr;
         HARP_CK(cudaMallocAsync((void**)&scratch, bytes, s));
         const size_t smem = sizeof(BigSmem);
         cudaError_t e = cudaFuncSetAttribute(k_tri_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) {
-            k_tri_big<<<152, kBigThreads, smem, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_mid + n, cnt_big,
+            k_tri_big<<<num_sms(), kBigThreads, smem, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_mid + n, cnt_big,
                                                       (unsigned long long*)&ws.acc[T_TRI_BIG], reuse, scratch, ws.te,
                                                       sink);
             note_launch();
@@ -850,7 +850,7 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
     }
     // fallback: per-warp frontier buffers of the largest possible out-degree
     if (dmax > cmax && dmax > bmax) {
-        const int fb_blocks = 152;
+        const int fb_blocks = num_sms();
         const int64_t per_warp = dmax + 32;
         const size_t bytes = (size_t)fb_blocks * 8 * (size_t)per_warp * sizeof(int32_t);
         int32_t* scratch = nullptr;

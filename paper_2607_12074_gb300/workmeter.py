@@ -12,8 +12,10 @@ Per unit (int32 ids and counters = 4 B, int64 offsets = 8 B):
   triangle      per anchor u: its list N+(u) (4 d+), per row v in N+(u): offsets (16) and the probed
                 part of N+(v) up to max N+(u) (4 each); per triangle: 3 t_e updates (8 each, RMW);
                 per out-arc: its own t_e update (8)
-  wedge (C4)    per root u and per pass over its lower neighbours (1 pass, or 1 per x-window):
-                N-(u) (4 d-) + offsets of each w (16 d-); per wedge element x of degree >= 2: 4
+  wedge (C4)    per root u: N-(u) read once (4 d-) + the row bounds of each w (16 d-); per wedge
+                element x of degree >= 2: 4.  The windowed kernel re-reads N-(u) and the row
+                bounds once per further x-window; those bytes are this design's overhead and are
+                reported apart ("overhead_bytes"), not counted as algorithmic
   reduction     t_e read: 4 m
 """
 from __future__ import annotations
@@ -143,7 +145,8 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
         passes = nwin[sel]
         out[name] = {"roots": int(sel.sum()), "wedges": int(W[sel].sum()),
                      "items": int(passes.sum()),
-                     "bytes": int((20 * dm[sel] * passes).sum() + 4 * W[sel].sum())}
+                     "bytes": int((20 * dm[sel]).sum() + 4 * W[sel].sum()),
+                     "overhead_bytes": int((20 * dm[sel] * (passes - 1)).sum())}
     out["c4_wedges_total"] = int(W.sum())
     out["reduce"] = {"bytes": 4 * m}
     return out
