@@ -335,9 +335,62 @@ def served_at_rate(harp, np, gs, rate, seed, budget):
             "peak_resident_bytes": st["peak_resident_bytes"]}
 
 
+def bench_partitioned(harp, graphgen, torch, n, cap_gib, steps=1, warmup=0, whole=True):
+    """The partitioned large-graph workload (Chung-Lu, exponent 2.1, max expected degree 1e6, mean
+    degree 48; n = 5e7 gives about 1.2e9 edges): harp_count4_partitioned under a device cap, timed
+    from the host edge list to the counts (Table IV's split: host / transfer / kernels), and the same
+    graph counted whole on the device (harp_build_csr from device-resident edges + harp_count4, no
+    cap) as the exactness check of the owner rule: the two counts must be equal."""
+    t0 = time.perf_counter()
+    g = graphgen.chung_lu_large(n)
+    t_gen = time.perf_counter() - t0
+    budget = int(cap_gib * (1 << 30))
+    runs = []
+    for k in range(warmup + steps):
+        t = time.perf_counter()
+        counts, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=budget)
+        wall = time.perf_counter() - t
+        if k >= warmup:
+            runs.append((wall, st, counts))
+    wall, st, counts = min(runs, key=lambda r: r[0])
+    m = st["m"]
+    out = {"workload": f"chung_lu(n={g.n}, gamma=2.1, max expected degree {1e6 * g.n / 5e7:g}, mean degree 48, "
+                       f"seed 1), partitioned under a {cap_gib:g} GiB device cap",
+           "n": g.n, "m": m, "value": m / wall, "unit": UNIT, "seconds": wall, "runs": len(runs),
+           "blocks": st["partitions"], "tri_blocks": st["tri_blocks"], "wedge_blocks": st["wedge_blocks"],
+           "wedge_sliced": st["wedge_sliced"], "device_peak_bytes": st["device_peak_bytes"],
+           "halo_arcs": st["halo_arcs"], "h2d_bytes": st["h2d_bytes"], "host_ms": st["host_ms"],
+           "host_graph_ms": st["graph_ms"], "host_cut_ms": st["cut_ms"], "device_tri_ms": st["tri_ms"],
+           "device_wedge_ms": st["wedge_ms"], "transfer_ms": st["transfer_ms"], "device_ms": st["device_ms"],
+           "transfer_share": st["transfer_ms"] / (1000 * wall), "generate_s": t_gen,
+           "counts": [int(x) for x in counts]}
+    if whole:
+        # the same edges whole on the device: no cap, one CSR, one count (per-segment CUDA events)
+        t = time.perf_counter()
+        src_d = torch.from_numpy(g.src).cuda()
+        dst_d = torch.from_numpy(g.dst).cuda()
+        csr = harp.harp_build_csr(g.n, src_d, dst_d)
+        del src_d, dst_d
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t
+        harp.harp_set_profiling(True)
+        t = time.perf_counter()
+        cw = harp.harp_count4(csr)
+        t_count = time.perf_counter() - t
+        ms, _ = harp.harp_last_stage_times()
+        harp.harp_set_profiling(False)
+        info = csr.info()
+        csr.close()
+        torch.cuda.empty_cache()
+        out["whole"] = {"m": info["m"], "device_bytes": info["device_bytes"], "build_s": t_build,
+                        "count_s": t_count, "value": info["m"] / t_count, "unit": UNIT,
+                        "segments_ms": {k: v for k, v in zip(SEGMENTS, ms)}, "counts": [int(x) for x in cw]}
+        out["partitioned_equals_whole"] = [int(x) for x in cw] == out["counts"] and info["m"] == m
+    return out
+
+
 def run_partitioned(args):
-    """The partitioned large-graph workload: one harp_count4_partitioned call (timed end to end)."""
-    import numpy as np
+    """The partitioned large-graph workload as its own JSON line (edges/s of the partitioned call)."""
     import torch
 
     import graphgen
@@ -349,33 +402,15 @@ def run_partitioned(args):
     torch.cuda.set_device(local)
     _build.build()
     harp.lib()
-    t0 = time.perf_counter()
-    g = graphgen.chung_lu_large(args.n)
-    t_gen = time.perf_counter() - t0
-    budget = int(args.cap_gib * (1 << 30))
-    runs = []
-    for k in range(args.warmup + args.steps):
-        with ClockSampler(local) as clocks:
-            t = time.perf_counter()
-            counts, st = harp.harp_count4_partitioned(g.n, g.src, g.dst, budget_bytes=budget)
-            wall = time.perf_counter() - t
-        if k >= args.warmup:
-            runs.append((wall, st, clocks.summary()))
-    wall, st, clk = min(runs, key=lambda r: r[0])
-    m = st["m"]
-    line = {"metric": METRIC, "value": m / wall, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * wall, "higher_is_better": True, "scaling": "weak",
+    with ClockSampler(local) as clocks:
+        r = bench_partitioned(harp, graphgen, torch, args.n, args.cap_gib, steps=args.steps, warmup=args.warmup,
+                              whole=not args.no_whole)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["runs"],
+            "warmup": args.warmup, "ms_per_step": 1000 * r["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"chung_lu(n={g.n}, gamma=2.1, max expected degree {1e6 * g.n / 5e7:g}, "
-                                   f"mean degree 48, seed 1), partitioned under a {args.cap_gib:g} GiB device cap",
-                       "n": g.n, "m": m, "parallelism": "single", "l2": "inputs larger than L2"},
-            "partition": {"blocks": st["partitions"], "device_peak_bytes": st["device_peak_bytes"],
-                          "halo_arcs": st["halo_arcs"], "h2d_bytes": st["h2d_bytes"], "host_ms": st["host_ms"],
-                          "host_graph_ms": st["graph_ms"], "host_cut_ms": st["cut_ms"],
-                          "device_tri_ms": st["tri_ms"], "device_wedge_ms": st["wedge_ms"],
-                          "transfer_ms": st["transfer_ms"], "device_ms": st["device_ms"],
-                          "transfer_share": st["transfer_ms"] / (1000 * wall)},
-            "generate_s": t_gen, "clocks": clk, "counts": [int(x) for x in counts]}
+            "config": {"workload": r["workload"], "n": r["n"], "m": r["m"], "parallelism": "single",
+                       "l2": "inputs larger than L2"},
+            "partitioned": r, "clocks": clocks.summary(), "counts": r["counts"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -439,6 +474,10 @@ def main():
                          "partitioned under --cap-gib or counted whole on the device")
     ap.add_argument("--n", type=int, default=50_000_000, help="vertices of the Chung-Lu workloads")
     ap.add_argument("--cap-gib", type=float, default=24.0, help="device cap of the partitioned workload")
+    ap.add_argument("--no-whole", action="store_true",
+                    help="partitioned workload: skip the uncapped whole-graph count it is checked against")
+    ap.add_argument("--no-partitioned", action="store_true",
+                    help="skip the partitioned large-graph block of the default line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -51,8 +51,9 @@ def _load():
             lib.gg_rgg.argtypes = [i64, dbl, u64, p32, p32, i64]
             lib.gg_rmat.argtypes = [i32, i64, dbl, dbl, dbl, u64, p32, p32, i64]
             lib.gg_chung_lu.argtypes = [i64, dbl, dbl, dbl, u64, i64, i64, p32, p32, i64]
+            lib.gg_chung_lu_induced.argtypes = [i64, dbl, dbl, dbl, u64, p32, i64, i64, i64, p32, p32, i64]
             lib.gg_splitmix64_at.argtypes = [u64, u64, i64]
-            for f in (lib.gg_ba, lib.gg_er, lib.gg_rgg, lib.gg_rmat, lib.gg_chung_lu):
+            for f in (lib.gg_ba, lib.gg_er, lib.gg_rgg, lib.gg_rmat, lib.gg_chung_lu, lib.gg_chung_lu_induced):
                 f.restype = i64
             lib.gg_splitmix64_at.restype = u64
             _lib = lib
@@ -127,13 +128,8 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: floa
     return Graph(n, src, dst, f"rmat(scale={scale},ef={edge_factor},seed={seed})")
 
 
-def chung_lu(n: int, gamma: float, max_weight: float, mean_degree: float, seed: int,
-             rows: tuple[int, int] | None = None) -> Graph:
-    """Chung-Lu power law with w_i = c (i + i0)^(-1/(gamma-1)).
-
-    c and i0 are fixed so that w_0 = max_weight and sum_i w_i ~= n * mean_degree (bisection on i0).
-    ``rows`` restricts sampling to pair rows [lo, hi) (for chunked generation of very large graphs).
-    """
+def _chung_lu_scale(n: int, gamma: float, max_weight: float, mean_degree: float):
+    """(c, i0) with w_0 = c i0^(-1/(gamma-1)) = max_weight and sum_i w_i ~= n * mean_degree."""
     ex = -1.0 / (gamma - 1.0)
     target = n * mean_degree
 
@@ -151,7 +147,18 @@ def chung_lu(n: int, gamma: float, max_weight: float, mean_degree: float, seed: 
         else:
             lo = mid
     i0 = math.sqrt(lo * hi)
-    c = max_weight * i0 ** (-ex)
+    return max_weight * i0 ** (-ex), i0
+
+
+def chung_lu(n: int, gamma: float, max_weight: float, mean_degree: float, seed: int,
+             rows: tuple[int, int] | None = None) -> Graph:
+    """Chung-Lu power law with w_i = c (i + i0)^(-1/(gamma-1)).
+
+    c and i0 are fixed so that w_0 = max_weight and sum_i w_i ~= n * mean_degree (bisection on i0).
+    ``rows`` restricts sampling to pair rows [lo, hi) (for chunked generation of very large graphs).
+    """
+    c, i0 = _chung_lu_scale(n, gamma, max_weight, mean_degree)
+    ex = -1.0 / (gamma - 1.0)
     name = f"chung_lu(n={n},gamma={gamma},seed={seed})"
     if rows is None and n >= 1_000_000:
         # every row draws from its own stream, so row chunks are independent: generate balanced
@@ -214,12 +221,56 @@ def chung_lu_large(n: int = 50_000_000, seed: int = 1) -> Graph:
     return chung_lu(n, 2.1, 1e6 * n / 50_000_000, 48.0, seed)
 
 
-def chung_lu_subsample(n_sub: int = 1_000_000, n_full: int = 50_000_000, seed: int = 1) -> Graph:
-    """Stand-in for the subgraph of ``chung_lu_large`` induced on a uniform n_sub-vertex subset: a
-    vertex keeps each neighbour with probability n_sub / n_full, so the subset is Chung-Lu with the
-    weights scaled by that fraction (max expected degree 1e6 f, mean degree 48 f)."""
-    f = n_sub / n_full
-    return chung_lu(n_sub, 2.1, 1e6 * f, 48.0 * f, seed)
+def chung_lu_induced(n: int, gamma: float, max_weight: float, mean_degree: float, seed: int, subset) -> Graph:
+    """The subgraph of ``chung_lu(n, gamma, max_weight, mean_degree, seed)`` induced on ``subset``
+    (distinct vertex ids), renumbered by the position of each vertex in the sorted subset.  Exactly
+    the edges of the full graph between subset vertices: every row of the full graph has its own
+    random stream, so only the subset's rows are drawn."""
+    sub_ids = np.unique(np.asarray(subset, dtype=np.int64)).astype(np.int32)
+    k = int(sub_ids.size)
+    c, i0 = _chung_lu_scale(n, gamma, max_weight, mean_degree)
+    name = f"chung_lu(n={n},gamma={gamma},seed={seed})[induced on {k} vertices]"
+    if k == 0:
+        return Graph(0, np.zeros(0, np.int32), np.zeros(0, np.int32), name)
+    import threading
+    parts = max(1, min(64, (os.cpu_count() or 4) * 2, k))
+    cuts = [k * j // parts for j in range(parts + 1)]
+    out = [None] * parts
+    psub = sub_ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    frac = k / max(n, 1)
+
+    def work(j):
+        a, b = cuts[j], cuts[j + 1]
+        cap = int((b - a) * mean_degree * frac * 2) + 1024
+        out[j] = _call_growing(_load().gg_chung_lu_induced, (n, gamma, c, i0, seed, psub, k, a, b), cap)
+
+    th = [threading.Thread(target=work, args=(j,)) for j in range(parts)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    return Graph(k, np.concatenate([o[0] for o in out]), np.concatenate([o[1] for o in out]), name)
+
+
+def uniform_subset(n: int, k: int, seed: int) -> np.ndarray:
+    """A seeded uniform k-subset of [0, n) (sorted int32): the first k of a SplitMix64-keyed
+    permutation, i.e. the k vertices with the smallest hash of (seed, vertex)."""
+    keys = np.empty(n, np.uint64)
+    # vectorised SplitMix64 finaliser of (seed, v): the same stream definition as the C generators use
+    z = np.arange(n, dtype=np.uint64) + np.uint64((seed * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    keys[:] = z ^ (z >> np.uint64(31))
+    idx = np.argpartition(keys, k - 1)[:k] if 0 < k < n else np.arange(min(k, n))
+    return np.sort(idx).astype(np.int32)
+
+
+def chung_lu_large_induced(n_sub: int = 1_000_000, n_full: int = 50_000_000, seed: int = 1,
+                           subset_seed: int = 2) -> Graph:
+    """The partitioned large-graph workload's oracle check input: the subgraph of
+    ``chung_lu_large(n_full, seed)`` induced on a seeded uniform n_sub-vertex subset."""
+    sub_ids = uniform_subset(n_full, n_sub, subset_seed)
+    return chung_lu_induced(n_full, 2.1, 1e6 * n_full / 50_000_000, 48.0, seed, sub_ids)
 
 
 def batch_spec(seed: int, n_lo: int = 50, n_hi: int = 20000) -> BatchSpec:

@@ -225,37 +225,79 @@ int64_t gg_rmat(int32_t scale, int64_t ef, double a, double b, double c, uint64_
  * upper bound p = min(1, w_i w_j / S), then accepts with q / p).
  * Returns the edge count or -(needed) if cap is too small.
  * ------------------------------------------------------------------------- */
+/* The expected-degree weights w_i = c (i + i0)^(-1/(gamma-1)) and their sum S (in index order). */
+static double cl_weights(int64_t n, double gamma, double c, double i0, double* w) {
+    double ex = -1.0 / (gamma - 1.0);
+    double S = 0.0;
+    for (int64_t i = 0; i < n; ++i) { w[i] = c * pow((double)i + i0, ex); S += w[i]; }
+    return S;
+}
+
+/* Row u of the Miller-Hagberg process: every pair (u, v), v > u, is an edge with probability
+ * min(1, w_u w_v / S), drawn from row u's own stream.  emit(v) is called for each edge. */
+#define CL_ROW(u, ...)                                                         \
+    do {                                                                       \
+        gg_rng r_ = gg_stream(seed, 0x100000000ULL + (uint64_t)(u));           \
+        int64_t v = (u) + 1;                                                   \
+        double p_ = w[u] * w[v < n ? v : n - 1] / S;                           \
+        if (p_ > 1.0) p_ = 1.0;                                                \
+        while (v < n && p_ > 0.0) {                                            \
+            if (p_ < 1.0) {                                                    \
+                double q_ = 1.0 - gg_unif(&r_);                                \
+                v += (int64_t)floor(log(q_) / log(1.0 - p_));                  \
+            }                                                                  \
+            if (v < n) {                                                       \
+                double qq_ = w[u] * w[v] / S;                                  \
+                if (qq_ > 1.0) qq_ = 1.0;                                      \
+                if (gg_unif(&r_) < qq_ / p_) { __VA_ARGS__; }                  \
+                p_ = qq_;                                                      \
+                ++v;                                                           \
+            }                                                                  \
+        }                                                                      \
+    } while (0)
+
 int64_t gg_chung_lu(int64_t n, double gamma, double c, double i0, uint64_t seed,
                     int64_t row_lo, int64_t row_hi,
                     int32_t* src, int32_t* dst, int64_t cap) {
     if (n <= 1) return 0;
-    double ex = -1.0 / (gamma - 1.0);
     double* w = (double*)malloc(sizeof(double) * (size_t)n);
-    double S = 0.0;
-    for (int64_t i = 0; i < n; ++i) { w[i] = c * pow((double)i + i0, ex); S += w[i]; }
+    double S = cl_weights(n, gamma, c, i0, w);
     int64_t e = 0, over = 0;
     if (row_hi > n) row_hi = n;
     for (int64_t u = row_lo; u < row_hi; ++u) {
-        gg_rng r = gg_stream(seed, 0x100000000ULL + (uint64_t)u);
-        int64_t v = u + 1;
-        double p = w[u] * w[v < n ? v : n - 1] / S;
-        if (p > 1.0) p = 1.0;
-        while (v < n && p > 0.0) {
-            if (p < 1.0) {
-                double q = 1.0 - gg_unif(&r);
-                v += (int64_t)floor(log(q) / log(1.0 - p));
+        CL_ROW(u, {
+            if (e < cap) { src[e] = (int32_t)u; dst[e] = (int32_t)v; } else over = 1;
+            ++e;
+        });
+    }
+    free(w);
+    return over ? -e : e;
+}
+
+/* The subgraph of gg_chung_lu(n, ...) induced on the vertex set sub[0 .. k) (sorted, distinct), its
+ * vertices renumbered by their index in sub.  Rows are independent streams, so only the rows of sub
+ * are drawn: the edges of row u = sub[i] whose other end lies in sub, for i in [i_lo, i_hi). */
+int64_t gg_chung_lu_induced(int64_t n, double gamma, double c, double i0, uint64_t seed,
+                            const int32_t* sub, int64_t k, int64_t i_lo, int64_t i_hi,
+                            int32_t* src, int32_t* dst, int64_t cap) {
+    if (n <= 1 || k <= 0) return 0;
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    double S = cl_weights(n, gamma, c, i0, w);
+    int64_t e = 0, over = 0;
+    if (i_hi > k) i_hi = k;
+    for (int64_t i = i_lo; i < i_hi; ++i) {
+        const int64_t u = sub[i];
+        CL_ROW(u, {
+            int64_t lo = i + 1, hi = k; /* v > u: its index, if any, lies after i */
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)sub[mid] < v) lo = mid + 1; else hi = mid;
             }
-            if (v < n) {
-                double qq = w[u] * w[v] / S;
-                if (qq > 1.0) qq = 1.0;
-                if (gg_unif(&r) < qq / p) {
-                    if (e < cap) { src[e] = (int32_t)u; dst[e] = (int32_t)v; } else over = 1;
-                    ++e;
-                }
-                p = qq;
-                ++v;
+            if (lo < k && (int64_t)sub[lo] == v) {
+                if (e < cap) { src[e] = (int32_t)i; dst[e] = (int32_t)lo; } else over = 1;
+                ++e;
             }
-        }
+        });
     }
     free(w);
     return over ? -e : e;

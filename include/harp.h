@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define HARP_ABI_VERSION 1u
+#define HARP_ABI_VERSION 2u  /* plans of version 1 (without the cache fields) are still accepted */
 
 typedef enum harp_status {
     HARP_OK = 0,
@@ -107,6 +107,15 @@ harp_status harp_csr_arrays(const harp_csr* g, const int64_t** offsets, const in
  * never changes the counts, only the work.  All-zero fields mean "library default".
  * ---------------------------------------------------------------------------------------------- */
 #define HARP_BASIS_TRIANGLE_WEDGE 0u  /* triangles + per-edge t_e + 4-clique extension + wedges  */
+/* The closure equations of Section III-F executed as printed: per triangle T the counts X_1, X_2, X_3
+ * of outside vertices adjacent to exactly 1, 2, 3 of T (paw = sum X_1, diamond = sum X_2 / 2,
+ * 4-clique = sum X_3 / 4); per edge e = (u, v) the pairs of A_e x B_e (4-path = non-edges, 4-cycle =
+ * edges / 4); per vertex u the star form on H_u = G[N(u)].  The 2-vertex frontiers it reads (common
+ * neighbours of an edge; of a non-adjacent pair) go through the signature cache of Section III-C,
+ * keyed by the generating pair and its adjacency / non-adjacency mask.  Same counts as the
+ * triangle-wedge basis, far more work on skewed graphs (harp_select_anchors weighs the two by Eq. 1).
+ * Single graphs only (harp_count4, harp_count4_stats, harp_count4_async). */
+#define HARP_BASIS_LITERAL 1u
 
 #define HARP_PROBE_HASH 1u     /* frontier membership by a shared-memory hash of N+(u)             */
 #define HARP_PROBE_BSEARCH 2u  /* frontier membership by binary search in the sorted N+(u)         */
@@ -114,7 +123,9 @@ harp_status harp_csr_arrays(const harp_csr* g, const int64_t** offsets, const in
 #define HARP_PLAN_NO_GRAPH 1u  /* flags: launch kernels one by one instead of a captured CUDA graph */
 #define HARP_PLAN_NO_REUSE 2u  /* flags: signature reuse off: every 4-clique extension recomputes  */
                                /* |N+(w) n S_uv| from N+(w) instead of reading the staged frontier */
-                               /* of (u, w) (Section III-C); the counts are identical              */
+                               /* of (u, w) (Section III-C); the literal basis computes every      */
+                               /* frontier instead of reading the signature cache; the counts are  */
+                               /* identical                                                        */
 #define HARP_PLAN_NO_BAND_MERGE 4u /* flags: keep every wedge counter width (3, 4, 5, 6, 8, 16, 32  */
                                    /* bits by the degree of x) as its own band of windows instead of */
                                    /* merging narrow bands that would cost more windows; the counts  */
@@ -141,6 +152,14 @@ typedef struct harp_plan {
     double est_reuse;            /* fraction of frontier reads expected to repeat (reuse)          */
     double est_yield;            /* closure yield: induced counts recoverable from the statistics */
     double objective;            /* value of the Eq. 1 objective for the chosen basis              */
+    /* version >= 2 only (a version-1 plan ends at `objective` and gets the defaults below) */
+    uint32_t lit_cache_log2;     /* literal basis: signature-cache slots = 2^this (0 = sized from m, */
+                                 /* at most 2^25; 16 bytes a slot)                                  */
+    uint32_t lit_cache_min_deg;  /* literal basis: degree bin admitted to the cache: a frontier is   */
+                                 /* cached only if both generating vertices have degree >= this     */
+                                 /* (smaller ones are recomputed; 0 = all)                          */
+    double est_cost_tw;          /* Eq. 1 objective of the triangle-wedge basis (harp_select_anchors) */
+    double est_cost_lit;         /* Eq. 1 objective of the literal basis                          */
 } harp_plan;
 
 typedef struct harp_select_opts {
@@ -150,7 +169,10 @@ typedef struct harp_select_opts {
     double lambda_inter, lambda_halo, lambda_reuse, lambda_yield;  /* 0 = normalised defaults     */
 } harp_select_opts;
 
-/* Fill *out with the plan chosen by the Eq. 1 objective for this graph.  opts may be NULL. */
+/* Fill *out with the plan chosen by the Eq. 1 objective for this graph: both legal bases
+ * (HARP_BASIS_TRIANGLE_WEDGE, HARP_BASIS_LITERAL) are scored from a sample of arcs (degrees and the
+ * exact common-neighbour count of each sampled arc) and the cheaper one is chosen; est_cost_tw and
+ * est_cost_lit hold both objectives.  opts may be NULL. */
 harp_status harp_select_anchors(const harp_csr* g, const harp_select_opts* opts, harp_plan* out);
 
 /* ------------------------------------------------------------------------------------------------
@@ -161,9 +183,11 @@ harp_status harp_select_anchors(const harp_csr* g, const harp_select_opts* opts,
  * handle's stream and returns after the counts are on the host in counts_out[6]. */
 harp_status harp_count4(const harp_csr* g, const harp_plan* plan, uint64_t counts_out[6]);
 
-/* Signature-reuse counters of the last blocking count on g (harp_count4 / harp_count4_stats):
- * lookups = 4-clique extensions (one per triangle), hits = those answered by a staged frontier
- * (Section III-C).  HARP_ENOTFOUND before the first blocking count. */
+/* Signature-reuse counters of the last blocking count on g (harp_count4 / harp_count4_stats)
+ * (Section III-C).  Triangle-wedge basis: lookups = 4-clique extensions (one per triangle), hits =
+ * those answered by a staged frontier.  Literal basis: lookups = frontier requests to the signature
+ * cache (common neighbours of an edge or of a non-adjacent pair), hits = those found in it.
+ * HARP_ENOTFOUND before the first blocking count. */
 harp_status harp_reuse_stats(const harp_csr* g, uint64_t* lookups, uint64_t* hits);
 
 /* As harp_count4, and also return the anchor statistics (HARP_STAT_* order) in stats_out[8]. */
@@ -186,6 +210,8 @@ harp_status harp_count4_async(const harp_csr* g, const harp_plan* plan, uint64_t
  *   5 wedge anchors, warp-local mode (+ work estimate of every root)
  *   6 wedge anchors, CTA hash mode           7 wedge anchors, windowed CTA mode
  *   8 reduction + closure
+ * A count with the literal basis fills 0 (orientation), 1 (per-triangle X_j pass), 5 (per-edge
+ * A_e x B_e pass) and 8 (per-vertex star pass + closure); the others read 0.
  * Call harp_set_profiling(1) first; the values are those of the last completed count.
  * launches_out receives the number of kernels the library launched in that count. */
 #define HARP_NSEGMENTS 9

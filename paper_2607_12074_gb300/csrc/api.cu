@@ -130,8 +130,8 @@ namespace {
 
 harp_status validate_plan(const harp_plan* p) {
     if (!p) return HARP_OK;
-    if (p->version != 0 && p->version != HARP_ABI_VERSION) return HARP_EINVAL;
-    if (p->basis != HARP_BASIS_TRIANGLE_WEDGE) return HARP_EINVAL;
+    if (p->version != 0 && p->version != 1 && p->version != HARP_ABI_VERSION) return HARP_EINVAL;
+    if (p->basis != HARP_BASIS_TRIANGLE_WEDGE && p->basis != HARP_BASIS_LITERAL) return HARP_EINVAL;
     return HARP_OK;
 }
 
@@ -155,9 +155,13 @@ harp_status enqueue_count(harp_csr* g, const harp_plan* user_plan, cudaStream_t 
     const int64_t l0 = g_launches.load();
     harp_status st = orient(g, ws, s);
     if (st == HARP_OK) st = prof_mark(s, SEG_ORIENT) == cudaSuccess ? HARP_OK : HARP_ECUDA;
-    if (st == HARP_OK) st = count_triangles_k4(g, ws, plan, s);
-    if (st == HARP_OK) st = count_wedge_c4(g, ws, plan, s);
-    if (st == HARP_OK) st = reduce_and_close(g, ws, s);
+    if (plan.basis == HARP_BASIS_LITERAL) {
+        if (st == HARP_OK) st = count_literal(g, ws, plan, s);
+    } else {
+        if (st == HARP_OK) st = count_triangles_k4(g, ws, plan, s);
+        if (st == HARP_OK) st = count_wedge_c4(g, ws, plan, s);
+        if (st == HARP_OK) st = reduce_and_close(g, ws, s);
+    }
     if (st == HARP_OK) st = prof_mark(s, SEG_REDUCE) == cudaSuccess ? HARP_OK : HARP_ECUDA;
     if (prof && st == HARP_OK && cudaEventSynchronize(t_marks[HARP_NSEGMENTS]) == cudaSuccess) {
         int prev = 0;
@@ -184,7 +188,8 @@ harp_status count_to_host(const harp_csr* gc, const harp_plan* plan, uint64_t* c
     HARP_CK(cudaMemcpyAsync(host, g->ws.acc, sizeof(host), cudaMemcpyDeviceToHost, g->stream));
     HARP_CK(cudaStreamSynchronize(g->stream));
     if (host[ACC_ERR]) return HARP_EDEVICE;  // a kernel's self-check skipped an out-of-range access
-    g->sig_lookups = host[ACC_T];
+    const bool literal = plan && plan->basis == HARP_BASIS_LITERAL;
+    g->sig_lookups = literal ? host[ACC_SIG_LOOKUPS] : host[ACC_T];
     g->sig_hits = host[ACC_SIG_HITS];
     g->have_reuse = true;
     std::memcpy(counts_out, host + OUT_COUNTS, 6 * sizeof(uint64_t));

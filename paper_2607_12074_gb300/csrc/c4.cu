@@ -36,13 +36,19 @@ namespace harp {
 namespace {
 
 constexpr int32_t kEmpty = -1;
-constexpr int kWinThreads = 512;
-// Window sizes by resident blocks per SM (plan.c4_window_bytes picks one): 100 KiB at 2 blocks,
-// 64 KiB at 3, 48 KiB at 4 (counters plus ~3 KiB of static and reserved shared memory per block).
+// Window sizes by resident blocks per SM (plan.c4_window_bytes picks one): 200 KiB for one
+// 1024-thread block, 100 KiB at 2 blocks of 512 threads (the default), 64 KiB at 3, 48 KiB at 4
+// (counters plus ~3 KiB of static and reserved shared memory per block).  On R-MAT scale 20 the
+// 200 KiB window measured 15.7 ms against 13.2 ms for 100 KiB: its fewer (root, window) items do not
+// pay for the 32-warp end-of-item barrier there; it is kept for graphs whose x-range spans many windows.
+constexpr int kWinWords1 = 51200;
 constexpr int kWinWords2 = 25600;
 constexpr int kWinWords3 = 16384;
 constexpr int kWinWords4 = 12288;
-__host__ __device__ constexpr int win_words(int minb) { return minb == 2 ? kWinWords2 : (minb == 3 ? kWinWords3 : kWinWords4); }
+__host__ __device__ constexpr int win_words(int minb) {
+    return minb == 1 ? kWinWords1 : (minb == 2 ? kWinWords2 : (minb == 3 ? kWinWords3 : kWinWords4));
+}
+__host__ __device__ constexpr int win_threads(int minb) { return minb == 1 ? 1024 : 512; }
 constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallSlots = 1024;            // per-warp hash table (W <= 512)
@@ -725,7 +731,7 @@ __device__ __forceinline__ void resolve_item(WinItem& it, int64_t t, int64_t tot
 }
 
 template <int MINB>
-__global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(win_threads(MINB), MINB) k_c4_window(const int64_t* __restrict__ off,
                                                               const int32_t* __restrict__ cols,
                                                               const int64_t* __restrict__ loff,
                                                               const int32_t* __restrict__ lcols,
@@ -771,7 +777,7 @@ __global__ void __launch_bounds__(kWinThreads, MINB) k_c4_window(const int64_t* 
             constexpr int per = 32 / decltype(wc)::value;
             words = (int)((xhi - xlo + per - 1) / per);
         });
-        for (int i = threadIdx.x; i < words; i += kWinThreads) cw[i] = 0;
+        for (int i = threadIdx.x; i < words; i += win_threads(MINB)) cw[i] = 0;
         __syncthreads();  // every thread holds this item; counters and work counters are reset
         if (threadIdx.x == 0)  // the next item, resolved while the block walks this one
             resolve_item<WORDS>(s_next, (int64_t)atomicAdd(ticket, 1ull), total, nroots, win_prefix, q_win, gid,
@@ -860,7 +866,7 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
     const size_t win_smem = (size_t)WORDS * sizeof(uint32_t);
     HARP_CK(cudaFuncSetAttribute(k_c4_window<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
-    k_c4_window<MINB><<<sms * MINB, kWinThreads, win_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus,
+    k_c4_window<MINB><<<sms * MINB, win_threads(MINB), win_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus,
                                                                 ws.fpos, ws.rev,
                                                                 ws.bpos, ws.gid, ws.ginfo, ws.q_win, ws.win_prefix,
                                                                 ws.acc, sink);
@@ -877,6 +883,7 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
     // window size: the largest of the three that fits plan.c4_window_bytes (at least the smallest)
     const bool merge = !(plan.flags & HARP_PLAN_NO_BAND_MERGE);
+    if (plan.c4_window_bytes >= (uint32_t)kWinWords1 * 4) return wedge_pass<1>(g, ws, warp_max, merge, s);
     if (plan.c4_window_bytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, merge, s);
     if (plan.c4_window_bytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, merge, s);
     return wedge_pass<4>(g, ws, warp_max, merge, s);

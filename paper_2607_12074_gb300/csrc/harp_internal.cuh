@@ -82,7 +82,17 @@ enum : int {
     Q_TRI_FB = 40,         // length of the unstaged-fallback triangle queue
     Q_TRI_BIG = 41,        // length of the global-staged triangle queue
     T_TRI_BIG = 42,        // its ticket
-    kOutLen = 48
+    // literal basis (Section III-F as printed): sums of the per-anchor terms; the three that are
+    // divided (X_2 / 2, X_3 / 4, cycle pairs / 4) are 128-bit (lo, hi) so the division is exact
+    ACC_LIT_X1 = 43,       // sum over triangles of X_1 (mod 2^64)
+    ACC_LIT_X2 = 44,       // 44 lo, 45 hi
+    ACC_LIT_X3 = 46,       // 46 lo, 47 hi
+    ACC_LIT_AB = 48,       // sum over edges of |A_e| |B_e| (mod 2^64)
+    ACC_LIT_E = 49,        // 49 lo, 50 hi: sum over edges of the A_e x B_e pairs that are edges
+    ACC_LIT_STAR = 51,     // sum over vertices of the H_u star form (mod 2^64)
+    ACC_LIT_T = 52,        // triangles enumerated by the literal triangle pass
+    ACC_SIG_LOOKUPS = 53,  // literal basis: frontier requests to the signature cache
+    kOutLen = 64
 };
 
 // Bits of acc[ACC_ERR].  Any set bit makes a blocking count return HARP_EDEVICE; the asynchronous
@@ -205,14 +215,20 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
 // c4.cu: wedge anchor, non-induced 4-cycles (step a5)
 harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s);
 
+// literal.cu: the literal basis (per-triangle X_j, per-edge A_e x B_e, per-vertex H_u stars) and its
+// closure, after orient(); writes acc[OUT_COUNTS..], acc[OUT_STATS..]
+harp_status count_literal(const harp_csr* g, Workspace& ws, const harp_plan& plan, cudaStream_t s);
+
 // reduce.cu: sum_e C(t_e,2), closure (step a7); writes acc[OUT_COUNTS..], acc[OUT_STATS..]
 harp_status reduce_and_close(const harp_csr* g, Workspace& ws, cudaStream_t s);
 // batch mode: per-graph sum_e C(t_e,2) and closure; d_out holds 16 uint64 per graph
 harp_status reduce_and_close_batch(const harp_csr* g, Workspace& ws, int64_t G, uint64_t* d_out, cudaStream_t s);
 
-// planner.cpp
+// planner.cu
 void default_plan(harp_plan* p);
 void normalise_plan(const harp_plan* in, harp_plan* out);
+// Bytes of a caller's plan that are read: version-1 plans end at `objective`.
+size_t plan_bytes(const harp_plan* p);
 
 // ---------------------------------------------------------------------------------------------
 // Device helpers.

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libharp.so")
 HARP_OK, HARP_EINVAL, HARP_ENOMEM, HARP_ECUDA, HARP_EOVERFLOW = 0, 1, 2, 3, 4
 HARP_EAGAIN, HARP_ETIMEOUT, HARP_ENOTFOUND, HARP_EDEVICE = 5, 6, 7, 8
 HARP_PTR_HOST, HARP_PTR_DEVICE = 0, 1
-HARP_ABI_VERSION = 1
-HARP_BASIS_TRIANGLE_WEDGE = 0
+HARP_ABI_VERSION = 2
+HARP_BASIS_TRIANGLE_WEDGE, HARP_BASIS_LITERAL = 0, 1
 HARP_PROBE_HASH, HARP_PROBE_BSEARCH = 1, 2
 HARP_PLAN_NO_GRAPH, HARP_PLAN_NO_REUSE, HARP_PLAN_NO_BAND_MERGE = 1, 2, 4
 HARP_NSEGMENTS = 9
@@ -57,6 +57,10 @@ class harp_plan(ctypes.Structure):
         ("est_reuse", ctypes.c_double),
         ("est_yield", ctypes.c_double),
         ("objective", ctypes.c_double),
+        ("lit_cache_log2", ctypes.c_uint32),
+        ("lit_cache_min_deg", ctypes.c_uint32),
+        ("est_cost_tw", ctypes.c_double),
+        ("est_cost_lit", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -268,8 +272,11 @@ def harp_csr_arrays(g: Csr) -> tuple[int, int]:
 
 
 def harp_select_anchors(g: Csr, sample_vertices: int = 0, seed: int = 0, memory_budget: int = 0) -> harp_plan:
+    """The Eq. 1 plan for g: the cheaper of the two bases (plan.basis), both objectives in
+    est_cost_tw / est_cost_lit."""
     opts = harp_select_opts(sample_vertices, seed, memory_budget, 0.0, 0.0, 0.0, 0.0)
     p = harp_plan()
+    p.version = HARP_ABI_VERSION
     _check(lib().harp_select_anchors(g.handle, ctypes.byref(opts), ctypes.byref(p)), "harp_select_anchors")
     return p
 
@@ -312,7 +319,9 @@ def harp_count4_noalloc(n: int, m: int, d_offsets: int, d_cols: int, d_out: int,
 
     For callers that may not allocate device memory while they run.  d_offsets / d_cols / d_out
     are device pointers (int64[n+1], int32[2m], uint64[16]); the work is only enqueued on `stream`.
-    Scratch is a static 64 MiB device array shared by all calls: serialise calls that could overlap.
+    d_out[6] is the device self-check word (0 = fine; nonzero = a CSR whose sizes or ids failed the
+    check, counted as edgeless).  Scratch is a static 64 MiB device array shared by all calls:
+    serialise calls that could overlap.
     """
     _check(lib().harp_count4_noalloc(int(n), int(m), ctypes.c_void_p(d_offsets), ctypes.c_void_p(d_cols),
                                      ctypes.c_void_p(d_out), _stream_handle(stream)), "harp_count4_noalloc")

@@ -25,7 +25,15 @@ import numpy as np
 WARP_MAX_TRI = 32
 CTA_SMALL_MAX = 256
 CTA_MAX = 1024
-WIN_WORDS = {2: 25600, 3: 16384, 4: 12288}  # counter words per wedge window by resident blocks per SM
+WIN_WORDS = {1: 51200, 2: 25600, 3: 16384, 4: 12288}  # counter words per wedge window by resident blocks per SM
+
+
+def window_words(c4_window_bytes):
+    """Counter words of the wedge window the kernel picks for plan.c4_window_bytes (the largest that fits)."""
+    for minb in (1, 2, 3):
+        if c4_window_bytes >= 4 * WIN_WORDS[minb]:
+            return WIN_WORDS[minb]
+    return WIN_WORDS[4]
 
 
 def _simple_edges(n, src, dst):
@@ -75,7 +83,7 @@ def _merged_windows(bounds, widths, mask, u, words):
     return total
 
 
-def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
+def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=100 * 1024):
     """Per-kernel work and algorithmic bytes (dict of dicts) under the given wedge plan fields."""
     G = rank_space(n, src, dst)
     m = G["m"]
@@ -127,7 +135,7 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=200 * 1024):
     dm = split
     # warp-local hash mode for W <= c4_warp_max, windowed counters above (no middle tier)
     tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= min(c4_warp_max, 512), 0, 2))
-    words = WIN_WORDS[2 if c4_window_bytes >= 4 * WIN_WORDS[2] else (3 if c4_window_bytes >= 4 * WIN_WORDS[3] else 4)]
+    words = window_words(c4_window_bytes)
     bounds = band_starts + [n]
     # narrow bands may merge into the next wider one: the mask with the fewest degree-weighted windows
     # over 64 roots spread evenly over the ranks of degree >= 64 (lowest mask on a tie)

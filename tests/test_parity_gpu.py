@@ -202,11 +202,12 @@ def test_async_entry_point_and_launch_count(harp):
 
 def test_large_grid_boundary_table(harp):
     """A grid of more than 15 windows per row keeps every 2^s-th boundary and finds the rest by a
-    galloping search: 2e6 vertices of degree >= 2 span about 30 windows of 48 KiB (and about 15 of
-    100 KiB); both agree with the oracle."""
+    galloping search: 2e6 vertices of degree >= 2 span about 30 windows of 48 KiB (about 15 of 100 KiB,
+    8 of 200 KiB); every window size (100 KiB for two 512-thread blocks per SM, the default; 200 KiB
+    for one 1024-thread block; 64 and 48 KiB for 3 and 4 blocks of 512) agrees with the oracle."""
     g = graphgen.chung_lu(2_000_000, 2.1, 3000, 4, 5)
     want = O.count4_combo(g.n, g.src, g.dst).tolist()
-    for bytes_ in (0, 49152):
+    for bytes_ in (0, 204800, 65536, 49152):
         p = harp.harp_plan()
         p.version = harp.HARP_ABI_VERSION
         p.c4_window_bytes = bytes_
