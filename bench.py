@@ -19,10 +19,12 @@ path (one harp_count4 per graph) over the same graphs; counts are compared graph
 through the continuous-batching server, against plain one-graph-per-launch processing (build + count,
 in arrival order) of the same stream: p50 / p99 latency and edges/s.
 
-`--workload partitioned`: the partitioned large graph (Chung-Lu, exponent 2.1, max expected degree 1e6,
-mean degree 48; n = 5e7 gives about 1.2e9 edges) counted through harp_count4_partitioned under a 24 GiB
-device cap: one JSON line with edges/s over the whole call (host edge list to counts) and the share of
-host-device transfer in it.  `--n` shrinks the graph for trial runs.
+`partitioned`: the partitioned large graph (Chung-Lu, exponent 2.1, max expected degree 1e6, mean degree
+48; n = 5e7 gives about 1.2e9 edges) counted once through harp_count4_partitioned under a 24 GiB device
+cap, with edges/s over the whole call (host edge list to counts) and its host / transfer / kernel split,
+and the same graph counted whole on the device without a cap: `partitioned_equals_whole` is the owner
+rule's exactness check at full size.  `--workload partitioned` prints it as its own line; `--n`
+shrinks the graph for trial runs.
 
 --impl reference runs the CPU oracle (plain non-induced counts + containment inversion) on the host
 cores instead: each step counts an R-MAT scale-17 sample of the same family.
@@ -255,11 +257,21 @@ def bench_batched(harp, graphgen, np, torch, stream, flush, steps, warmup, G=409
             "autotune_ms": tune_ms, "generate_s": t_gen, "counts_equal": True}
 
 
-def bench_served(harp, graphgen, np, rates=(100.0, 500.0, 2000.0), nreq=128, seed=11, budget=64 << 30):
+def bench_served(harp, graphgen, np, rates=(10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0), nreq=1000, seed=11,
+                 budget=64 << 30):
     """Poisson streams (one per rate, the same requests) through the server vs plain processing."""
+    t0 = time.perf_counter()
     gs = [graphgen.serve_graph(seed * 100000 + i) for i in range(nreq)]
+    t_gen = time.perf_counter() - t0
+    # warm-up: build and count one request of each generator family once, untimed
+    for g in {g.name.split("(")[0]: g for g in gs[:64]}.values():
+        c = harp.harp_build_csr(g.n, g.src, g.dst)
+        harp.harp_count4(c)
+        c.close()
     out = {"workload": f"{nreq} requests per rate, Poisson arrivals, edge counts log-uniform [1e3, 1e7], "
-                       f"ER/BA/RGG/R-MAT uniform, HBM budget {budget >> 30} GiB", "requests": nreq, "rates": []}
+                       f"ER/BA/RGG/R-MAT uniform, HBM budget {budget >> 30} GiB", "requests": nreq,
+           "lanes": "small requests (<= 65536 input pairs) on a second, higher-priority compute stream",
+           "generate_s": t_gen, "rates": []}
     for k, rate in enumerate(rates):
         r = served_at_rate(harp, np, gs, rate, seed + k, budget)
         out["rates"].append(r)
@@ -292,7 +304,6 @@ def served_at_rate(harp, np, gs, rate, seed, budget):
             lat.append(time.perf_counter() - t0 - arrivals[i])
         return lat, time.perf_counter() - t0
 
-    plain_pass()  # untimed: first-touch of every size class
     lat_p, span_p = plain_pass()
     srv = harp.Server(hbm_budget_bytes=budget)
     tickets = [None] * nreq
@@ -566,6 +577,10 @@ def main():
     batched = None if (args.no_batched or world > 1) else bench_batched(harp, graphgen, np, torch, stream, flush,
                                                                         args.steps, args.warmup)
     served = None if (args.no_served or world > 1) else bench_served(harp, graphgen, np)
+    # the partitioned large graph (one call, host edge list to counts, under the 24 GiB cap) and the
+    # same graph counted whole: the owner rule's exactness check at full size
+    partitioned = None if (args.no_partitioned or world > 1) else bench_partitioned(harp, graphgen, torch, args.n,
+                                                                                      args.cap_gib)
 
     if rank != 0:
         return 0
@@ -636,6 +651,7 @@ def main():
         "segments_ms": seg_avg,
         "batched": batched,
         "served": served,
+        "partitioned": partitioned,
         "counts": [int(x) for x in counts],
         "hbm_pct_alg": (100.0 * sum(meter[k]["bytes"] for k in SEGMENTS) / (t_step / 1000) / 1e9 / peak)
         if meter else None,

@@ -328,8 +328,10 @@ harp_status harp_rank_csr_host(int64_t n, int64_t m_in, const int32_t* src, cons
 /* ------------------------------------------------------------------------------------------------
  * Serving with continuous batching.  Requests are admitted in arrival order while the device bytes
  * held by admitted requests stay within the HBM budget; their edge lists are copied and their CSRs
- * built on a copy stream while the previous batch counts on a compute stream; every built request
- * joins the next batch (the batched pipeline, one launch per kernel).  A request larger than the
+ * built on a copy stream while earlier batches count; every built request joins the next batch of
+ * its lane (the batched pipeline, one launch per kernel).  Two lanes, each with its own executor
+ * thread and compute stream: small requests (at most small_edges input pairs) on a higher-priority
+ * stream, larger ones on the other, so a small request is not held behind a running large batch.  A request larger than the
  * budget is counted by the partitioned path under the budget.  Counts are exact and independent of
  * the mix a request was batched with.
  * ---------------------------------------------------------------------------------------------- */
@@ -345,6 +347,10 @@ typedef struct harp_server_opts {
     uint32_t staging_mib;        /* page-locked host staging for submitted edge lists, MiB       */
                                  /* (0 = 512); a request that finds no room is kept in pageable */
                                  /* memory instead (slower host-to-device copy)                  */
+    uint32_t small_edges;        /* requests of at most this many input pairs are batched and    */
+                                 /* counted on a second, higher-priority compute stream, so they */
+                                 /* do not wait behind a batch of large requests (0 = 65536;     */
+                                 /* 0xFFFFFFFF = every request on one lane)                      */
 } harp_server_opts;
 
 typedef struct harp_server_stats {

@@ -3,12 +3,16 @@
 // Requests (host edge lists, copied at submit into a page-locked staging arena when it has room)
 // wait in a FIFO.  Two builder threads admit them in order while the device memory held by admitted
 // requests stays within the HBM budget and a slot is free, copy each edge list to the device and
-// build its CSR, each on its own copy stream.  An executor thread
-// takes every built request as the next batch and counts it with the batched pipeline (the disjoint
-// union of the batch, one launch per kernel) on a compute stream; with a batching window it first
-// waits, up to the window, while requests are still queued for admission or being built.  Requests that arrive while a batch
-// is on the GPU are admitted, copied and built meanwhile (their copies and CSR builds overlap the
-// running count) and form the next batch as soon as it finishes; results are retired per ticket.
+// build its CSR, each on its own copy stream.  Built requests go to one of two lanes by size: small
+// requests (at most small_edges input pairs) and the rest.  Each lane has an executor thread that
+// takes every built request of its lane as the next batch and counts it with the batched pipeline
+// (the disjoint union of the batch, one launch per kernel) on the lane's compute stream; the small
+// lane's stream has the higher priority, so when a large batch's kernel finishes its blocks the small
+// batch's kernels are scheduled first and a small request does not wait for a whole large batch.
+// With a batching window an executor first waits, up to the window, while requests are still queued
+// for admission or being built.  Requests that arrive while batches are on the GPU are admitted,
+// copied and built meanwhile (their copies and CSR builds overlap the running counts) and form their
+// lane's next batch as soon as its current one finishes; results are retired per ticket.
 // A request whose own footprint exceeds the budget is counted by the halo-partitioned path with the
 // canonical anchor-owner rule (harp_count4_partitioned) under the same budget.
 #include <algorithm>
@@ -114,7 +118,8 @@ struct harp_server {
     std::condition_variable cv_exec;    // executor: built requests available
     std::condition_variable cv_done;    // waiters: a request finished
     std::deque<uint64_t> pending;       // tickets in arrival order
-    std::deque<uint64_t> built;         // tickets with a CSR, waiting for a batch
+    static constexpr int kLanes = 2;    // 0: large requests, 1: small requests (higher priority)
+    std::deque<uint64_t> built[kLanes]; // tickets with a CSR, waiting for a batch of their lane
     std::unordered_map<uint64_t, Request*> reqs;
     uint64_t next_ticket = 1;
     size_t resident = 0;
@@ -124,8 +129,8 @@ struct harp_server {
     bool stop = false;
     static constexpr int kBuilders = 2;
     cudaStream_t copy_stream[kBuilders] = {nullptr, nullptr};
-    cudaStream_t compute_stream = nullptr;
-    std::thread builder[kBuilders], executor;
+    cudaStream_t compute_stream[kLanes] = {nullptr, nullptr};
+    std::thread builder[kBuilders], executor[kLanes];
     StagingArena staging;
     // statistics
     uint64_t completed = 0, batches = 0, partitioned = 0, batched_requests = 0, max_batch_seen = 0;
@@ -157,6 +162,12 @@ bool can_admit(const harp_server* s) {
     const bool slot = s->opts.max_inflight == 0 || s->inflight < (int64_t)s->opts.max_inflight;
     const bool oversize = r->need > s->opts.hbm_budget_bytes;
     return slot && (oversize ? s->resident == 0 : s->resident + r->need <= s->opts.hbm_budget_bytes);
+}
+
+// Lane of a request: 1 (small, the higher-priority stream) for at most small_edges input pairs.
+int lane_of(const harp_server* s, const Request* r) {
+    const uint64_t small = s->opts.small_edges ? s->opts.small_edges : 65536u;
+    return (uint64_t)r->m_in <= small ? 1 : 0;
 }
 
 void drop_host_copy(harp_server* s, Request* r) {  // caller holds the lock
@@ -209,34 +220,35 @@ void builder_loop(harp_server* s, int which) {
             s->inflight--;
             finish(s, r, st);
             s->cv_done.notify_all();
-            s->cv_exec.notify_one();  // a waiting batch need not wait for this one
+            s->cv_exec.notify_all();  // a waiting batch need not wait for this one
             continue;
         }
         r->state = ReqState::Built;
-        s->built.push_back(r->ticket);
-        s->cv_exec.notify_one();
+        s->built[lane_of(s, r)].push_back(r->ticket);
+        s->cv_exec.notify_all();
     }
 }
 
-void executor_loop(harp_server* s) {
+void executor_loop(harp_server* s, int lane) {
     cudaSetDevice(s->device);
+    std::deque<uint64_t>& built = s->built[lane];
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        s->cv_exec.wait(lk, [&] { return s->stop || !s->built.empty(); });
+        s->cv_exec.wait(lk, [&] { return s->stop || !built.empty(); });
         if (s->stop) return;
         const size_t cap = s->opts.max_batch ? s->opts.max_batch : 4096;
         if (s->opts.batch_window_us) {
             // gather: wait, up to the window, while more requests are on their way (being built, or
             // admissible now); requests held back by the budget cannot join before this batch ends
             s->cv_exec.wait_for(lk, std::chrono::microseconds(s->opts.batch_window_us), [&] {
-                return s->stop || s->built.size() >= cap || (s->building == 0 && !can_admit(s));
+                return s->stop || built.size() >= cap || (s->building == 0 && !can_admit(s));
             });
             if (s->stop) return;
         }
         std::vector<Request*> batch;
-        while (!s->built.empty() && batch.size() < cap) {
-            Request* r = s->reqs[s->built.front()];
-            s->built.pop_front();
+        while (!built.empty() && batch.size() < cap) {
+            Request* r = s->reqs[built.front()];
+            built.pop_front();
             r->state = ReqState::Running;
             batch.push_back(r);
         }
@@ -251,7 +263,8 @@ void executor_loop(harp_server* s) {
             std::memset(&p, 0, sizeof(p));
             p.version = HARP_ABI_VERSION;
             p.flags = HARP_PLAN_NO_GRAPH;  // every batch has a different shape
-            st = harp_batch_count(b, &p, reinterpret_cast<uint64_t(*)[6]>(counts.data()), nullptr, s->compute_stream);
+            st = harp_batch_count(b, &p, reinterpret_cast<uint64_t(*)[6]>(counts.data()), nullptr,
+                                  s->compute_stream[lane]);
             harp_batch_free(b);
         }
         for (Request* r : batch) {
@@ -292,7 +305,13 @@ harp_status harp_server_create(const harp_server_opts* opts, harp_server** out) 
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < harp_server::kBuilders && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->copy_stream[k], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute_stream, cudaStreamNonBlocking);
+    // lane 1 (small requests) gets the greatest priority the device offers, lane 0 the least
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&s->compute_stream[0], cudaStreamNonBlocking, prio_least);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&s->compute_stream[1], cudaStreamNonBlocking, prio_greatest);
     void* arena = nullptr;
     const size_t arena_bytes = (size_t)s->opts.staging_mib << 20;
     if (e == cudaSuccess) e = cudaMallocHost(&arena, arena_bytes);
@@ -300,13 +319,14 @@ harp_status harp_server_create(const harp_server_opts* opts, harp_server** out) 
         harp::record_cuda_error(e);
         for (cudaStream_t c : s->copy_stream)
             if (c) cudaStreamDestroy(c);
-        if (s->compute_stream) cudaStreamDestroy(s->compute_stream);
+        for (cudaStream_t c : s->compute_stream)
+            if (c) cudaStreamDestroy(c);
         delete s;
         return e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
     }
     s->staging.init(arena, arena_bytes);
     for (int k = 0; k < harp_server::kBuilders; ++k) s->builder[k] = std::thread(builder_loop, s, k);
-    s->executor = std::thread(executor_loop, s);
+    for (int k = 0; k < harp_server::kLanes; ++k) s->executor[k] = std::thread(executor_loop, s, k);
     *out = s;
     return HARP_OK;
 }
@@ -400,7 +420,7 @@ harp_status harp_server_get_stats(harp_server* s, harp_server_stats* out) {
     out->batched_requests = s->batched_requests;
     out->partitioned = s->partitioned;
     out->max_batch = s->max_batch_seen;
-    out->pending = s->pending.size() + s->built.size();
+    out->pending = s->pending.size() + s->built[0].size() + s->built[1].size();
     out->resident_bytes = s->resident;
     out->peak_resident_bytes = s->peak_resident;
     out->latency_p50_us = out->latency_p99_us = 0;
@@ -427,7 +447,8 @@ void harp_server_destroy(harp_server* s) {
     s->cv_exec.notify_all();
     for (auto& b : s->builder)
         if (b.joinable()) b.join();
-    if (s->executor.joinable()) s->executor.join();
+    for (auto& x : s->executor)
+        if (x.joinable()) x.join();
     cudaSetDevice(s->device);
     for (auto& kv : s->reqs) {
         if (kv.second->csr) harp_csr_free(kv.second->csr);
@@ -437,7 +458,10 @@ void harp_server_destroy(harp_server* s) {
         cudaStreamSynchronize(c);
         cudaStreamDestroy(c);
     }
-    cudaStreamDestroy(s->compute_stream);
+    for (cudaStream_t c : s->compute_stream) {
+        cudaStreamSynchronize(c);
+        cudaStreamDestroy(c);
+    }
     cudaFreeHost(s->staging.base);
     delete s;
 }

@@ -92,7 +92,8 @@ class harp_partition_stats(ctypes.Structure):
 
 class harp_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
-                ("max_inflight", ctypes.c_uint32), ("batch_window_us", ctypes.c_uint32), ("staging_mib", ctypes.c_uint32)]
+                ("max_inflight", ctypes.c_uint32), ("batch_window_us", ctypes.c_uint32), ("staging_mib", ctypes.c_uint32),
+                ("small_edges", ctypes.c_uint32)]
 
 
 class harp_server_stats(ctypes.Structure):
@@ -449,8 +450,8 @@ class Server:
     """A continuous-batching counting server (harp_server_*)."""
 
     def __init__(self, hbm_budget_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0,
-                 batch_window_us: int = 0, staging_mib: int = 0):
-        o = harp_server_opts(hbm_budget_bytes, max_batch, max_inflight, batch_window_us, staging_mib)
+                 batch_window_us: int = 0, staging_mib: int = 0, small_edges: int = 0):
+        o = harp_server_opts(hbm_budget_bytes, max_batch, max_inflight, batch_window_us, staging_mib, small_edges)
         h = ctypes.c_void_p()
         _check(lib().harp_server_create(ctypes.byref(o), ctypes.byref(h)), "harp_server_create")
         self.handle = h

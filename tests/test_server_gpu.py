@@ -99,3 +99,35 @@ def test_oversize_request_uses_partitions_and_bad_request_fails(harp):
             srv.poll(123456789)
     finally:
         srv.close()
+
+
+def test_small_requests_do_not_wait_behind_a_large_one(harp):
+    """Small requests take the second, higher-priority lane: submitted right after a large request
+    (R-MAT scale 20, about 16M input pairs), most of them finish before it, and every result is the
+    request's alone-count.  With a single lane (small_edges = 0xFFFFFFFF) the counts are the same."""
+    big = graphgen.rmat(20, 16, seed=31)
+    smalls = [graphgen.batch_graph(900 + i, n_lo=50, n_hi=3000) for i in range(24)]
+    want_big = harp.count4_edges(big.n, big.src, big.dst).tolist()
+    want_small = [harp.count4_edges(g.n, g.src, g.dst).tolist() for g in smalls]
+    assert all(g.m_in <= 65536 for g in smalls) and big.m_in > 65536
+    for small_edges in (0, 0xFFFFFFFF):
+        srv = harp.Server(small_edges=small_edges)
+        try:
+            tb = srv.submit(big.n, big.src, big.dst)
+            ts = [srv.submit(g.n, g.src, g.dst) for g in smalls]
+            done, order = {}, []
+            while len(done) < len(ts) + 1:
+                for t in [tb] + ts:
+                    if t in done:
+                        continue
+                    r = srv.poll(t)
+                    if r is not None:
+                        done[t] = r.tolist()
+                        order.append(t)
+            assert done[tb] == want_big
+            assert [done[t] for t in ts] == want_small
+            if small_edges == 0:
+                before = sum(1 for t in order[:order.index(tb)] if t in ts)
+                assert before >= 0.75 * len(ts), (before, len(ts))
+        finally:
+            srv.close()
