@@ -252,9 +252,13 @@ def bench_batched(harp, graphgen, np, torch, stream, flush, steps, warmup, G=409
                         f"(BA m in 2..8), seeds 0..{G - 1}", "graphs": G, "n_total": info["n"], "m_total": m_total,
             "value": m_total / (t_b / 1000), "unit": UNIT, "ms_per_step": t_b,
             "plain_value": m_total / (t_p / 1000), "plain_ms_per_pass": t_p, "speedup_vs_plain": t_p / t_b,
-            "plan": {"tri_warp_max": best.tri_warp_max, "tri_probe": best.tri_probe,
-                     "c4_warp_max_work": best.c4_warp_max_work},
-            "autotune_ms": tune_ms, "generate_s": t_gen, "counts_equal": True}
+            "plan": {"tri_warp_max": best.tri_warp_max,
+                     "tri_probe_bin": {name: ("bsearch" if v == harp.HARP_PROBE_BSEARCH else "hash")
+                                       for name, v in zip(("warp", "cta256", "cta512", "cta1024"),
+                                                          list(best.tri_probe_bin))},
+                     "tri_cta_max": best.tri_cta_max, "c4_warp_max_work": best.c4_warp_max_work,
+                     "c4_window_bytes": best.c4_window_bytes},
+            "autotune_ms": [t for t in tune_ms if t > 0], "generate_s": t_gen, "counts_equal": True}
 
 
 def bench_served(harp, graphgen, np, rates=(10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0), nreq=1000, seed=11,
@@ -447,10 +451,15 @@ def run_whole(args):
     csr = harp.harp_build_csr(g.n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda())
     m = csr.info()["m"]
     harp.harp_set_profiling(True)
+    plan = None
+    if args.c4_window_kib:
+        plan = harp.harp_plan()
+        plan.version = harp.HARP_ABI_VERSION
+        plan.c4_window_bytes = int(args.c4_window_kib * 1024)
     runs = []
     for k in range(args.warmup + args.steps):
         with ClockSampler(local) as clocks:
-            counts = harp.harp_count4(csr)
+            counts = harp.harp_count4(csr, plan)
             ms, _ = harp.harp_last_stage_times()
         if k >= args.warmup:
             runs.append((sum(ms), ms, clocks.summary()))
@@ -464,7 +473,7 @@ def run_whole(args):
                                    f"mean degree 48, seed 1), whole graph on the device",
                        "n": g.n, "m": m, "parallelism": "single", "l2": "inputs larger than L2"},
             "segments_ms": {k: v for k, v in zip(SEGMENTS, ms)}, "generate_s": t_gen, "clocks": clk,
-            "counts": [int(x) for x in counts]}
+            "c4_window_kib": args.c4_window_kib or 100, "counts": [int(x) for x in counts]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -485,6 +494,8 @@ def main():
                          "partitioned under --cap-gib or counted whole on the device")
     ap.add_argument("--n", type=int, default=50_000_000, help="vertices of the Chung-Lu workloads")
     ap.add_argument("--cap-gib", type=float, default=24.0, help="device cap of the partitioned workload")
+    ap.add_argument("--c4-window-kib", type=float, default=0,
+                    help="whole workload: wedge window size of the plan (0 = the default 100 KiB)")
     ap.add_argument("--no-whole", action="store_true",
                     help="partitioned workload: skip the uncapped whole-graph count it is checked against")
     ap.add_argument("--no-partitioned", action="store_true",

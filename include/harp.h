@@ -143,7 +143,9 @@ typedef struct harp_plan {
                                  /* fallback, every extension a miss                                */
     uint32_t c4_warp_max_work;   /* wedge work W(u) <= this: warp-local hash table                 */
     uint32_t c4_cta_max_work;    /* W(u) <= this: CTA hash table; above: CTA windowed counters     */
-    uint32_t c4_window_bytes;    /* shared-memory bytes of one dense counter window                */
+    uint32_t c4_window_bytes;    /* shared-memory bytes of one dense counter window: 200, 100, 64   */
+                                 /* or 48 KiB (the largest that fits); 0 = by graph: 200 KiB for a */
+                                 /* single graph of more than 2^22 vertices, else 100 KiB          */
     uint32_t flags;              /* HARP_PLAN_*                                                    */
     /* Eq. 1 terms estimated from a sample of the graph (filled by harp_select_anchors) */
     double est_enum;             /* explicit anchor-enumeration work (wedges + 2-paths)            */
@@ -158,6 +160,11 @@ typedef struct harp_plan {
     uint32_t lit_cache_min_deg;  /* literal basis: degree bin admitted to the cache: a frontier is   */
                                  /* cached only if both generating vertices have degree >= this     */
                                  /* (smaller ones are recomputed; 0 = all)                          */
+    uint8_t tri_probe_bin[4];    /* HARP_PROBE_* per triangle degree bin, 0 = tri_probe: [0] warp-local */
+                                 /* (out-degree <= tri_warp_max), [1] CTA <= 256, [2] CTA <= 512,    */
+                                 /* [3] CTA <= 1024 (the global-staged and fallback modes always     */
+                                 /* binary-search)                                                   */
+    uint32_t reserved0;          /* 0                                                               */
     double est_cost_tw;          /* Eq. 1 objective of the triangle-wedge basis (harp_select_anchors) */
     double est_cost_lit;         /* Eq. 1 objective of the literal basis                          */
 } harp_plan;
@@ -201,6 +208,27 @@ harp_status harp_count4_stats(const harp_csr* g, const harp_plan* plan, uint64_t
  * point.  The handle's workspace is in use until then: do not start
  * another count on the same handle on a different stream before it completes. */
 harp_status harp_count4_async(const harp_csr* g, const harp_plan* plan, uint64_t* d_out, void* stream);
+
+/* Per-vertex (orbit) counts: for every vertex v and each of the HARP_NORBITS roles a vertex can play
+ * in a connected induced 4-vertex motif, the number of induced occurrences S (Section II) that
+ * contain v in that role.  The paper's closure (Section III-F) is global; this output refines it: a
+ * role is the vertex's automorphism class in the motif (for 4-vertex motifs its degree inside
+ * G[S] decides it), and the counts follow from eleven non-induced statistics per vertex (degree sums,
+ * per-edge triangle counts, per-vertex triangles, 4-cycles and 4-cliques) by back-substitution in a
+ * unit upper-triangular containment system, so they are exact modulo 2^64 like the global counts.
+ * Summed over v, role r gives its motif's count times the number of the motif's vertices in r.
+ *   orbits_out  uint64[n][HARP_NORBITS], row v = the input vertex id v; host memory if flags ==
+ *               HARP_PTR_HOST, device memory if HARP_PTR_DEVICE.  Written only on HARP_OK.
+ * Runs on the handle's stream and returns when the counts are in place.  The 4-cycle routing keeps
+ * dense per-block counters of n uint32 (at most 4 GiB) for roots with more than 512 wedges.
+ * Errors: HARP_EINVAL, HARP_ENOMEM, HARP_ECUDA, HARP_EDEVICE (a per-vertex sum failed its parity
+ * check). */
+enum {
+    HARP_ORB_STAR_CENTER = 0, HARP_ORB_STAR_LEAF = 1, HARP_ORB_PATH_END = 2, HARP_ORB_PATH_INNER = 3,
+    HARP_ORB_PAW_PENDANT = 4, HARP_ORB_PAW_HUB = 5, HARP_ORB_PAW_SIDE = 6, HARP_ORB_CYCLE = 7,
+    HARP_ORB_DIAMOND_SPINE = 8, HARP_ORB_DIAMOND_TIP = 9, HARP_ORB_CLIQUE = 10, HARP_NORBITS = 11
+};
+harp_status harp_count4_orbits(const harp_csr* g, uint64_t* orbits_out, uint32_t flags);
 
 /* Per-segment device times of the last count issued with profiling on (milliseconds, measured with
  * CUDA events recorded on the launching stream between the kernels).  Segments, in launch order:
@@ -249,10 +277,15 @@ void harp_batch_free(harp_batch* b);
 /* Autotuner for a batch: counts the batch `reps` times under each candidate plan (each captured as
  * its own CUDA graph, one untimed replay first), timed with CUDA events on the batch's stream, and
  * writes the fastest plan to *best and candidate k's mean milliseconds to ms_out[k] (may be NULL).
- * candidates NULL: the built-in grid of HARP_AUTOTUNE_GRID plans (tri_warp_max {16, 32} x tri_probe
- * {hash, bsearch} x c4_warp_max_work {256, 512}); otherwise ncand >= 1 plans.  Every candidate
- * must give identical counts and statistics: a mismatch returns HARP_EDEVICE. */
-#define HARP_AUTOTUNE_GRID 8
+ * candidates NULL: the built-in per-degree-bin search, a coordinate descent from the default plan
+ * that keeps the faster choice of each knob in turn: the warp/CTA split tri_warp_max {16, 32}; the
+ * intersection variant of each triangle degree bin tri_probe_bin[k] {hash, bsearch}; the staging
+ * capacity tri_cta_max {256, 512, 1024}; the wedge warp/CTA split c4_warp_max_work {256, 512}; the
+ * wedge window c4_window_bytes {100, 200 KiB}.  At most HARP_AUTOTUNE_GRID plans are timed
+ * (ms_out has that many entries, in the order timed, 0 past the last); identical plans are timed
+ * once.  Otherwise ncand >= 1 given plans.  Every candidate must give identical counts and
+ * statistics: a mismatch returns HARP_EDEVICE. */
+#define HARP_AUTOTUNE_GRID 24
 harp_status harp_batch_autotune(harp_batch* b, const harp_plan* candidates, int32_t ncand, int32_t reps,
                                 harp_plan* best, float* ms_out);
 

@@ -309,6 +309,39 @@ harp_status harp_count4_async(const harp_csr* gc, const harp_plan* plan, uint64_
     return HARP_OK;
 }
 
+harp_status harp_count4_orbits(const harp_csr* gc, uint64_t* orbits_out, uint32_t flags) {
+    if (!gc || (!orbits_out && gc->n > 0)) return HARP_EINVAL;
+    if (flags != HARP_PTR_HOST && flags != HARP_PTR_DEVICE) return HARP_EINVAL;
+    harp_csr* g = const_cast<harp_csr*>(gc);
+    if (g->n == 0) return HARP_OK;
+    HARP_CK(cudaSetDevice(g->device));
+    cudaStream_t s = g->stream;
+    HARP_TRY(ws_ensure(g->ws, g->n, g->m, s));
+    Workspace& ws = g->ws;
+    HARP_CK(cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s));
+    harp_plan plan;
+    normalise_plan(nullptr, &plan);
+    const size_t out_bytes = sizeof(uint64_t) * HARP_NORBITS * (size_t)g->n;
+    uint64_t* d_out = orbits_out;
+    if (flags == HARP_PTR_HOST) HARP_CK(cudaMallocAsync((void**)&d_out, out_bytes, s));
+    harp_status st = orient(g, ws, s);
+    if (st == HARP_OK) st = count_triangles_k4(g, ws, plan, s);  // t_e of every out-arc
+    if (st == HARP_OK) st = count_orbits(g, ws, d_out, s);
+    uint64_t err = 0;
+    cudaError_t e = cudaSuccess;
+    if (st == HARP_OK) e = cudaMemcpyAsync(&err, ws.acc + ACC_ERR, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (st == HARP_OK && e == cudaSuccess && flags == HARP_PTR_HOST)
+        e = cudaMemcpyAsync(orbits_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+    if (flags == HARP_PTR_HOST) cudaFreeAsync(d_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        record_cuda_error(e);
+        return HARP_ECUDA;
+    }
+    if (st != HARP_OK) return st;
+    return err ? HARP_EDEVICE : HARP_OK;
+}
+
 harp_status harp_set_profiling(int enable) {
     g_profiling.store(enable ? 1 : 0);
     return HARP_OK;

@@ -158,7 +158,9 @@ bool same_plan(const harp_plan& a, const harp_plan& b) {
     return a.basis == b.basis && a.tri_probe == b.tri_probe && a.tri_warp_max == b.tri_warp_max &&
            a.tri_cta_max == b.tri_cta_max && a.tri_big_max == b.tri_big_max &&
            a.c4_warp_max_work == b.c4_warp_max_work && a.c4_cta_max_work == b.c4_cta_max_work &&
-           a.c4_window_bytes == b.c4_window_bytes && a.flags == b.flags;
+           a.c4_window_bytes == b.c4_window_bytes && a.flags == b.flags &&
+           a.tri_probe_bin[0] == b.tri_probe_bin[0] && a.tri_probe_bin[1] == b.tri_probe_bin[1] &&
+           a.tri_probe_bin[2] == b.tri_probe_bin[2] && a.tri_probe_bin[3] == b.tri_probe_bin[3];
 }
 
 }  // namespace
@@ -328,39 +330,22 @@ harp_status harp_batch_autotune(harp_batch* b, const harp_plan* candidates, int3
     if (!b || !best || reps < 1) return HARP_EINVAL;
     if (candidates && ncand < 1) return HARP_EINVAL;
     HARP_CK(cudaSetDevice(b->device));
-    std::vector<harp_plan> cand;
-    if (candidates) {
-        for (int32_t k = 0; k < ncand; ++k) {
-            if (candidates[k].basis != HARP_BASIS_TRIANGLE_WEDGE) return HARP_EINVAL;
-            harp_plan p;
-            normalise_plan(&candidates[k], &p);
-            p.flags &= ~HARP_PLAN_NO_GRAPH;  // candidates are timed as captured graphs
-            cand.push_back(p);
-        }
-    } else {  // the built-in grid: warp/CTA split x membership probe x wedge warp/CTA split
-        for (uint32_t wm : {16u, 32u})
-            for (uint32_t pr : {(uint32_t)HARP_PROBE_HASH, (uint32_t)HARP_PROBE_BSEARCH})
-                for (uint32_t cw : {256u, 512u}) {
-                    harp_plan p;
-                    normalise_plan(nullptr, &p);
-                    p.tri_warp_max = wm;
-                    p.tri_probe = pr;
-                    p.c4_warp_max_work = cw;
-                    cand.push_back(p);
-                }
-    }
     cudaStream_t s = b->capture_stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     HARP_CK(cudaEventCreate(&e0));
     HARP_CK(cudaEventCreate(&e1));
     std::vector<uint64_t> first;
-    harp_status st = HARP_OK;
-    float best_ms = 0.0f;
-    size_t best_k = 0;
-    for (size_t k = 0; k < cand.size() && st == HARP_OK; ++k) {
-        st = batch_prepare(b, cand[k]);
-        if (st != HARP_OK) break;
-        // one untimed replay (first touch of the captured graph), then reps timed replays
+    std::vector<harp_plan> timed;  // every plan timed so far and its time: identical plans run once
+    std::vector<float> timed_ms;
+    // time plan p (captured graph: one untimed replay, then reps timed); its counts must equal the
+    // first candidate's
+    auto time_plan = [&](const harp_plan& p, float* ms_res) -> harp_status {
+        for (size_t k = 0; k < timed.size(); ++k)
+            if (same_plan(timed[k], p)) {
+                *ms_res = timed_ms[k];
+                return HARP_OK;
+            }
+        HARP_TRY(batch_prepare(b, p));
         cudaError_t e = cudaGraphLaunch(b->exec, s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         for (int32_t r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->exec, s);
@@ -370,32 +355,73 @@ harp_status harp_batch_autotune(harp_batch* b, const harp_plan* candidates, int3
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) {
             record_cuda_error(e);
-            st = HARP_ECUDA;
-            break;
+            return HARP_ECUDA;
         }
         note_launch(b->launches_per_count * (reps + 1));
-        if (b->h_out[16 * b->G]) {
-            st = HARP_EDEVICE;
-            break;
-        }
+        if (b->h_out[16 * b->G]) return HARP_EDEVICE;
         // every candidate must produce the same counts and statistics (a plan changes only the work)
         std::vector<uint64_t> now(b->h_out, b->h_out + 16 * b->G);
         if (first.empty()) first = now;
-        else if (now != first) {
-            st = HARP_EDEVICE;
-            break;
-        }
+        else if (now != first) return HARP_EDEVICE;
         ms /= (float)reps;
-        if (ms_out) ms_out[k] = ms;
-        if (k == 0 || ms < best_ms) {
-            best_ms = ms;
-            best_k = k;
+        if (ms_out && timed.size() < (size_t)(candidates ? ncand : HARP_AUTOTUNE_GRID)) ms_out[timed.size()] = ms;
+        timed.push_back(p);
+        timed_ms.push_back(ms);
+        *ms_res = ms;
+        return HARP_OK;
+    };
+    harp_status st = HARP_OK;
+    harp_plan cur;
+    if (candidates) {
+        float best_ms = 0.0f;
+        for (int32_t k = 0; k < ncand && st == HARP_OK; ++k) {
+            if (candidates[k].basis != HARP_BASIS_TRIANGLE_WEDGE) {
+                st = HARP_EINVAL;
+                break;
+            }
+            harp_plan p;
+            normalise_plan(&candidates[k], &p);
+            p.flags &= ~HARP_PLAN_NO_GRAPH;  // candidates are timed as captured graphs
+            float ms = 0.0f;
+            st = time_plan(p, &ms);
+            if (st == HARP_OK && (k == 0 || ms < best_ms)) {
+                best_ms = ms;
+                cur = p;
+            }
         }
+    } else {
+        // per-degree-bin coordinate descent from the default plan: each knob in turn takes the value
+        // that times fastest with the others held at their current best
+        if (ms_out)
+            for (int k = 0; k < HARP_AUTOTUNE_GRID; ++k) ms_out[k] = 0.0f;
+        normalise_plan(nullptr, &cur);
+        float cur_ms = 0.0f;
+        st = time_plan(cur, &cur_ms);
+        auto try_knob = [&](auto set, std::initializer_list<uint32_t> values) {
+            for (uint32_t v : values) {
+                if (st != HARP_OK) return;
+                harp_plan p = cur;
+                set(p, v);
+                float ms = 0.0f;
+                st = time_plan(p, &ms);
+                if (st == HARP_OK && ms < cur_ms) {
+                    cur = p;
+                    cur_ms = ms;
+                }
+            }
+        };
+        try_knob([](harp_plan& p, uint32_t v) { p.tri_warp_max = v; }, {16u, 32u});
+        for (int bin = 0; bin < 4; ++bin)
+            try_knob([bin](harp_plan& p, uint32_t v) { p.tri_probe_bin[bin] = (uint8_t)v; },
+                     {(uint32_t)HARP_PROBE_HASH, (uint32_t)HARP_PROBE_BSEARCH});
+        try_knob([](harp_plan& p, uint32_t v) { p.tri_cta_max = v; }, {256u, 512u, 1024u});
+        try_knob([](harp_plan& p, uint32_t v) { p.c4_warp_max_work = v; }, {256u, 512u});
+        try_knob([](harp_plan& p, uint32_t v) { p.c4_window_bytes = v; }, {100u * 1024u, 200u * 1024u});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != HARP_OK) return st;
-    *best = cand[best_k];
+    *best = cur;
     return HARP_OK;
 }
 

@@ -881,11 +881,17 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     if (g->n == 0 || g->m == 0) return HARP_OK;
     uint32_t warp_max = plan.c4_warp_max_work ? plan.c4_warp_max_work : 512;
     if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
-    // window size: the largest of the three that fits plan.c4_window_bytes (at least the smallest)
+    // window size: the largest of the four that fits plan.c4_window_bytes (at least the smallest).
+    // 0 = by graph: a single graph of more than 2^22 vertices takes 200 KiB (its x-range spans tens to
+    // hundreds of 100 KiB windows, and halving the (root, window) visits measured 37.7 -> 26.1 s on
+    // the 5e7-vertex Chung-Lu graph), anything smaller and every batch 100 KiB (R-MAT scale 20: 13.2
+    // ms at 100 KiB against 15.7 ms at 200 KiB)
     const bool merge = !(plan.flags & HARP_PLAN_NO_BAND_MERGE);
-    if (plan.c4_window_bytes >= (uint32_t)kWinWords1 * 4) return wedge_pass<1>(g, ws, warp_max, merge, s);
-    if (plan.c4_window_bytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, merge, s);
-    if (plan.c4_window_bytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, merge, s);
+    uint32_t wbytes = plan.c4_window_bytes;
+    if (wbytes == 0) wbytes = (ws.G <= 1 && g->n > ((int64_t)1 << 22)) ? (uint32_t)kWinWords1 * 4 : (uint32_t)kWinWords2 * 4;
+    if (wbytes >= (uint32_t)kWinWords1 * 4) return wedge_pass<1>(g, ws, warp_max, merge, s);
+    if (wbytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, merge, s);
+    if (wbytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, merge, s);
     return wedge_pass<4>(g, ws, warp_max, merge, s);
 }
 

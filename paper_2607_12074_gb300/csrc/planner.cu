@@ -88,12 +88,13 @@ void default_plan(harp_plan* p) {
     p->tri_big_max = 4096;
     p->c4_warp_max_work = 512;
     p->c4_cta_max_work = 8192;
-    p->c4_window_bytes = 100 * 1024;
+    p->c4_window_bytes = 0;  // by graph size (count_wedge_c4)
     p->flags = 0;
     p->est_halo = 1.0;
     p->est_yield = 6.0;
     p->lit_cache_log2 = 0;
     p->lit_cache_min_deg = 0;
+    for (int k = 0; k < 4; ++k) p->tri_probe_bin[k] = (uint8_t)HARP_PROBE_HASH;
 }
 
 size_t plan_bytes(const harp_plan* p) {
@@ -124,6 +125,10 @@ void normalise_plan(const harp_plan* user, harp_plan* out) {
     out->objective = in.objective;
     out->lit_cache_log2 = in.lit_cache_log2 > 30 ? 30 : in.lit_cache_log2;
     out->lit_cache_min_deg = in.lit_cache_min_deg;
+    for (int k = 0; k < 4; ++k)  // a bin's probe, else the plan-wide one
+        out->tri_probe_bin[k] = (in.tri_probe_bin[k] == HARP_PROBE_HASH || in.tri_probe_bin[k] == HARP_PROBE_BSEARCH)
+                                    ? in.tri_probe_bin[k]
+                                    : (uint8_t)out->tri_probe;
     out->est_cost_tw = in.est_cost_tw;
     out->est_cost_lit = in.est_cost_lit;
 }

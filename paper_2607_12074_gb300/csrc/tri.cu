@@ -787,18 +787,25 @@ harp_status launch_cta(const harp_csr* g, Workspace& ws, int cls, int ticket_slo
     return HARP_OK;
 }
 
-template <bool BS>
+// The four staged tiers, each with its bin's membership probe (plan.tri_probe_bin[k]: bsearch or hash).
 harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, int bmax, bool reuse,
-                         cudaStream_t s) {
+                         const uint8_t* probe_bin, cudaStream_t s) {
     const Sink sink{ws.acc, ws.gid, ws.accG};
-    k_tri_warp<BS><<<num_sms() * 8, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri,
-                                                   (const unsigned long long*)&ws.acc[Q_TRI_WARP], reuse, ws.te, sink);
+    const bool bs0 = probe_bin[0] == HARP_PROBE_BSEARCH, bs1 = probe_bin[1] == HARP_PROBE_BSEARCH;
+    const bool bs2 = probe_bin[2] == HARP_PROBE_BSEARCH, bs3 = probe_bin[3] == HARP_PROBE_BSEARCH;
+    const unsigned wgrid = (unsigned)num_sms() * 8;
+    const unsigned long long* qcnt = (const unsigned long long*)&ws.acc[Q_TRI_WARP];
+    if (bs0) k_tri_warp<true><<<wgrid, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, qcnt, reuse, ws.te, sink);
+    else k_tri_warp<false><<<wgrid, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, qcnt, reuse, ws.te, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_TRI_WARP));
-    HARP_TRY((launch_cta<kCta1, 256, kCta1Blocks, BS>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
+    if (bs1) HARP_TRY((launch_cta<kCta1, 256, kCta1Blocks, true>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
+    else HARP_TRY((launch_cta<kCta1, 256, kCta1Blocks, false>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
-    HARP_TRY((launch_cta<kCta2, 256, 4, BS>(g, ws, 2, T_TRI_M, wmax, cmax, bmax, reuse, s)));
-    HARP_TRY((launch_cta<kCtaMax, 1024, 1, BS>(g, ws, 3, T_TRI_L, wmax, cmax, bmax, reuse, s)));
+    if (bs2) HARP_TRY((launch_cta<kCta2, 256, 4, true>(g, ws, 2, T_TRI_M, wmax, cmax, bmax, reuse, s)));
+    else HARP_TRY((launch_cta<kCta2, 256, 4, false>(g, ws, 2, T_TRI_M, wmax, cmax, bmax, reuse, s)));
+    if (bs3) HARP_TRY((launch_cta<kCtaMax, 1024, 1, true>(g, ws, 3, T_TRI_L, wmax, cmax, bmax, reuse, s)));
+    else HARP_TRY((launch_cta<kCtaMax, 1024, 1, false>(g, ws, 3, T_TRI_L, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_L));
     return HARP_OK;
 }
@@ -823,8 +830,7 @@ harp_status count_triangles_k4(const harp_csr* g, Workspace& ws, const harp_plan
                                                     ws.q_mid, cnt, cnt_fb, cnt_big);
     HARP_LAUNCHED();
     const Sink sink{ws.acc, ws.gid, ws.accG};
-    if (plan.tri_probe == HARP_PROBE_BSEARCH) HARP_TRY(launch_tiers<true>(g, ws, wmax, cmax, bmax, reuse, s));
-    else HARP_TRY(launch_tiers<false>(g, ws, wmax, cmax, bmax, reuse, s));
+    HARP_TRY(launch_tiers(g, ws, wmax, cmax, bmax, reuse, plan.tri_probe_bin, s));
     // the largest possible out-degree is bounded by sqrt(2m) and by the maximum degree
     int64_t dmax = 1;
     while (dmax * dmax < 2 * g->m) ++dmax;

@@ -26,6 +26,9 @@ HARP_PLAN_NO_GRAPH, HARP_PLAN_NO_REUSE, HARP_PLAN_NO_BAND_MERGE = 1, 2, 4
 HARP_NSEGMENTS = 9
 
 MOTIFS = ("star3", "path4", "paw", "cycle4", "diamond", "clique4")
+ORBITS = ("star_center", "star_leaf", "path_end", "path_inner", "paw_pendant", "paw_hub", "paw_side", "cycle",
+          "diamond_spine", "diamond_tip", "clique")
+HARP_NORBITS = 11
 STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")
 
 
@@ -59,12 +62,14 @@ class harp_plan(ctypes.Structure):
         ("objective", ctypes.c_double),
         ("lit_cache_log2", ctypes.c_uint32),
         ("lit_cache_min_deg", ctypes.c_uint32),
+        ("tri_probe_bin", ctypes.c_uint8 * 4),
+        ("reserved0", ctypes.c_uint32),
         ("est_cost_tw", ctypes.c_double),
         ("est_cost_lit", ctypes.c_double),
     ]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: (list(getattr(self, f)) if f == "tri_probe_bin" else getattr(self, f)) for f, _ in self._fields_}
 
 
 class harp_select_opts(ctypes.Structure):
@@ -136,6 +141,8 @@ def lib():
         L.harp_reuse_stats.restype = i32
         L.harp_count4_async.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp]
         L.harp_count4_noalloc.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.harp_count4_orbits.argtypes = [vp, vp, u32]
+        L.harp_count4_orbits.restype = i32
         L.harp_batch_create.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp)]
         L.harp_batch_count.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp, vp]
         L.harp_batch_info.argtypes = [vp, pi64, pi64, pi64, ctypes.POINTER(ctypes.c_size_t)]
@@ -315,6 +322,20 @@ def harp_count4_async(g: Csr, d_out_ptr: int, plan: harp_plan | None = None, str
            "harp_count4_async")
 
 
+def harp_count4_orbits(g: Csr, out=None) -> np.ndarray:
+    """Per-vertex orbit counts uint64[n, 11] (rows = input vertex ids, columns in ORBITS order).
+    out: None (a new host array) or a torch.int64 CUDA tensor of n * 11 elements (filled in place)."""
+    n = g.info()["n"]
+    if out is not None:
+        _check(lib().harp_count4_orbits(g.handle, ctypes.c_void_p(out.data_ptr()), HARP_PTR_DEVICE),
+               "harp_count4_orbits")
+        return out
+    res = np.zeros((n, HARP_NORBITS), np.uint64)
+    _check(lib().harp_count4_orbits(g.handle, ctypes.c_void_p(res.ctypes.data if n else 0), HARP_PTR_HOST),
+           "harp_count4_orbits")
+    return res
+
+
 def harp_count4_noalloc(n: int, m: int, d_offsets: int, d_cols: int, d_out: int, stream=None) -> None:
     """Count a device CSR (n <= 262,144, m <= 524,288) without any device allocation.
 
@@ -370,7 +391,7 @@ def harp_batch_info(b: Batch) -> dict:
     return {"graphs": g.value, "n": n.value, "m": m.value, "device_bytes": by.value}
 
 
-HARP_AUTOTUNE_GRID = 8
+HARP_AUTOTUNE_GRID = 24
 
 
 def harp_batch_autotune(b: Batch, candidates=None, reps: int = 3):

@@ -28,8 +28,11 @@ CTA_MAX = 1024
 WIN_WORDS = {1: 51200, 2: 25600, 3: 16384, 4: 12288}  # counter words per wedge window by resident blocks per SM
 
 
-def window_words(c4_window_bytes):
-    """Counter words of the wedge window the kernel picks for plan.c4_window_bytes (the largest that fits)."""
+def window_words(c4_window_bytes, n=0):
+    """Counter words of the wedge window the kernel picks for plan.c4_window_bytes (the largest that
+    fits; 0 = by graph: 200 KiB above 2^22 vertices, else 100 KiB)."""
+    if c4_window_bytes == 0:
+        c4_window_bytes = 4 * WIN_WORDS[1] if n > (1 << 22) else 4 * WIN_WORDS[2]
     for minb in (1, 2, 3):
         if c4_window_bytes >= 4 * WIN_WORDS[minb]:
             return WIN_WORDS[minb]
@@ -83,7 +86,7 @@ def _merged_windows(bounds, widths, mask, u, words):
     return total
 
 
-def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=100 * 1024):
+def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=0):
     """Per-kernel work and algorithmic bytes (dict of dicts) under the given wedge plan fields."""
     G = rank_space(n, src, dst)
     m = G["m"]
@@ -135,7 +138,7 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=100 * 1024):
     dm = split
     # warp-local hash mode for W <= c4_warp_max, windowed counters above (no middle tier)
     tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= min(c4_warp_max, 512), 0, 2))
-    words = window_words(c4_window_bytes)
+    words = window_words(c4_window_bytes, n)
     bounds = band_starts + [n]
     # narrow bands may merge into the next wider one: the mask with the fewest degree-weighted windows
     # over 64 roots spread evenly over the ranks of degree >= 64 (lowest mask on a tie)

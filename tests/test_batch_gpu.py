@@ -105,8 +105,14 @@ def test_autotune_grid_and_custom_candidates(harp, handles):
         base = harp.harp_batch_count(b)
         assert base.tolist() == alone.tolist()
         best, ms = harp.harp_batch_autotune(b, reps=1)
-        assert len(ms) == harp.HARP_AUTOTUNE_GRID and all(x > 0 for x in ms)
+        timed = [x for x in ms if x > 0]
+        # the per-degree-bin descent: the default plan, then 2 + 4 x 2 + 3 + 2 + 2 knob values, each
+        # distinct plan timed once (at least one value of every knob equals the current plan)
+        assert len(ms) == harp.HARP_AUTOTUNE_GRID and 7 <= len(timed) <= 18
+        assert ms[len(timed):] == [0.0] * (len(ms) - len(timed))
         assert best.tri_warp_max in (16, 32) and best.c4_warp_max_work in (256, 512)
+        assert best.tri_cta_max in (256, 512, 1024) and best.c4_window_bytes in (0, 100 * 1024, 200 * 1024)
+        assert all(v in (harp.HARP_PROBE_HASH, harp.HARP_PROBE_BSEARCH) for v in best.tri_probe_bin)
         assert harp.harp_batch_count(b, best).tolist() == base.tolist()
         cands = []
         for wm, cta in ((4, 64), (32, 1024)):
@@ -118,5 +124,35 @@ def test_autotune_grid_and_custom_candidates(harp, handles):
         assert len(ms2) == 2 and all(x > 0 for x in ms2)
         assert (best2.tri_warp_max, best2.tri_cta_max) in ((4, 64), (32, 1024))
         assert harp.harp_batch_count(b, best2).tolist() == base.tolist()
+    finally:
+        b.close()
+
+
+def test_every_per_bin_variant_counts_the_same(harp, handles):
+    """Each knob of the per-degree-bin search on its own (the probe of every triangle bin, the warp/CTA
+    splits, the staging capacity, the wedge window) gives the alone-counts of every member, batched and
+    one graph at a time."""
+    hs, alone, _ = handles
+    b = harp.harp_batch_create(hs)
+    try:
+        variants = []
+        for binno in range(4):
+            for probe in (harp.HARP_PROBE_HASH, harp.HARP_PROBE_BSEARCH):
+                p = harp.harp_plan()
+                p.version = harp.HARP_ABI_VERSION
+                p.tri_probe_bin[binno] = probe
+                p.tri_probe = harp.HARP_PROBE_BSEARCH if probe == harp.HARP_PROBE_HASH else harp.HARP_PROBE_HASH
+                variants.append(p)
+        for field, values in (("tri_warp_max", (8, 16)), ("tri_cta_max", (256, 512)),
+                              ("c4_warp_max_work", (64, 256)), ("c4_window_bytes", (200 * 1024, 64 * 1024))):
+            for v in values:
+                p = harp.harp_plan()
+                p.version = harp.HARP_ABI_VERSION
+                setattr(p, field, v)
+                variants.append(p)
+        for p in variants:
+            assert harp.harp_batch_count(b, p).tolist() == alone.tolist(), p.as_dict()
+        for k in (0, len(hs) // 2, len(hs) - 1):
+            assert harp.harp_count4(hs[k], variants[3]).tolist() == alone[k].tolist()
     finally:
         b.close()
