@@ -117,7 +117,7 @@ def test_literal_ba2000_against_literal_oracle(harp):
     assert counts.tolist() == O.count4_literal(g.n, g.src, g.dst).tolist()
 
 
-@pytest.mark.parametrize("scale", [14, 15])
+@pytest.mark.parametrize("scale", [14, 15, 16])
 def test_literal_rmat_against_stored_literal_oracle(harp, scale):
     with open(os.path.join(HERE, "golden", "rmat_literal_oracle.json")) as f:
         rec = json.load(f)[str(scale)]
