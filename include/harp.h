@@ -230,6 +230,24 @@ enum {
 };
 harp_status harp_count4_orbits(const harp_csr* g, uint64_t* orbits_out, uint32_t flags);
 
+/* Per-edge (edge orbit) counts: for every edge e and each of the HARP_NEDGE_ORBITS roles an edge can
+ * play in a connected induced 4-vertex motif (decided by its endpoints' degrees inside G[S]), the
+ * number of induced occurrences S whose G[S] contains e in that role.  Ten non-induced statistics per
+ * edge (degree and triangle sums, triangles routed to their edges, 4-cycles routed from the wedge
+ * walk to their edges, 4-cliques through the edge) and a unit upper-triangular containment system,
+ * exact modulo 2^64.  Summed over the edges, role r gives its motif's count times the motif's edges
+ * in r.
+ *   orbits_out  uint64[m][HARP_NEDGE_ORBITS]; row k = the k-th edge (a, b), a < b, of the simple
+ *               graph in lexicographic order of the input ids (the order of harp_csr_arrays' rows);
+ *               host memory if flags == HARP_PTR_HOST, device memory if HARP_PTR_DEVICE.
+ * Blocking on the handle's stream.  Errors as harp_count4_orbits. */
+enum {
+    HARP_EORB_STAR = 0, HARP_EORB_PATH_END = 1, HARP_EORB_PATH_MID = 2, HARP_EORB_PAW_PENDANT = 3,
+    HARP_EORB_PAW_HUB = 4, HARP_EORB_PAW_FAR = 5, HARP_EORB_CYCLE = 6, HARP_EORB_DIAMOND_SPINE = 7,
+    HARP_EORB_DIAMOND_RIM = 8, HARP_EORB_CLIQUE = 9, HARP_NEDGE_ORBITS = 10
+};
+harp_status harp_count4_edge_orbits(const harp_csr* g, uint64_t* orbits_out, uint32_t flags);
+
 /* Per-segment device times of the last count issued with profiling on (milliseconds, measured with
  * CUDA events recorded on the launching stream between the kernels).  Segments, in launch order:
  *   0 orientation (degree ranking, relabelled sorted CSR, out-CSR)

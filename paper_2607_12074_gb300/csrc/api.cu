@@ -200,6 +200,41 @@ harp_status count_to_host(const harp_csr* gc, const harp_plan* plan, uint64_t* c
 }  // namespace
 }  // namespace harp
 
+namespace harp {
+namespace {
+// shared body of the per-vertex and per-edge orbit outputs: orientation, the triangle pass (t_e of
+// every out-arc), then `run` writes rows*cols uint64 into the device output
+template <typename Run>
+harp_status orbit_output(harp_csr* g, uint64_t* orbits_out, uint32_t flags, size_t rows, size_t cols, Run run) {
+    cudaStream_t s = g->stream;
+    HARP_TRY(ws_ensure(g->ws, g->n, g->m, s));
+    Workspace& ws = g->ws;
+    HARP_CK(cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s));
+    harp_plan plan;
+    normalise_plan(nullptr, &plan);
+    const size_t out_bytes = sizeof(uint64_t) * cols * rows;
+    uint64_t* d_out = orbits_out;
+    if (flags == HARP_PTR_HOST) HARP_CK(cudaMallocAsync((void**)&d_out, out_bytes, s));
+    harp_status st = orient(g, ws, s);
+    if (st == HARP_OK) st = count_triangles_k4(g, ws, plan, s);
+    if (st == HARP_OK) st = run(ws, d_out, s);
+    uint64_t err = 0;
+    cudaError_t e = cudaSuccess;
+    if (st == HARP_OK) e = cudaMemcpyAsync(&err, ws.acc + ACC_ERR, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (st == HARP_OK && e == cudaSuccess && flags == HARP_PTR_HOST)
+        e = cudaMemcpyAsync(orbits_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+    if (flags == HARP_PTR_HOST) cudaFreeAsync(d_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        record_cuda_error(e);
+        return HARP_ECUDA;
+    }
+    if (st != HARP_OK) return st;
+    return err ? HARP_EDEVICE : HARP_OK;
+}
+}  // namespace
+}  // namespace harp
+
 using namespace harp;
 
 extern "C" {
@@ -309,37 +344,24 @@ harp_status harp_count4_async(const harp_csr* gc, const harp_plan* plan, uint64_
     return HARP_OK;
 }
 
+harp_status harp_count4_edge_orbits(const harp_csr* gc, uint64_t* orbits_out, uint32_t flags) {
+    if (!gc || (!orbits_out && gc->m > 0)) return HARP_EINVAL;
+    if (flags != HARP_PTR_HOST && flags != HARP_PTR_DEVICE) return HARP_EINVAL;
+    harp_csr* g = const_cast<harp_csr*>(gc);
+    if (g->m == 0) return HARP_OK;
+    HARP_CK(cudaSetDevice(g->device));
+    return orbit_output(g, orbits_out, flags, (size_t)g->m, HARP_NEDGE_ORBITS,
+                        [&](Workspace& ws, uint64_t* d_out, cudaStream_t s) { return count_edge_orbits(g, ws, d_out, s); });
+}
+
 harp_status harp_count4_orbits(const harp_csr* gc, uint64_t* orbits_out, uint32_t flags) {
     if (!gc || (!orbits_out && gc->n > 0)) return HARP_EINVAL;
     if (flags != HARP_PTR_HOST && flags != HARP_PTR_DEVICE) return HARP_EINVAL;
     harp_csr* g = const_cast<harp_csr*>(gc);
     if (g->n == 0) return HARP_OK;
     HARP_CK(cudaSetDevice(g->device));
-    cudaStream_t s = g->stream;
-    HARP_TRY(ws_ensure(g->ws, g->n, g->m, s));
-    Workspace& ws = g->ws;
-    HARP_CK(cudaMemsetAsync(ws.acc, 0, sizeof(uint64_t) * kOutLen, s));
-    harp_plan plan;
-    normalise_plan(nullptr, &plan);
-    const size_t out_bytes = sizeof(uint64_t) * HARP_NORBITS * (size_t)g->n;
-    uint64_t* d_out = orbits_out;
-    if (flags == HARP_PTR_HOST) HARP_CK(cudaMallocAsync((void**)&d_out, out_bytes, s));
-    harp_status st = orient(g, ws, s);
-    if (st == HARP_OK) st = count_triangles_k4(g, ws, plan, s);  // t_e of every out-arc
-    if (st == HARP_OK) st = count_orbits(g, ws, d_out, s);
-    uint64_t err = 0;
-    cudaError_t e = cudaSuccess;
-    if (st == HARP_OK) e = cudaMemcpyAsync(&err, ws.acc + ACC_ERR, sizeof(err), cudaMemcpyDeviceToHost, s);
-    if (st == HARP_OK && e == cudaSuccess && flags == HARP_PTR_HOST)
-        e = cudaMemcpyAsync(orbits_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
-    if (flags == HARP_PTR_HOST) cudaFreeAsync(d_out, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        record_cuda_error(e);
-        return HARP_ECUDA;
-    }
-    if (st != HARP_OK) return st;
-    return err ? HARP_EDEVICE : HARP_OK;
+    return orbit_output(g, orbits_out, flags, (size_t)g->n, HARP_NORBITS,
+                        [&](Workspace& ws, uint64_t* d_out, cudaStream_t s) { return count_orbits(g, ws, d_out, s); });
 }
 
 harp_status harp_set_profiling(int enable) {

@@ -222,6 +222,8 @@ harp_status count_literal(const harp_csr* g, Workspace& ws, const harp_plan& pla
 // orbits.cu: per-vertex orbit counts (11 roles) after orient() and count_triangles_k4(); d_out is
 // device uint64[n][11] indexed by input vertex id
 harp_status count_orbits(const harp_csr* g, Workspace& ws, uint64_t* d_out, cudaStream_t s);
+// per-edge orbit counts (10 roles); d_out is device uint64[m][10] in the input graph's edge order
+harp_status count_edge_orbits(const harp_csr* g, Workspace& ws, uint64_t* d_out, cudaStream_t s);
 
 // reduce.cu: sum_e C(t_e,2), closure (step a7); writes acc[OUT_COUNTS..], acc[OUT_STATS..]
 harp_status reduce_and_close(const harp_csr* g, Workspace& ws, cudaStream_t s);

@@ -31,6 +31,20 @@
 //                 sum_{x in its segment} (cnt(x) - 1)
 //   k_orb_close   warp per vertex: N2, N4, N0, N3, N5, N9, N10 and the back-substitution, written to
 //                 the input id of the vertex.
+//
+// Per-edge (edge orbit) counts use the same passes with routing to edges instead of vertices: ten
+// roles of an edge inside G[S] (its endpoints' degrees there decide them), ten statistics E_i(e) for
+// e = (a, b) and a unit upper-triangular 10 x 10 containment system:
+//   E0 = C(d_a - 1, 2) + C(d_b - 1, 2)          E1 = S1(a) + S1(b) - d_a - d_b + 2 - 2 t_ab
+//   E2 = (d_a - 1)(d_b - 1) - t_ab              E3 = t_a + t_b - 2 t_ab
+//   E4 = t_ab (d_a + d_b - 4)                   E5 = sum_{h in N(a) n N(b)} (d_h - 2)
+//   E6 = 4-cycles through e                     E7 = C(t_ab, 2)
+//   E8 = sum_{s in N(a) n N(b)} (t_as - 1) + (t_bs - 1)
+//   E9 = 4-cliques through e = (1/2) sum over the triangles T on e of X_3(T)
+// E5, E8 and E9 are routed from each triangle to its three edges (k_orb_tri), E6 from the wedge walk:
+// each wedge u - w - x adds cnt(x) - 1 to the arcs (u, w) and (w, x) (k_orb_c4w / k_orb_c4b), and
+// k_eorb_close evaluates one edge per thread and writes it at the edge's index in the input graph's
+// edge list ((a, b), a < b, lexicographic by input id).
 #include "harp_internal.cuh"
 
 namespace harp {
@@ -65,11 +79,15 @@ __device__ __forceinline__ bool has(const int32_t* __restrict__ cols, int64_t b,
     return p < e && __ldg(cols + p) == x;
 }
 
-// t of the edge {a, b}, a != b adjacent: the out-arc of the lower rank
-__device__ __forceinline__ uint64_t t_of(const OrbGraph& G, int32_t a, int32_t b) {
+// the out-arc of the edge {a, b} (a != b adjacent): the lower rank's out-list holds the higher one
+__device__ __forceinline__ int64_t arc_of(const OrbGraph& G, int32_t a, int32_t b) {
     const int32_t lo = a < b ? a : b, hi = a < b ? b : a;
     const int64_t pb = G.offp[lo], pe = G.offp[lo + 1];
-    return (uint64_t)G.te[pb + lower_bound_i32(G.colsp + pb, pe - pb, hi)];
+    return pb + lower_bound_i32(G.colsp + pb, pe - pb, hi);
+}
+// t of the edge {a, b}
+__device__ __forceinline__ uint64_t t_of(const OrbGraph& G, int32_t a, int32_t b) {
+    return (uint64_t)G.te[arc_of(G, a, b)];
 }
 
 __device__ __forceinline__ int32_t arc_row(const int64_t* __restrict__ offp, int64_t n, int64_t a) {
@@ -85,9 +103,16 @@ __device__ __forceinline__ int32_t arc_row(const int64_t* __restrict__ offp, int
 // ---------------------------------------------------------------------------------------------
 // Triangles: N9 and tau3 routing.
 // ---------------------------------------------------------------------------------------------
+// Per-edge routing targets of the triangle pass (per out-arc; all nullptr for the per-vertex mode).
+struct EdgeRoute {
+    unsigned long long* e5;  // sum of (d of the third vertex - 2)
+    unsigned long long* e8;  // sum of (t - 1) of the other two edges
+    unsigned long long* e9;  // sum of X_3 (twice the 4-cliques through the edge)
+};
+
 __global__ void __launch_bounds__(kOrbThreads) k_orb_tri(OrbGraph G, int64_t n, int64_t m,
                                                          unsigned long long* __restrict__ n9,
-                                                         unsigned long long* __restrict__ tau3) {
+                                                         unsigned long long* __restrict__ tau3, EdgeRoute er) {
     __shared__ int32_t sbuf[kOrbWarps][kOrbStage];
     const int w = threadIdx.x >> 5, l = lane_id();
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -123,7 +148,7 @@ __global__ void __launch_bounds__(kOrbThreads) k_orb_tri(OrbGraph G, int64_t n, 
                 }
             }
             c3 = warp_sum(c3);
-            if (l == 0) {
+            if (l == 0 && n9) {
                 const uint64_t t_uw = t_of(G, u, wv), t_vw = t_of(G, v, wv);
                 atomicAdd(&n9[u], (unsigned long long)(t_vw - 1));
                 atomicAdd(&n9[v], (unsigned long long)(t_uw - 1));
@@ -132,6 +157,22 @@ __global__ void __launch_bounds__(kOrbThreads) k_orb_tri(OrbGraph G, int64_t n, 
                     atomicAdd(&tau3[u], (unsigned long long)c3);
                     atomicAdd(&tau3[v], (unsigned long long)c3);
                     atomicAdd(&tau3[wv], (unsigned long long)c3);
+                }
+            }
+            if (l == 0 && er.e5) {  // the triangle's three edges: (u, v) = arc a, (u, w), (v, w)
+                const int64_t a_uw = arc_of(G, u, wv), a_vw = arc_of(G, v, wv);
+                const uint64_t t_uw = G.te[a_uw], t_vw = G.te[a_vw];
+                const uint64_t du = (uint64_t)G.deg[u], dv = (uint64_t)G.deg[v], dw = (uint64_t)G.deg[wv];
+                atomicAdd(&er.e5[a], (unsigned long long)(dw - 2));
+                atomicAdd(&er.e5[a_uw], (unsigned long long)(dv - 2));
+                atomicAdd(&er.e5[a_vw], (unsigned long long)(du - 2));
+                atomicAdd(&er.e8[a], (unsigned long long)((t_uw - 1) + (t_vw - 1)));
+                atomicAdd(&er.e8[a_uw], (unsigned long long)((t_uv - 1) + (t_vw - 1)));
+                atomicAdd(&er.e8[a_vw], (unsigned long long)((t_uv - 1) + (t_uw - 1)));
+                if (c3) {
+                    atomicAdd(&er.e9[a], (unsigned long long)c3);
+                    atomicAdd(&er.e9[a_uw], (unsigned long long)c3);
+                    atomicAdd(&er.e9[a_vw], (unsigned long long)c3);
                 }
             }
         };
@@ -235,7 +276,8 @@ __device__ __forceinline__ uint32_t* hash_slot(int32_t* keys, uint32_t* cnt, int
 __global__ void __launch_bounds__(kOrbThreads) k_orb_c4w(OrbGraph G, const int32_t* __restrict__ q,
                                                          const unsigned long long* __restrict__ qcnt,
                                                          unsigned long long* __restrict__ n7,
-                                                         unsigned long long* __restrict__ n7x2) {
+                                                         unsigned long long* __restrict__ n7x2,
+                                                         unsigned long long* __restrict__ e6a) {
     __shared__ int32_t keys[kOrbWarps][kHashSlots];
     __shared__ uint32_t cnt[kOrbWarps][kHashSlots];
     const int w = threadIdx.x >> 5, l = lane_id();
@@ -270,13 +312,15 @@ __global__ void __launch_bounds__(kOrbThreads) k_orb_c4w(OrbGraph G, const int32
                 const int32_t x = __ldg(G.cols + p);
                 const uint32_t c = *hash_slot(keys[w], cnt[w], x, false) - 1u;
                 sw += c;
-                if (c) atomicAdd(&n7x2[x], (unsigned long long)c);
+                if (c && n7x2) atomicAdd(&n7x2[x], (unsigned long long)c);
+                if (c && e6a) atomicAdd(&e6a[p], (unsigned long long)c);  // the arc (w, x)
             }
-            if (sw) atomicAdd(&n7[wv], (unsigned long long)sw);
+            if (sw && n7) atomicAdd(&n7[wv], (unsigned long long)sw);
+            if (sw && e6a) atomicAdd(&e6a[ub + k], (unsigned long long)sw);  // the arc (u, w)
             root2 += sw;
         }
         root2 = warp_sum(root2);
-        if (l == 0 && root2) atomicAdd(&n7[u], (unsigned long long)(root2 >> 1));
+        if (l == 0 && root2 && n7) atomicAdd(&n7[u], (unsigned long long)(root2 >> 1));
         __syncwarp();
     }
 }
@@ -287,7 +331,8 @@ __global__ void __launch_bounds__(kOrbThreads) k_orb_c4b(OrbGraph G, int64_t n, 
                                                          const unsigned long long* __restrict__ qcnt,
                                                          uint32_t* __restrict__ dense,
                                                          unsigned long long* __restrict__ n7,
-                                                         unsigned long long* __restrict__ n7x2) {
+                                                         unsigned long long* __restrict__ n7x2,
+                                                         unsigned long long* __restrict__ e6a) {
     __shared__ uint64_t red[32];
     uint32_t* cntv = dense + (size_t)blockIdx.x * (size_t)n;
     const int64_t nq = (int64_t)qcnt[1];
@@ -311,21 +356,23 @@ __global__ void __launch_bounds__(kOrbThreads) k_orb_c4b(OrbGraph G, int64_t n, 
                     } else if (pass == 1) {
                         const uint32_t c = cntv[x] - 1u;
                         sw += c;
-                        if (c) atomicAdd(&n7x2[x], (unsigned long long)c);
+                        if (c && n7x2) atomicAdd(&n7x2[x], (unsigned long long)c);
+                        if (c && e6a) atomicAdd(&e6a[p], (unsigned long long)c);  // the arc (w, x)
                     } else {
                         cntv[x] = 0;
                     }
                 }
                 if (pass == 1) {
                     sw = warp_sum(sw);
-                    if (l == 0 && sw) atomicAdd(&n7[wv], (unsigned long long)sw);
+                    if (l == 0 && sw && n7) atomicAdd(&n7[wv], (unsigned long long)sw);
+                    if (l == 0 && sw && e6a) atomicAdd(&e6a[ub + k], (unsigned long long)sw);  // the arc (u, w)
                     root2 += sw;
                 }
             }
             __syncthreads();  // every counter of the pass is final before the next reads it
             if (pass == 1) {
                 root2 = block_sum_u64(l == 0 ? root2 : 0, red);
-                if (threadIdx.x == 0 && root2) atomicAdd(&n7[u], (unsigned long long)(root2 >> 1));
+                if (threadIdx.x == 0 && root2 && n7) atomicAdd(&n7[u], (unsigned long long)(root2 >> 1));
             }
         }
     }
@@ -388,6 +435,77 @@ __global__ void __launch_bounds__(kOrbThreads) k_orb_close(OrbGraph G, int64_t n
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Per-edge statistics and back-substitution.
+// ---------------------------------------------------------------------------------------------
+constexpr int kEdgeOrbits = 10;
+__constant__ uint8_t c_econtain[kEdgeOrbits][kEdgeOrbits] = {
+    {1, 0, 0, 1, 1, 0, 0, 2, 1, 2}, {0, 1, 0, 2, 0, 2, 2, 0, 3, 4}, {0, 0, 1, 0, 1, 0, 1, 2, 1, 2},
+    {0, 0, 0, 1, 0, 0, 0, 0, 1, 2}, {0, 0, 0, 0, 1, 0, 0, 4, 1, 4}, {0, 0, 0, 0, 0, 1, 0, 0, 1, 2},
+    {0, 0, 0, 0, 0, 0, 1, 0, 1, 2}, {0, 0, 0, 0, 0, 0, 0, 1, 0, 1}, {0, 0, 0, 0, 0, 0, 0, 0, 1, 4},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 1}};
+
+// up[x] = neighbours of input vertex x above x (its row's suffix in the input CSR)
+__global__ void k_eorb_up(const int64_t* __restrict__ off_in, const int32_t* __restrict__ cols_in, int64_t n,
+                          int32_t* __restrict__ up) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = off_in[x], e = off_in[x + 1];
+        up[x] = (int32_t)(e - b - lower_bound_i32(cols_in + b, e - b, (int32_t)x + 1));
+    }
+}
+
+// One thread per out-arc (u, v) of the rank-order graph: the ten statistics, the back-substitution,
+// and the write at the edge's index in the input edge list.
+__global__ void k_eorb_close(OrbGraph G, int64_t n, int64_t m, const int32_t* __restrict__ dplus,
+                             const uint64_t* __restrict__ tsum, const uint64_t* __restrict__ s1,
+                             const unsigned long long* __restrict__ e5, const unsigned long long* __restrict__ e8,
+                             const unsigned long long* __restrict__ e9, const unsigned long long* __restrict__ e6a,
+                             const int32_t* __restrict__ order, const int64_t* __restrict__ off_in,
+                             const int32_t* __restrict__ cols_in, const int32_t* __restrict__ up,
+                             const int64_t* __restrict__ ebase, uint64_t* __restrict__ out,
+                             uint64_t* __restrict__ acc) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = arc_row(G.offp, n, a);
+        const int32_t v = G.colsp[a];
+        const uint64_t du = (uint64_t)G.deg[u], dv = (uint64_t)G.deg[v];
+        const uint64_t t = (uint64_t)G.te[a];
+        const uint64_t tu = tsum[u] >> 1, tv = tsum[v] >> 1;
+        // the two arcs of the edge in the rank-order CSR: (u, v) in u's suffix, (v, u) in v's prefix
+        const int64_t p_uv = G.off[u] + ((int64_t)G.deg[u] - dplus[u]) + (a - G.offp[u]);
+        const int64_t vb = G.off[v];
+        const int64_t p_vu = vb + lower_bound_i32(G.cols + vb, (int64_t)G.deg[v] - dplus[v], u);
+        uint64_t E[kEdgeOrbits];
+        E[0] = choose2_u64(du - 1) + choose2_u64(dv - 1);
+        E[1] = s1[u] + s1[v] - du - dv + 2 - 2 * t;
+        E[2] = (du - 1) * (dv - 1) - t;
+        E[3] = tu + tv - 2 * t;
+        E[4] = t * (du + dv - 4);
+        E[5] = e5[a];
+        E[6] = e6a[p_uv] + e6a[p_vu];
+        E[7] = choose2_u64(t);
+        E[8] = e8[a];
+        E[9] = e9[a] >> 1;
+        if (e9[a] & 1) atomicOr((unsigned long long*)&acc[ACC_ERR], (unsigned long long)kErrLitDiv);
+        uint64_t o[kEdgeOrbits];
+#pragma unroll
+        for (int i = kEdgeOrbits - 1; i >= 0; --i) {
+            uint64_t x = E[i];
+#pragma unroll
+            for (int j = i + 1; j < kEdgeOrbits; ++j) x -= (uint64_t)c_econtain[i][j] * o[j];
+            o[i] = x;
+        }
+        // index of the edge in the input edge list: (lo, hi) by input id, rows' upper suffixes in order
+        const int32_t ia = order[u], ib = order[v];
+        const int32_t lo = ia < ib ? ia : ib, hi = ia < ib ? ib : ia;
+        const int64_t rb = off_in[lo], re = off_in[lo + 1];
+        const int64_t pos = lower_bound_i32(cols_in + rb, re - rb, hi);  // within lo's row
+        const int64_t idx = ebase[lo] + (pos - ((re - rb) - up[lo]));
+        uint64_t* dst = out + idx * kEdgeOrbits;
+#pragma unroll
+        for (int i = 0; i < kEdgeOrbits; ++i) dst[i] = o[i];
+    }
+}
+
 unsigned orb_grid(int64_t warps) {
     int64_t b = (warps * 32 + kOrbThreads - 1) / kOrbThreads;
     if (b < 1) b = 1;
@@ -430,7 +548,7 @@ harp_status count_orbits(const harp_csr* g, Workspace& ws, uint64_t* d_out, cuda
         if (e == cudaSuccess) e = cudaGetLastError();
     };
     if (e == cudaSuccess && m > 0) {
-        k_orb_tri<<<orb_grid(m), kOrbThreads, 0, s>>>(G, n, m, n9, tau3);
+        k_orb_tri<<<orb_grid(m), kOrbThreads, 0, s>>>(G, n, m, n9, tau3, EdgeRoute{nullptr, nullptr, nullptr});
         launched();
     }
     if (e == cudaSuccess) {
@@ -441,11 +559,11 @@ harp_status count_orbits(const harp_csr* g, Workspace& ws, uint64_t* d_out, cuda
         k_orb_classify<<<orb_grid(n), kOrbThreads, 0, s>>>(G, n, q_light, q_heavy, qcnt);
         launched();
         if (e == cudaSuccess) {
-            k_orb_c4w<<<orb_grid(n), kOrbThreads, 0, s>>>(G, q_light, qcnt, n7, n7x2);
+            k_orb_c4w<<<orb_grid(n), kOrbThreads, 0, s>>>(G, q_light, qcnt, n7, n7x2, nullptr);
             launched();
         }
         if (e == cudaSuccess) {
-            k_orb_c4b<<<heavy_blocks, kOrbThreads, 0, s>>>(G, n, q_heavy, qcnt, dense, n7, n7x2);
+            k_orb_c4b<<<heavy_blocks, kOrbThreads, 0, s>>>(G, n, q_heavy, qcnt, dense, n7, n7x2, nullptr);
             launched();
         }
     }
@@ -460,6 +578,84 @@ harp_status count_orbits(const harp_csr* g, Workspace& ws, uint64_t* d_out, cuda
         return e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
     }
     return HARP_OK;
+}
+
+}  // namespace harp
+
+namespace harp {
+
+harp_status count_edge_orbits(const harp_csr* g, Workspace& ws, uint64_t* d_out, cudaStream_t s) {
+    const int64_t n = g->n, m = g->m;
+    if (m == 0) return HARP_OK;
+    // scratch: tsum, s1 (uint64 n), N (unused here, 11 n), e5, e8, e9 (uint64 m), e6a (uint64 2m),
+    // up (int32 n), ebase (int64 n + 1), root queues (int32 2n), counters, dense counters
+    int64_t hb = ((int64_t)4 << 30) / (4 * (n > 0 ? n : 1));
+    if (hb > num_sms()) hb = num_sms();
+    const int heavy_blocks = hb < 1 ? 1 : (int)hb;
+    const size_t bytes = 8 * (size_t)(2 * n) + 8 * (size_t)(11 * n) + 8 * (size_t)(3 * m) + 8 * (size_t)(2 * m) +
+                         4 * (size_t)n + 8 * (size_t)(n + 2) + 4 * (size_t)(2 * n) + 128 +
+                         (size_t)heavy_blocks * (size_t)n * 4;
+    unsigned char* base = nullptr;
+    HARP_CK(cudaMallocAsync((void**)&base, bytes, s));
+    uint64_t* tsum = reinterpret_cast<uint64_t*>(base);
+    uint64_t* s1 = tsum + n;
+    uint64_t* N = s1 + n;
+    unsigned long long* e5 = reinterpret_cast<unsigned long long*>(N + 11 * n);
+    unsigned long long* e8 = e5 + m;
+    unsigned long long* e9 = e8 + m;
+    unsigned long long* e6a = e9 + m;
+    int64_t* ebase = reinterpret_cast<int64_t*>(e6a + 2 * m);
+    int32_t* up = reinterpret_cast<int32_t*>(ebase + n + 2);   // n + 2 int64 keep what follows 8-aligned
+    int32_t* q_light = up + n;
+    int32_t* q_heavy = q_light + n;
+    // up, q_light and q_heavy hold 3n int32: round up to 8 bytes before the uint64 counters
+    unsigned long long* qcnt = reinterpret_cast<unsigned long long*>(q_heavy + n + (n & 1));
+    uint32_t* dense = reinterpret_cast<uint32_t*>(qcnt + 8);
+    const OrbGraph G{ws.off, ws.cols, ws.deg, ws.offp, ws.colsp, ws.te};
+    cudaError_t e = cudaMemsetAsync(base, 0, bytes, s);
+    auto launched = [&]() {
+        note_launch();
+        if (e == cudaSuccess) e = cudaGetLastError();
+    };
+    if (e == cudaSuccess) {
+        k_orb_tri<<<orb_grid(m), kOrbThreads, 0, s>>>(G, n, m, nullptr, nullptr, EdgeRoute{e5, e8, e9});
+        launched();
+    }
+    if (e == cudaSuccess) {
+        k_orb_vertex<<<orb_grid(n), kOrbThreads, 0, s>>>(G, n, tsum, s1, N);
+        launched();
+    }
+    if (e == cudaSuccess) {
+        k_orb_classify<<<orb_grid(n), kOrbThreads, 0, s>>>(G, n, q_light, q_heavy, qcnt);
+        launched();
+    }
+    if (e == cudaSuccess) {
+        k_orb_c4w<<<orb_grid(n), kOrbThreads, 0, s>>>(G, q_light, qcnt, nullptr, nullptr, e6a);
+        launched();
+    }
+    if (e == cudaSuccess) {
+        k_orb_c4b<<<heavy_blocks, kOrbThreads, 0, s>>>(G, n, q_heavy, qcnt, dense, nullptr, nullptr, e6a);
+        launched();
+    }
+    if (e == cudaSuccess) {
+        const int64_t blocks = (n + 255) / 256;
+        k_eorb_up<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(g->off, g->cols, n, up);
+        launched();
+    }
+    harp_status st = HARP_OK;
+    if (e == cudaSuccess) st = exclusive_scan_i32_to_i64(up, ebase, n, ws.scan_tmp, ws.scan_tmp_len, s);
+    if (e == cudaSuccess && st == HARP_OK) {
+        const int64_t blocks = (m + 255) / 256;
+        k_eorb_close<<<(unsigned)(blocks < (int64_t)num_sms() * 16 ? blocks : (int64_t)num_sms() * 16), 256, 0, s>>>(
+            G, n, m, ws.dplus, tsum, s1, e5, e8, e9, e6a, ws.order, g->off, g->cols, up, ebase, d_out, ws.acc);
+        launched();
+    }
+    cudaFreeAsync(base, s);
+    if (e != cudaSuccess) {
+        record_cuda_error(e);
+        return e == cudaErrorMemoryAllocation ? HARP_ENOMEM : HARP_ECUDA;
+    }
+    return st;
 }
 
 }  // namespace harp

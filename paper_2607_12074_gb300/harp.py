@@ -29,6 +29,9 @@ MOTIFS = ("star3", "path4", "paw", "cycle4", "diamond", "clique4")
 ORBITS = ("star_center", "star_leaf", "path_end", "path_inner", "paw_pendant", "paw_hub", "paw_side", "cycle",
           "diamond_spine", "diamond_tip", "clique")
 HARP_NORBITS = 11
+EDGE_ORBITS = ("star_edge", "path_end_edge", "path_mid_edge", "paw_pendant_edge", "paw_hub_edge",
+               "paw_far_edge", "cycle_edge", "diamond_spine_edge", "diamond_rim_edge", "clique_edge")
+HARP_NEDGE_ORBITS = 10
 STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")
 
 
@@ -143,6 +146,8 @@ def lib():
         L.harp_count4_noalloc.argtypes = [i64, i64, vp, vp, vp, vp]
         L.harp_count4_orbits.argtypes = [vp, vp, u32]
         L.harp_count4_orbits.restype = i32
+        L.harp_count4_edge_orbits.argtypes = [vp, vp, u32]
+        L.harp_count4_edge_orbits.restype = i32
         L.harp_batch_create.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp)]
         L.harp_batch_count.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp, vp]
         L.harp_batch_info.argtypes = [vp, pi64, pi64, pi64, ctypes.POINTER(ctypes.c_size_t)]
@@ -333,6 +338,21 @@ def harp_count4_orbits(g: Csr, out=None) -> np.ndarray:
     res = np.zeros((n, HARP_NORBITS), np.uint64)
     _check(lib().harp_count4_orbits(g.handle, ctypes.c_void_p(res.ctypes.data if n else 0), HARP_PTR_HOST),
            "harp_count4_orbits")
+    return res
+
+
+def harp_count4_edge_orbits(g: Csr, out=None) -> np.ndarray:
+    """Per-edge orbit counts uint64[m, 10] (rows = edges (a, b), a < b, in lexicographic order of the input
+    ids; columns in EDGE_ORBITS order).  out: None (a new host array) or a torch.int64 CUDA tensor of
+    m * 10 elements (filled in place)."""
+    m = g.info()["m"]
+    if out is not None:
+        _check(lib().harp_count4_edge_orbits(g.handle, ctypes.c_void_p(out.data_ptr()), HARP_PTR_DEVICE),
+               "harp_count4_edge_orbits")
+        return out
+    res = np.zeros((m, HARP_NEDGE_ORBITS), np.uint64)
+    _check(lib().harp_count4_edge_orbits(g.handle, ctypes.c_void_p(res.ctypes.data if m else 0), HARP_PTR_HOST),
+           "harp_count4_edge_orbits")
     return res
 
 

@@ -7,7 +7,8 @@
   counters) against orbits4_combo;
 * on larger graphs (R-MAT 14, 16) every role summed over the vertices equals the GPU's global count
   times the role's vertices in its motif;
-* the device-output form equals the host one.
+* the device-output form equals the host one;
+* per-edge orbit counts (harp_count4_edge_orbits) the same way against oracle.edge_orbits.
 """
 import os
 import sys
@@ -16,6 +17,7 @@ import numpy as np
 import pytest
 
 import graphgen
+from oracle import edge_orbits as EB
 from oracle import orbits as OB
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -113,3 +115,61 @@ def test_device_output_equals_host_output(harp):
         assert dev.cpu().numpy().view(np.uint64).reshape(g.n, -1).tolist() == host.tolist()
     finally:
         csr.close()
+
+
+
+def gpu_edge_orbits(H, n, src, dst):
+    g = H.harp_build_csr(n, torch.from_numpy(np.ascontiguousarray(src, np.int32)).cuda(),
+                         torch.from_numpy(np.ascontiguousarray(dst, np.int32)).cuda())
+    try:
+        return H.harp_count4_edge_orbits(g), H.harp_count4(g)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("name", list(MOTIF_GRAPHS))
+def test_edge_orbits_each_motif_graph_alone(harp, name):
+    s, d = MOTIF_GRAPHS[name]
+    got, _ = gpu_edge_orbits(harp, 4, s, d)
+    assert got.tolist() == EB.edge_orbits4_brute(4, s, d).tolist()
+
+
+@pytest.mark.parametrize("name,n,e", FAMILIES, ids=[f[0] for f in FAMILIES])
+def test_edge_orbits_closed_form_families(harp, name, n, e):
+    s, d = e
+    got, _ = gpu_edge_orbits(harp, n, s, d)
+    want = EB.edge_orbits4_brute(n, s, d) if n <= 14 else EB.edge_orbits4_combo(n, s, d)
+    assert got.tolist() == want.tolist()
+
+
+def test_edge_orbits_random_graphs_against_brute_force(harp):
+    rng = np.random.default_rng(78)
+    for trial in range(30):
+        n = int(rng.integers(5, 22))
+        p = float(rng.uniform(0.1, 0.7))
+        iu, ju = np.triu_indices(n, 1)
+        keep = rng.random(iu.size) < p
+        s, d = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+        if s.size == 0:
+            continue
+        got, _ = gpu_edge_orbits(harp, n, s, d)
+        assert got.tolist() == EB.edge_orbits4_brute(n, s, d).tolist(), (trial, n, p)
+
+
+@pytest.mark.parametrize("make", [lambda: graphgen.ba(1500, 4, 1), lambda: graphgen.er(1200, 10, 3),
+                                  lambda: graphgen.rgg(1500, 12, 4), lambda: graphgen.chung_lu(2500, 2.1, 150, 6, 5)],
+                         ids=["ba1500", "er1200", "rgg1500", "chunglu2500"])
+def test_edge_orbits_generated_graphs_against_the_per_edge_oracle(harp, make):
+    g = make()
+    got, _ = gpu_edge_orbits(harp, g.n, g.src, g.dst)
+    assert got.tolist() == EB.edge_orbits4_combo(g.n, g.src, g.dst).tolist()
+
+
+@pytest.mark.parametrize("scale", [14, 16])
+def test_edge_role_sums_equal_global_counts(harp, scale):
+    g = graphgen.rmat(scale, 16, 0.57, 0.19, 0.19, seed=3)
+    got, counts = gpu_edge_orbits(harp, g.n, g.src, g.dst)
+    sums = got.sum(axis=0, dtype=np.uint64)
+    for r in range(10):
+        want = (int(counts[EB.EDGE_ORBIT_MOTIF[r]]) * EB.EDGE_ORBIT_SIZE[r]) % 2**64
+        assert int(sums[r]) == want, EB.EDGE_ORBITS[r]
