@@ -248,6 +248,20 @@ enum {
 };
 harp_status harp_count4_edge_orbits(const harp_csr* g, uint64_t* orbits_out, uint32_t flags);
 
+/* Connected induced 5-vertex motif counts (the paper's future work, Section VI): counts_out[21] (host)
+ * in the order of the 21 connected 5-vertex classes.  Class order: a labelled graph on vertices 0..4
+ * is a 10-bit mask, bit k for the k-th pair (i, j), i < j, in lexicographic order; its key is the
+ * smallest mask over the 120 vertex permutations; the classes are numbered by increasing (edge count,
+ * key) (harp_motif5_classes gives the keys).  Every connected 5-vertex subset is enumerated once on the
+ * GPU (ESU rooted at each subset's lowest-ranked vertex) and classified by its adjacency mask; the work
+ * is the number of connected 5-subsets, so this is for small and sparse graphs (a 5-vertex closure in
+ * the manner of Section III-F is not built).  Scratch: 36 bytes x maximum degree per thread, at most
+ * 4 GiB.  Blocking on the handle's stream.  Errors: HARP_EINVAL, HARP_ENOMEM, HARP_ECUDA. */
+#define HARP_NMOTIFS5 21
+harp_status harp_count5(const harp_csr* g, uint64_t counts_out[HARP_NMOTIFS5]);
+/* The 21 class keys (10-bit canonical adjacency masks) in count order.  Host only (no device work). */
+harp_status harp_motif5_classes(uint16_t keys_out[HARP_NMOTIFS5]);
+
 /* Per-segment device times of the last count issued with profiling on (milliseconds, measured with
  * CUDA events recorded on the launching stream between the kernels).  Segments, in launch order:
  *   0 orientation (degree ranking, relabelled sorted CSR, out-CSR)

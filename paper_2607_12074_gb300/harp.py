@@ -32,6 +32,7 @@ HARP_NORBITS = 11
 EDGE_ORBITS = ("star_edge", "path_end_edge", "path_mid_edge", "paw_pendant_edge", "paw_hub_edge",
                "paw_far_edge", "cycle_edge", "diamond_spine_edge", "diamond_rim_edge", "clique_edge")
 HARP_NEDGE_ORBITS = 10
+HARP_NMOTIFS5 = 21
 STATS = ("T", "K4", "C4_non", "S_non", "P_non", "paw_non", "D_non", "m")
 
 
@@ -148,6 +149,10 @@ def lib():
         L.harp_count4_orbits.restype = i32
         L.harp_count4_edge_orbits.argtypes = [vp, vp, u32]
         L.harp_count4_edge_orbits.restype = i32
+        L.harp_count5.argtypes = [vp, pu64]
+        L.harp_count5.restype = i32
+        L.harp_motif5_classes.argtypes = [ctypes.POINTER(ctypes.c_uint16)]
+        L.harp_motif5_classes.restype = i32
         L.harp_batch_create.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp)]
         L.harp_batch_count.argtypes = [vp, ctypes.POINTER(harp_plan), vp, vp, vp]
         L.harp_batch_info.argtypes = [vp, pi64, pi64, pi64, ctypes.POINTER(ctypes.c_size_t)]
@@ -354,6 +359,20 @@ def harp_count4_edge_orbits(g: Csr, out=None) -> np.ndarray:
     _check(lib().harp_count4_edge_orbits(g.handle, ctypes.c_void_p(res.ctypes.data if m else 0), HARP_PTR_HOST),
            "harp_count4_edge_orbits")
     return res
+
+
+def harp_count5(g: Csr) -> np.ndarray:
+    """Connected induced 5-vertex motif counts uint64[21], classes in harp_motif5_classes() order."""
+    out = np.zeros(HARP_NMOTIFS5, np.uint64)
+    _check(lib().harp_count5(g.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "harp_count5")
+    return out
+
+
+def harp_motif5_classes() -> list[int]:
+    """The 21 class keys (10-bit canonical adjacency masks over the lexicographic vertex pairs) in order."""
+    keys = (ctypes.c_uint16 * HARP_NMOTIFS5)()
+    _check(lib().harp_motif5_classes(keys), "harp_motif5_classes")
+    return list(keys)
 
 
 def harp_count4_noalloc(n: int, m: int, d_offsets: int, d_cols: int, d_out: int, stream=None) -> None:
