@@ -142,7 +142,9 @@ typedef struct harp_plan {
                                  /* staged in an L2-resident global scratch; above: unstaged        */
                                  /* fallback, every extension a miss                                */
     uint32_t c4_warp_max_work;   /* wedge work W(u) <= this: warp-local hash table                 */
-    uint32_t c4_cta_max_work;    /* W(u) <= this: CTA hash table; above: CTA windowed counters     */
+    uint32_t c4_cta_max_work;    /* W(u) <= this (at most 2048): the middle tier, a warp-local hash */
+                                 /* table of 4096 slots; above: windowed counters (<= c4_warp_max_ */
+                                 /* work turns the middle tier off)                                */
     uint32_t c4_window_bytes;    /* shared-memory bytes of one dense counter window: 200, 100, 64   */
                                  /* or 48 KiB (the largest that fits); 0 = by graph: 200 KiB for a */
                                  /* single graph of more than 2^22 vertices, else 100 KiB          */

@@ -23,7 +23,9 @@
 // (Section III-C explains why a frontier alone must not be reused as an induced state).
 //
 // Work per root W(u) = sum_{w in N-(u)} (pos_w(u) - fpos[w]) picks the execution mode:
-//   W <= warp_max   one warp, hash table in shared memory (warp-local mode)
+//   W <= warp_max   one warp, hash table of 1024 slots in shared memory (warp-local mode)
+//   W <= mid_max    one warp, hash table of 4096 slots (the middle tier: roots with few wedges spread
+//                   over many windows would otherwise cost a whole window pass per window)
 //   larger          one block per (root, grid window): dense packed counters in shared memory
 //                   (CTA mode); lower neighbours are handed to warps in groups of 32, heaviest first,
 //                   and segments of 2048+ elements are split across all warps of the block.  The
@@ -52,6 +54,8 @@ __host__ __device__ constexpr int win_threads(int minb) { return minb == 1 ? 102
 constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallSlots = 1024;            // per-warp hash table (W <= 512)
+constexpr int kMidSlots = 4096;              // per-warp hash table of the middle tier (W <= 2048)
+constexpr int kMidWarps = 2;                 // warps per block of the middle tier (64 KiB of tables)
 constexpr int kLong = 32;                    // segments this long are read warp-coalesced
 constexpr int kSplit = 2048;                 // segments this long are split across the block
 constexpr int kSplitQ = 128;                 // split-queue capacity per window item
@@ -457,13 +461,14 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
                                                      const int32_t* __restrict__ rev,
                                                      const int32_t* __restrict__ gid,
                                                      const int64_t* __restrict__ ginfo, int64_t n, int64_t own_lo,
-                                                     int64_t own_hi, uint32_t warp_max,
+                                                     int64_t own_hi, uint32_t warp_max, uint32_t mid_max,
                                                      int32_t* __restrict__ q_small, int32_t* __restrict__ q_win,
                                                      int32_t* __restrict__ wcount, uint64_t* __restrict__ acc) {
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long* qcnt_small = (unsigned long long*)&acc[Q_C4_MID];
+    unsigned long long* qcnt_mid = (unsigned long long*)&acc[Q_C4_MIDW];
     unsigned long long* qcnt_win = (unsigned long long*)&acc[Q_C4_WIN];
     for (int64_t k = wid; k < n; k += nw) {  // descending rank: the heaviest roots are queued first
         const int32_t u = (int32_t)(n - 1 - k);
@@ -483,6 +488,10 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
                 const unsigned long long slot = atomicAdd(qcnt_small, 1ull);
                 q_small[slot] = u;
                 q_small[n + slot] = (int32_t)W;
+            } else if (W <= mid_max) {  // the middle tier fills the same queue from the back
+                const unsigned long long slot = atomicAdd(qcnt_mid, 1ull);
+                q_small[n - 1 - (int64_t)slot] = u;
+                q_small[2 * n - 1 - (int64_t)slot] = (int32_t)W;
             } else {
                 const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
                 const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
@@ -496,7 +505,10 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
 // ---------------------------------------------------------------------------------------------
 // Warp-local mode: one warp per queued small root, hash table in shared memory.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __restrict__ off,
+// SLOTS hash slots per warp, WARPS warps per block; MID: the middle tier's queue (from the back of
+// q_small, length acc[Q_C4_MIDW]) instead of the warp-local one (from the front, acc[Q_C4_MID]).
+template <int SLOTS, int WARPS, bool MID>
+__global__ void __launch_bounds__(WARPS * 32, 3) k_c4_small(const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ cols,
                                                             const int64_t* __restrict__ loff,
                                                             const int32_t* __restrict__ lcols,
@@ -507,18 +519,19 @@ __global__ void __launch_bounds__(kSmallThreads, 3) k_c4_small(const int64_t* __
                                                             const int32_t* __restrict__ q_small, int64_t n,
                                                             uint64_t* __restrict__ acc, Sink sink) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int32_t* my_keys = reinterpret_cast<int32_t*>(smem_raw) + (threadIdx.x >> 5) * kSmallSlots;
-    uint32_t* my_cnt = reinterpret_cast<uint32_t*>(smem_raw + kSmallWarps * kSmallSlots * sizeof(int32_t)) +
-                       (threadIdx.x >> 5) * kSmallSlots;
+    int32_t* my_keys = reinterpret_cast<int32_t*>(smem_raw) + (threadIdx.x >> 5) * SLOTS;
+    uint32_t* my_cnt = reinterpret_cast<uint32_t*>(smem_raw + WARPS * SLOTS * sizeof(int32_t)) +
+                       (threadIdx.x >> 5) * SLOTS;
     __shared__ uint64_t red[32];
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nq = (int64_t)acc[Q_C4_MID];
+    const int64_t nq = (int64_t)acc[MID ? Q_C4_MIDW : Q_C4_MID];
     uint64_t c4 = 0;
     for (int64_t k = wid; k < nq; k += nw) {
-        const int32_t u = q_small[k];
-        const uint32_t W = (uint32_t)q_small[n + k];
+        const int64_t slot = MID ? n - 1 - k : k;
+        const int32_t u = q_small[slot];
+        const uint32_t W = (uint32_t)q_small[n + slot];
         const int64_t dm = (int64_t)deg[u] - dplus[u];
         const int64_t ub = loff[u];
         uint32_t P = 32;
@@ -823,7 +836,8 @@ unsigned grid_cap(int64_t work, int threads, int64_t cap) {
 
 // The whole wedge pass for one window size (MINB resident window blocks per SM).
 template <int MINB>
-harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool merge, cudaStream_t s) {
+harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, uint32_t mid_max, bool merge,
+                       cudaStream_t s) {
     constexpr int WORDS = win_words(MINB);
     const int64_t n = g->n;
     const int64_t G = ws.G > 0 ? ws.G : 1;
@@ -853,16 +867,24 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, bool
     HARP_LAUNCHED();
     k_c4_classify<WORDS><<<grid_cap(n * 32, 256, (int64_t)sms * 32), 256, 0, s>>>(
         loff, lcols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
-        ws.q_mid, ws.q_win, wcount, ws.acc);
+        mid_max, ws.q_mid, ws.q_win, wcount, ws.acc);
     HARP_LAUNCHED();
     const size_t small_smem = (size_t)kSmallWarps * kSmallSlots * (sizeof(int32_t) + sizeof(uint32_t));
-    HARP_CK(cudaFuncSetAttribute(k_c4_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
-    k_c4_small<<<sms * 3, kSmallThreads, small_smem, s>>>(ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus, ws.fpos,
-                                                          ws.rev, ws.q_mid,
-                                                          n, ws.acc, sink);
+    HARP_CK(cudaFuncSetAttribute(k_c4_small<kSmallSlots, kSmallWarps, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+    k_c4_small<kSmallSlots, kSmallWarps, false><<<sms * 3, kSmallThreads, small_smem, s>>>(
+        ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.q_mid, n, ws.acc, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_C4_SMALL));
-    HARP_CK(prof_mark(s, SEG_C4_MID));  // the CTA-hash mode is folded into the windowed mode
+    if (mid_max > warp_max) {  // the middle tier: 4096-slot warp tables, three 2-warp blocks per SM
+        const size_t mid_smem = (size_t)kMidWarps * kMidSlots * (sizeof(int32_t) + sizeof(uint32_t));
+        HARP_CK(cudaFuncSetAttribute(k_c4_small<kMidSlots, kMidWarps, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_smem));
+        k_c4_small<kMidSlots, kMidWarps, true><<<sms * 3, kMidWarps * 32, mid_smem, s>>>(
+            ws.off, ws.cols, loff, lcols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.q_mid, n, ws.acc, sink);
+        HARP_LAUNCHED();
+    }
+    HARP_CK(prof_mark(s, SEG_C4_MID));
     HARP_TRY(exclusive_scan_i32_to_i64(wcount, ws.win_prefix, n, ws.scan_tmp, ws.scan_tmp_len, s));
     const size_t win_smem = (size_t)WORDS * sizeof(uint32_t);
     HARP_CK(cudaFuncSetAttribute(k_c4_window<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
@@ -881,6 +903,10 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     if (g->n == 0 || g->m == 0) return HARP_OK;
     uint32_t warp_max = plan.c4_warp_max_work ? plan.c4_warp_max_work : 512;
     if (warp_max > kSmallSlots / 2) warp_max = kSmallSlots / 2;
+    // the middle tier takes kMidSlots / 2 wedges at most; c4_cta_max_work <= warp_max turns it off
+    uint32_t mid_max = plan.c4_cta_max_work;
+    if (mid_max > kMidSlots / 2) mid_max = kMidSlots / 2;
+    if (mid_max < warp_max) mid_max = warp_max;
     // window size: the largest of the four that fits plan.c4_window_bytes (at least the smallest).
     // 0 = by graph: a single graph of more than 2^22 vertices takes 200 KiB (its x-range spans tens to
     // hundreds of 100 KiB windows, and halving the (root, window) visits measured 37.7 -> 26.1 s on
@@ -889,10 +915,10 @@ harp_status count_wedge_c4(const harp_csr* g, Workspace& ws, const harp_plan& pl
     const bool merge = !(plan.flags & HARP_PLAN_NO_BAND_MERGE);
     uint32_t wbytes = plan.c4_window_bytes;
     if (wbytes == 0) wbytes = (ws.G <= 1 && g->n > ((int64_t)1 << 22)) ? (uint32_t)kWinWords1 * 4 : (uint32_t)kWinWords2 * 4;
-    if (wbytes >= (uint32_t)kWinWords1 * 4) return wedge_pass<1>(g, ws, warp_max, merge, s);
-    if (wbytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, merge, s);
-    if (wbytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, merge, s);
-    return wedge_pass<4>(g, ws, warp_max, merge, s);
+    if (wbytes >= (uint32_t)kWinWords1 * 4) return wedge_pass<1>(g, ws, warp_max, mid_max, merge, s);
+    if (wbytes >= (uint32_t)kWinWords2 * 4) return wedge_pass<2>(g, ws, warp_max, mid_max, merge, s);
+    if (wbytes >= (uint32_t)kWinWords3 * 4) return wedge_pass<3>(g, ws, warp_max, mid_max, merge, s);
+    return wedge_pass<4>(g, ws, warp_max, mid_max, merge, s);
 }
 
 }  // namespace harp

@@ -92,6 +92,7 @@ enum : int {
     ACC_LIT_STAR = 51,     // sum over vertices of the H_u star form (mod 2^64)
     ACC_LIT_T = 52,        // triangles enumerated by the literal triangle pass
     ACC_SIG_LOOKUPS = 53,  // literal basis: frontier requests to the signature cache
+    Q_C4_MIDW = 54,        // length of the wedge middle tier's queue (from the back of q_mid)
     kOutLen = 64
 };
 

@@ -87,7 +87,7 @@ void default_plan(harp_plan* p) {
     p->tri_cta_max = 1024;
     p->tri_big_max = 4096;
     p->c4_warp_max_work = 512;
-    p->c4_cta_max_work = 8192;
+    p->c4_cta_max_work = 2048;
     p->c4_window_bytes = 0;  // by graph size (count_wedge_c4)
     p->flags = 0;
     p->est_halo = 1.0;
@@ -226,7 +226,7 @@ extern "C" harp_status harp_select_anchors(const harp_csr* g, const harp_select_
     p.est_cost_lit = J_lit;
     // Execution-mode thresholds: light graphs keep more roots in warp-local mode.
     p.c4_warp_max_work = mean_deg < 8 ? 512 : 256;
-    p.c4_cta_max_work = 8192;
+    p.c4_cta_max_work = 2048;
     // out->version picks the layout written: 1 = a version-1 plan (ends at `objective`), else current
     if (out->version == 1) p.version = 1;
     std::memcpy(out, &p, plan_bytes(&p));

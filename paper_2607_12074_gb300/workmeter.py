@@ -86,7 +86,7 @@ def _merged_windows(bounds, widths, mask, u, words):
     return total
 
 
-def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=0):
+def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=0, c4_mid_max=2048):
     """Per-kernel work and algorithmic bytes (dict of dicts) under the given wedge plan fields."""
     G = rank_space(n, src, dst)
     m = G["m"]
@@ -136,8 +136,11 @@ def meter(n, src, dst, c4_warp_max=512, c4_window_bytes=0):
     seg = np.maximum(pos[rev] - fpos[rw], 0)
     W = np.bincount(ru, weights=seg, minlength=n).astype(np.int64)
     dm = split
-    # warp-local hash mode for W <= c4_warp_max, windowed counters above (no middle tier)
-    tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= min(c4_warp_max, 512), 0, 2))
+    # warp-local hash mode for W <= c4_warp_max (1024 slots), the middle tier for W <= c4_mid_max (4096
+    # slots), windowed counters above
+    wmax = min(c4_warp_max, 512)
+    mmax = max(min(c4_mid_max, 2048), wmax)
+    tier = np.where((dm < 2) | (W == 0), -1, np.where(W <= wmax, 0, np.where(W <= mmax, 1, 2)))
     words = window_words(c4_window_bytes, n)
     bounds = band_starts + [n]
     # narrow bands may merge into the next wider one: the mask with the fewest degree-weighted windows

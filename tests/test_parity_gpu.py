@@ -246,3 +246,17 @@ def test_band_merging_never_changes_counts(harp):
             p.c4_warp_max_work = wm
             p.flags = flags
             assert harp.count4_edges(g.n, g.src, g.dst, p).tolist() == want, (wm, flags)
+
+
+def test_wedge_middle_tier_never_changes_counts(harp):
+    """Roots with wedge work between the warp limit and c4_cta_max_work (at most 2048) take the middle
+    tier (a 4096-slot warp hash) instead of the windows: off, default, and every root up to 2048 wedges
+    in it (warp limit 1) all give the oracle's counts, on a skewed and a flat graph."""
+    for g in (graphgen.rmat(15, 16, seed=21), graphgen.chung_lu(60000, 2.1, 2500, 10, 8), graphgen.er(20000, 24, 3)):
+        want = O.count4_combo(g.n, g.src, g.dst).tolist()
+        for wm, mid in ((0, 1), (0, 0), (1, 2048), (256, 1024)):
+            p = harp.harp_plan()
+            p.version = harp.HARP_ABI_VERSION
+            p.c4_warp_max_work = wm
+            p.c4_cta_max_work = mid
+            assert harp.count4_edges(g.n, g.src, g.dst, p).tolist() == want, (g.name, wm, mid)

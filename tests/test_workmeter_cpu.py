@@ -80,12 +80,15 @@ def test_wedge_and_probe_totals(name):
 
 
 def test_warp_limit_moves_roots_to_the_windows():
-    """Roots with work W(u) <= the warp limit take the warp hash, the rest the windowed counters."""
+    """Roots with work W(u) <= the warp limit take the warp hash, those up to the middle limit the
+    middle tier's larger hash, the rest the windowed counters."""
     g = graphgen.ba(400, 5, 3)
     adj = rank_adjacency(g.n, g.src, g.dst)
     _, per_root = brute_wedges(adj)
     dm = [sum(1 for x in adj[u] if x < u) for u in range(len(adj))]
-    for limit in (1, 16, 64):
-        m = workmeter.meter(g.n, g.src, g.dst, c4_warp_max=limit)
-        assert m["c4_window"]["wedges"] == sum(w for u, w in enumerate(per_root) if dm[u] >= 2 and w > limit)
+    for limit, mid in ((1, 1), (16, 16), (64, 64), (16, 200), (64, 2048)):
+        m = workmeter.meter(g.n, g.src, g.dst, c4_warp_max=limit, c4_mid_max=mid)
+        assert m["c4_window"]["wedges"] == sum(w for u, w in enumerate(per_root) if dm[u] >= 2 and w > mid)
+        assert m["c4_mid"]["wedges"] == sum(w for u, w in enumerate(per_root) if dm[u] >= 2 and limit < w <= mid)
+        assert m["c4_mid"]["items"] == m["c4_mid"]["roots"]
         assert m["c4_small"]["wedges"] == sum(w for u, w in enumerate(per_root) if dm[u] >= 2 and 0 < w <= limit)
