@@ -164,6 +164,20 @@ def oracle_sample_rate(scale: int, threads: int = 0, counts: bool = False):
     return r
 
 
+def oracle_a_rate():
+    """Oracle A (Wernicke's ESU over every connected 4-subset, one thread) on the plain small graph
+    (Barabasi-Albert n = 2000, 4 edges per new vertex, seed 1), in a fresh process."""
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import graphgen, oracle\n"
+        "g = graphgen.ba_2000()\n"
+        "m, _ = oracle.graph_summary(g.n, g.src, g.dst)\n"
+        "t = time.perf_counter(); c = oracle.count4_esu(g.n, g.src, g.dst, 1); t = time.perf_counter() - t\n"
+        "print(json.dumps({'m': m, 'seconds': t, 'counts': [int(x) for x in c]}))\n" % (ROOT,))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def max_over_ranks(value: float, world: int, device: str) -> float:
     """The largest value over all ranks (a replicated job takes as long as its slowest rank)."""
     if world <= 1:
@@ -643,6 +657,14 @@ def main():
                          f"seed 1; m={r['m']}), oracle count4_combo (non-induced counts + inversion, OpenMP), "
                          f"one run of {r['seconds']:.1f} s",
                "counts_equal_gpu": [int(x) for x in counts] == r["counts"]}
+        # Oracle A (the plain definition by ESU, one thread) on the plain small graph, against the GPU
+        ra = oracle_a_rate()
+        ga = graphgen.ba_2000()
+        ca = harp.count4_edges(ga.n, ga.src, ga.dst)
+        cpu["oracle_a"] = {"value": ra["m"] / ra["seconds"], "unit": UNIT, "threads": 1, "seconds": ra["seconds"],
+                           "sample": f"Barabasi-Albert n=2000, 4 edges per new vertex, seed 1 (m={ra['m']}), "
+                                     "oracle count4_esu (every connected 4-subset once, Wernicke's ESU)",
+                           "counts_equal_gpu": [int(x) for x in ca] == ra["counts"]}
     value = replica_throughput(m, world, t_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
