@@ -177,24 +177,67 @@ __device__ __forceinline__ void probe_list(const int32_t* __restrict__ colsp, in
     }
 }
 
-// Probe every element of colsp[b, e) (an exact range: no clip tests, no early exit), kRangeUnroll
-// warp-wide chunks of loads in flight.
-constexpr int kRangeUnroll = 4;
-
-template <typename F>
-__device__ __forceinline__ void probe_range(const int32_t* __restrict__ colsp, int64_t b, int64_t e, F&& probe) {
-    const int l = lane_id();
-    for (int64_t p0 = b; p0 < e; p0 += 32 * kRangeUnroll) {
-        int32_t ys[kRangeUnroll];
-#pragma unroll
-        for (int r = 0; r < kRangeUnroll; ++r) {
-            const int64_t p = p0 + r * 32 + l;
-            ys[r] = p < e ? colsp[p] : 0;
+// Probe every element of colsp[b, e) (an exact range) with 16-byte loads.  The range is widened to
+// 4-element boundaries: colsp starts on a 256-byte boundary and its allocation is padded to a multiple
+// of 256 bytes, so the wider loads stay inside it; lane l takes elements a + 128 k + 4 l .. + 3 (a = b
+// rounded down to a multiple of 4) and masks those outside [b, e).  visit(y, p) gets the element and
+// its position in colsp.
+// With `filter` (warp-uniform) the membership test may_hold(y) (a filter bit: 0 proves y absent) runs
+// first on all four elements and the lane then visits only those that pass, so 128 elements pay for
+// the divergent lookup and hit paths once per candidate of the busiest lane, instead of once per 32
+// elements whenever any lane holds a candidate.  Without it (rows where hits are common) every
+// element is visited.
+template <typename Filter, typename Visit>
+__device__ __forceinline__ void probe_filtered(const int32_t* __restrict__ colsp, int64_t b, int64_t e, bool filter,
+                                               Filter&& may_hold, Visit&& visit) {
+    const int64_t a = b & ~(int64_t)3;
+    const int4* __restrict__ v = reinterpret_cast<const int4*>(colsp + a);
+    const int lo = (int)(b - a), hi = (int)(e - a);  // the range's offsets from a: lo <= 3
+    for (int q = 4 * lane_id(); q < hi; q += 128) {
+        const int4 y = __ldg(v + (q >> 2));
+        uint32_t valid = hi - q >= 4 ? 0xfu : (1u << (hi - q)) - 1u;
+        if (q < lo) valid &= 0xfu << (lo - q);
+        if (filter) {
+            uint32_t cand = may_hold(y.x) | (may_hold(y.y) << 1) | (may_hold(y.z) << 2) | (may_hold(y.w) << 3);
+            cand &= valid;
+            while (cand) {
+                const int r = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int32_t x = r == 0 ? y.x : (r == 1 ? y.y : (r == 2 ? y.z : y.w));
+                visit(x, a + q + r);
+            }
+        } else {
+            if (valid & 1u) visit(y.x, a + q);
+            if (valid & 2u) visit(y.y, a + q + 1);
+            if (valid & 4u) visit(y.z, a + q + 2);
+            if (valid & 8u) visit(y.w, a + q + 3);
         }
-#pragma unroll
-        for (int r = 0; r < kRangeUnroll; ++r)
-            if (p0 + r * 32 + l < e) probe(ys[r], p0 + r * 32 + l);
     }
+}
+
+// Whether the next row is probed through the membership filter: the filter pays while hits are rare.
+// Each warp keeps its own probe and hit totals over the rows it has taken (halved past 2^20 probes, so
+// they follow the current anchors) and filters while fewer than one probe in eight has hit.
+struct FilterChoice {
+    uint32_t probes = 0, hits = 0;
+    __device__ __forceinline__ bool use() const { return 8u * hits <= probes; }
+    __device__ __forceinline__ void add(int64_t row_probes, uint32_t row_hits) {
+        probes += (uint32_t)row_probes;
+        hits += row_hits;
+        if (probes > (1u << 20)) {
+            probes >>= 1;
+            hits >>= 1;
+        }
+    }
+};
+
+// Membership filter in front of the hash lookup: bit (top FB bits of hash32(y)) is set for every key,
+// so a clear bit proves y is not in L (most probes miss; a miss then costs one shared load).
+template <int FB>
+__device__ __forceinline__ uint32_t filter_may_hold(const uint32_t* filt, int32_t y) {
+    const uint32_t h = hash32((uint32_t)y) >> (32 - FB);
+    const uint32_t w = filt[h >> 5];
+    return __funnelshift_r(w, w, h) & 1u;  // bit (h mod 32) of the word: the rotate takes h mod 32
 }
 
 // single-graph mode: one block reduction and one atomic per statistic at the end of the kernel;
@@ -221,6 +264,7 @@ __device__ __forceinline__ void flush_block(const Sink& sink, uint64_t tri, uint
 constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
 constexpr int kWarpHashBits = 7;  // 128 slots for <= 32 keys: load <= 1/4, ~1.4 slot reads per miss
+constexpr int kWarpFilterBits = 10;  // membership filter of 1024 bits: false positives <= 32 / 1024
 
 template <bool BS>
 __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __restrict__ offp,
@@ -233,10 +277,12 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
     __shared__ uint32_t sRow[kWarpsPerBlock][32];
     __shared__ int32_t sHk[kWarpsPerBlock][1 << kWarpHashBits];
     __shared__ uint8_t sHv[kWarpsPerBlock][1 << kWarpHashBits];
+    __shared__ uint32_t sFilt[kWarpsPerBlock][(1 << kWarpFilterBits) / 32];
     __shared__ uint64_t red[32];
     const int w = threadIdx.x >> 5, l = lane_id();
     const int64_t nq = (int64_t)cnt[0];
     uint64_t tri = 0, k4 = 0, paw = 0, hits = 0;
+    FilterChoice fc;
     for (int64_t k = ((int64_t)blockIdx.x * kWarpsPerBlock + w); k < nq; k += (int64_t)gridDim.x * kWarpsPerBlock) {
         const int32_t u = q[k];
         const int64_t ub = offp[u];
@@ -246,8 +292,13 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         sRow[w][l] = 0;
 #pragma unroll
         for (int hs = 0; hs < (1 << kWarpHashBits); hs += 32) sHk[w][l + hs] = kNoKey;
+        sFilt[w][l] = 0;
         __syncwarp();
-        if (!BS && l < d) hash_put(sHk[w], sHv[w], kWarpHashBits, x, l);
+        if (l < d) {
+            if (!BS) hash_put(sHk[w], sHv[w], kWarpHashBits, x, l);
+            const uint32_t h = hash32((uint32_t)x) >> (32 - kWarpFilterBits);
+            atomicOr(&sFilt[w][h >> 5], 1u << (h & 31));
+        }
         __syncwarp();
         const int32_t last = sL[w][d - 1];
         auto lookup = [&](int32_t y) {
@@ -265,14 +316,17 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         for (int i = 0; i < d - 1; ++i) {
             const int64_t b = __shfl_sync(kFull, myb, i), e = __shfl_sync(kFull, mye, i);
             uint32_t row = 0;
-            probe_range(colsp, b, e, [&](int32_t y, int64_t p) {  // y is in [next, last] already
-                const int j = lookup(y);
-                if (j >= 0) {
-                    atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
-                    row |= 1u << j;
-                }
-            });
+            probe_filtered(colsp, b, e, fc.use(),
+                           [&](int32_t y) { return filter_may_hold<kWarpFilterBits>(sFilt[w], y); },
+                           [&](int32_t y, int64_t p) {  // y is in [next, last] already
+                               const int j = lookup(y);
+                               if (j >= 0) {
+                                   atomicAdd(&te[p], 1u);  // arc (v, y): top edge of triangle (u, v, y)
+                                   row |= 1u << j;
+                               }
+                           });
             row = __reduce_or_sync(kFull, row);
+            fc.add(e - b, (uint32_t)__popc(row));  // each set bit is one hit
             col += (row >> l) & 1u;
             if (l == i) sRow[w][i] = row;
         }
@@ -330,10 +384,11 @@ struct CtaSmem {
     static constexpr int W = DMAX / 32;             // words per row
     static constexpr int WS = W | 1;                // odd row stride: no bank conflicts
     static constexpr int HB = (DMAX <= 256) ? 10 : ((DMAX <= 512) ? 11 : 12);  // 4 * DMAX hash slots
-    static constexpr int FB = HB + 2;                                          // filter: 16 bits per key
+    // filter: 64 bits per key (2, 4 and 8 KB); false positives at most d / 2^FB <= 1 / 64
+    static constexpr int FB = HB + 4;
     // The 256 and 1024 modes resolve every row's exact probe range up front (one binary search per
-    // thread per bound); the 512 mode keeps the warp-wide search per row: the two range arrays would
-    // cost it a resident block per SM.
+    // thread per bound); the 512 mode finds each row's range with the warp-wide search when the row
+    // is taken: the two range arrays would cost it a resident block per SM.
     static constexpr bool PRE = DMAX <= 256 || DMAX >= 1024;
     int32_t L[DMAX];
     uint32_t own[DMAX];
@@ -347,13 +402,6 @@ struct CtaSmem {
     uint64_t red[32];
 };
 
-// Membership filter in front of the hash lookup: bit (top FB bits of hash32(y)) is set for every key,
-// so a clear bit proves y is not in L (most probes miss; a miss then costs one shared load).
-template <int FB>
-__device__ __forceinline__ bool filter_may_hold(const uint32_t* filt, int32_t y) {
-    const uint32_t h = hash32((uint32_t)y) >> (32 - FB);
-    return (filt[h >> 5] >> (h & 31)) & 1u;
-}
 
 template <int DMAX, int THREADS, int MINB, bool BS>
 __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __restrict__ offp,
@@ -372,6 +420,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
     const int w = threadIdx.x >> 5, l = lane_id();
     const int64_t nq = (int64_t)cnt[1];
     uint64_t tri = 0, k4 = 0, paw = 0, hits = 0;
+    FilterChoice fc;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ticket, 1ull);
         __syncthreads();
@@ -410,91 +459,66 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
             if (!filter_may_hold<S::FB>(s.filt, y)) return -1;
             return BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
         };
-        // rows: warp per row, ordered intersection of N+(L[i]) with L
+        // rows: warp per row, ordered intersection of N+(L[i]) with L over the exact range of N+(L[i]) in
+        // [L[i+1], max L] (no smaller element can be in L after L[i], no larger one at all)
         for (int i = w; i < d - 1; i += NW) {
-            const int32_t next = s.L[i + 1];
             int64_t b = 0, e = 0;
             if (S::PRE) {
                 b = s.rb[i];
                 e = s.re[i];
             } else {
                 const int32_t v = s.L[i];
-                e = offp[v + 1];
-                b = offp[v];
-                if (e - b > 64) b = warp_lower_bound(colsp, b, e, next);
+                const int64_t e0 = offp[v + 1];
+                b = warp_lower_bound(colsp, offp[v], e0, s.L[i + 1]);
+                e = warp_lower_bound(colsp, b, e0, last + 1);
             }
+            uint32_t* Ri = &s.R[i * WS];
             uint32_t hits = 0;
-            auto probe = [&](int32_t y, int64_t p) {
-                if (y >= next && y <= last) {
-                    const int j = lookup(y);
-                    if (j >= 0) {
-                        atomicAdd(&te[p], 1u);
-                        atomicOr(&s.R[i * WS + (j >> 5)], 1u << (j & 31));
-                        atomicAdd(&s.own[j], 1u);
-                        ++hits;
-                    }
-                }
-            };
-            if (S::PRE) {
-                probe_range(colsp, b, e, [&](int32_t y, int64_t p) {  // y is in [next, last] already
-                    const int jj = lookup(y);
-                    if (jj >= 0) {
-                        atomicAdd(&te[p], 1u);
-                        atomicOr(&s.R[i * WS + (jj >> 5)], 1u << (jj & 31));
-                        atomicAdd(&s.own[jj], 1u);
-                        ++hits;
-                    }
-                });
-            } else {
-                probe_list(colsp, b, e, last, probe);
-            }
+            probe_filtered(colsp, b, e, fc.use(), [&](int32_t y) { return filter_may_hold<S::FB>(s.filt, y); },
+                           [&](int32_t y, int64_t p) {
+                               const int j = BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
+                               if (j >= 0) {
+                                   atomicAdd(&te[p], 1u);  // arc (L[i], y): top edge of triangle (u, L[i], y)
+                                   atomicOr(&Ri[j >> 5], 1u << (j & 31));
+                                   atomicAdd(&s.own[j], 1u);
+                                   ++hits;
+                               }
+                           });
             hits = warp_sum(hits);
+            fc.add(e - b, hits);
             if (l == 0 && hits) atomicAdd(&s.own[i], hits);
         }
         __syncthreads();
-        // 4-cliques: warp per row i; the set bits j of row i are dealt to the lanes (32 per round), and
-        // each lane adds popc(row_i & row_j) over the words from j's word on.
+        // triangles and 4-cliques (the X_3 extension): the bitmap's (word, row) units are dealt to all the
+        // block's threads.  Unit (x, i) counts the set bits j of word x of row i (the triangles (u, L[i],
+        // L[j])) and adds |row_i n row_j| for each, over the words from x on (row j has no bit at or
+        // below j), so the work is spread by the bits themselves and no lane searches for its bit.  A
+        // warp's lanes take one word of consecutive rows: equal word spans, conflict-free row reads.
         uint64_t a_tri = 0, a_k4 = 0, a_paw = 0;
-        for (int i = w; i < d - 1; i += NW) {
+        const int rows = d - 1;  // row d - 1 is empty
+        for (int t = threadIdx.x; t < rows * W; t += THREADS) {
+            const int x = t / rows, i = t - x * rows;
+            if ((x << 5) + 31 <= i) continue;  // row i has no bit at or below i
             const uint32_t* Ri = &s.R[i * WS];
-            const uint32_t myw = l < W ? Ri[l] : 0u;  // W <= 32: lane l holds word l of the row
-            const int c = __popc(myw);
-            int pre = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, pre, o);
-                if (l >= o) pre += y;
-            }
-            const int B = __shfl_sync(kFull, pre, 31);  // bits in the row = triangles (u, L[i], *)
-            pre -= c;
-            a_tri += (l == 0) ? (uint64_t)B : 0;
-            for (int k0 = 0; k0 < B; k0 += 32) {
-                const int k = k0 + l;
-                int o = 0;  // word holding the k-th set bit: last lane with pre <= k
-#pragma unroll
-                for (int sft = 16; sft >= 1; sft >>= 1) {
-                    const int e = __shfl_sync(kFull, pre, o + sft);
-                    if (e <= k) o += sft;
-                }
-                const uint32_t word = __shfl_sync(kFull, myw, o);
-                const int rank = k - __shfl_sync(kFull, pre, o);
-                if (k < B) {
-                    const int j = (o << 5) + (int)__fns(word, 0, rank + 1);
-                    uint32_t cnt = 0;
-                    if (reuse) {  // the staged frontier of (u, L[j])
-                        const uint32_t* Rj = &s.R[j * WS];
-                        for (int x = o; x < W; ++x) cnt += __popc(Ri[x] & Rj[x]);
-                    } else {      // recompute from N+(L[j]) in global memory
-                        const int32_t wv = s.L[j];
-                        for (int64_t p = offp[wv], pe = offp[wv + 1]; p < pe; ++p) {
-                            const int32_t y = colsp[p];
-                            if (y > last) break;
-                            const int jj = lookup(y);
-                            if (jj >= 0 && ((Ri[jj >> 5] >> (jj & 31)) & 1u)) ++cnt;
-                        }
+            uint32_t bits = Ri[x];
+            a_tri += (uint64_t)__popc(bits);
+            while (bits) {
+                const int j = (x << 5) + __ffs(bits) - 1;
+                bits &= bits - 1;
+                uint32_t cnt = 0;
+                if (reuse) {  // the staged frontier of (u, L[j])
+                    const uint32_t* Rj = &s.R[j * WS];
+                    for (int y = x; y < W; ++y) cnt += __popc(Ri[y] & Rj[y]);
+                } else {      // recompute from N+(L[j]) in global memory
+                    const int32_t wv = s.L[j];
+                    for (int64_t p = offp[wv], pe = offp[wv + 1]; p < pe; ++p) {
+                        const int32_t y = colsp[p];
+                        if (y > last) break;
+                        const int jj = lookup(y);
+                        if (jj >= 0 && ((Ri[jj >> 5] >> (jj & 31)) & 1u)) ++cnt;
                     }
-                    a_k4 += cnt;
                 }
+                a_k4 += cnt;
             }
         }
         for (int i = threadIdx.x; i < d; i += THREADS) {
