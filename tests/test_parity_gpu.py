@@ -119,6 +119,20 @@ def test_rmat_scale20_full_workload(harp):
     assert counts.tolist() == gold["counts"]
 
 
+def test_rmat_scale20_repeated_counts(harp):
+    """Eight counts of the bench workload, each on a fresh handle (fresh workspace memory; device and
+    host inputs alternating), all equal to the stored counts: a race or an undefined read in a kernel
+    shows up as an occasional count that differs from the rest, which one count alone would catch
+    only by chance."""
+    with open(os.path.join(HERE, "golden", "rmat20_oracle.json")) as f:
+        gold = json.load(f)
+    g = graphgen.rmat_scale20()
+    for k in range(8):
+        counts, stats = gpu_count(harp, g.n, g.src, g.dst, device_input=(k % 2 == 0))
+        assert stats.tolist() == gold["stats"], k
+        assert counts.tolist() == gold["counts"], k
+
+
 def test_host_and_device_inputs_agree(harp):
     g = graphgen.ba(3000, 6, 5)
     a, _ = gpu_count(harp, g.n, g.src, g.dst, device_input=True)
