@@ -9,15 +9,17 @@
 // Output (workspace): deg, order (new -> old), perm (old -> new), off/cols (relabelled CSR with
 // every row sorted), dplus, offp/colsp (out-CSR: only N+), te zeroed, S = sum_v C(d_v, 3).
 //
-// Rows are sorted by three kernels chosen by degree: a warp bitonic network for d <= 32 (every row
-// is visited), a shared-memory bitonic sort for d <= 4096 and a per-row LSD radix sort through global
-// memory for hubs (both from queues filled by the relabel pass).
+// Rows are sorted by four kernels chosen by degree: a warp bitonic network in registers for d <= 32
+// (every row is visited), a warp bitonic sort in the warp's shared buffer for d <= 256, a block
+// bitonic sort in shared memory for d <= 4096 and a per-row LSD radix sort through global memory for
+// hubs (the last three from queues filled by the relabel pass; the warp and block sorts share one).
 #include "harp_internal.cuh"
 
 namespace harp {
 namespace {
 
 constexpr int kTierA = 32;
+constexpr int kTierB1 = 256;
 constexpr int kTierB = 4096;
 
 int bits_for(int64_t x) {
@@ -135,7 +137,61 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restric
     }
 }
 
-// Tier B: 32 < d <= 4096, one block per row, bitonic sort in shared memory.
+// Tier B1: 32 < d <= 256, one warp per row, bitonic sort in the warp's shared buffer (a block per
+// row would leave most of its warps idle behind a block barrier at every stage).
+constexpr int kMidWarps = 8;
+
+__global__ void __launch_bounds__(kMidWarps * 32) k_sort_rows_mid(const int64_t* __restrict__ goff,
+                                                                   const int32_t* __restrict__ gcols,
+                                                                   const int32_t* __restrict__ order,
+                                                                   const int32_t* __restrict__ perm,
+                                                                   const int32_t* __restrict__ deg,
+                                                                   const int64_t* __restrict__ off, int64_t n,
+                                                                   int32_t* __restrict__ cols,
+                                                                   int32_t* __restrict__ dplus,
+                                                                   const int32_t* __restrict__ q,
+                                                                   const unsigned long long* __restrict__ qcnt) {
+    __shared__ int32_t sbuf[kMidWarps][kTierB1];
+    const int w = threadIdx.x >> 5, l = lane_id();
+    int32_t* buf = sbuf[w];
+    const int64_t nq = (int64_t)qcnt[0];
+    for (int64_t qi = (int64_t)blockIdx.x * kMidWarps + w; qi < nq; qi += (int64_t)gridDim.x * kMidWarps) {
+        const int64_t i = q[qi];
+        const int d = deg[i];
+        if (d > kTierB1) continue;  // the block sort's row
+        int P = 64;
+        while (P < d) P <<= 1;
+        const int64_t src = goff[order[i]];
+        for (int k = l; k < P; k += 32) buf[k] = (k < d) ? perm[gcols[src + k]] : 0x7fffffff;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = l; t < (P >> 1); t += 32) {
+                    const int a = 2 * t - (t & (j - 1));  // index with bit j clear
+                    const int c = a + j;
+                    const bool up = (a & k) == 0;
+                    const int32_t x = buf[a], y = buf[c];
+                    if ((x > y) == up) {
+                        buf[a] = y;
+                        buf[c] = x;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int below = 0;
+        for (int k = l; k < d; k += 32) {
+            const int32_t x = buf[k];
+            cols[off[i] + k] = x;
+            below += x < (int32_t)i;
+        }
+        below = warp_sum(below);
+        if (l == 0) dplus[i] = d - below;
+        __syncwarp();  // every lane has read the buffer before the next row fills it
+    }
+}
+
+// Tier B: 256 < d <= 4096, one block per row, bitonic sort in shared memory.
 __global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restrict__ goff,
                                                          const int32_t* __restrict__ gcols,
                                                          const int32_t* __restrict__ order,
@@ -152,6 +208,7 @@ __global__ void __launch_bounds__(512) k_sort_rows_block(const int64_t* __restri
     for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
         const int64_t i = q[qi];
         const int d = deg[i];
+        if (d <= kTierB1) continue;  // the warp sort's row (the same value in every thread)
         int P = 64;
         while (P < d) P <<= 1;
         const int64_t src = goff[order[i]];
@@ -336,7 +393,9 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     HARP_LAUNCHED();
     uint64_t* k0 = ws.vkeys;
     uint64_t* k1 = ws.vkeys_alt;
-    HARP_TRY(radix_sort_u64(&k0, &k1, n, 0, b + bd + bg, ws.hist, ws.scan_tmp, ws.scan_tmp_len, s));
+    // the keys are written in id order and every pass is stable, so only the graph and degree bits
+    // need sorting: equal (graph, degree) keep ascending ids
+    HARP_TRY(radix_sort_u64(&k0, &k1, n, b, b + bd + bg, ws.hist, ws.scan_tmp, ws.scan_tmp_len, s));
     unsigned long long* qsort = (unsigned long long*)&ws.acc[Q_SORT_CTA];
     k_relabel<<<grid_for(n, 256), 256, 0, s>>>(k0, n, b, bd, ws.order, ws.perm, ws.deg, ws.gid_in, ws.gid, ws.q_tri,
                                                qsort);
@@ -345,6 +404,9 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     if (m > 0) {
         k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
                                                                 ws.off, n, ws.cols, ws.dplus);
+        HARP_LAUNCHED();
+        k_sort_rows_mid<<<num_sms() * 8, kMidWarps * 32, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
+                                                                 ws.off, n, ws.cols, ws.dplus, ws.q_tri, qsort);
         HARP_LAUNCHED();
         k_sort_rows_block<<<num_sms() * 4, 512, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg, ws.off, n,
                                                    ws.cols, ws.dplus, ws.q_tri, qsort);
