@@ -231,6 +231,28 @@ struct FilterChoice {
     }
 };
 
+// Row i's hits can be found from either side: probe every element of its range (one load and a
+// filter or hash lookup each), or search each of the keys of L left after L[i] in the range (a binary
+// search of about log2(len) + 1 dependent loads each, which the row's few cache lines keep in L1).
+// Searching costs less when keys * (log2(len) + 1) < 2 * len: rows near the end of L and rows of long
+// ranges.  Both find exactly the members of L in the range.
+__device__ __forceinline__ bool row_searches(int keys, int64_t len) {
+    if (len <= 0) return false;  // no element: nothing to do either way
+    const int lg = 64 - __clzll(len);  // floor(log2(len)) + 1
+    return (int64_t)keys * lg < 2 * len;
+}
+
+// Position of key in the sorted colsp[b, b + len), or -1.
+__device__ __forceinline__ int64_t find_in_range(const int32_t* __restrict__ colsp, int64_t b, int len, int32_t key) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(colsp + b + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < len && __ldg(colsp + b + lo) == key) ? b + lo : -1;
+}
+
 // Membership filter in front of the hash lookup: bit (top FB bits of hash32(y)) is set for every key,
 // so a clear bit proves y is not in L (most probes miss; a miss then costs one shared load).
 template <int FB>
@@ -312,8 +334,42 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
             myb = b0 + lower_bound_i32(colsp + b0, e0 - b0, sL[w][l + 1]);
             mye = myb + lower_bound_i32(colsp + myb, e0 - myb, sL[w][d - 1] + 1);
         }
-        uint32_t col = 0;  // # rows with bit l
+        // rows that search (see row_searches): their (row, key) pairs are flattened over the lanes, so
+        // one round of binary searches covers several short rows; pair t belongs to the last row whose
+        // first pair is at or before t
+        const bool mysearch = l < d - 1 && row_searches(d - 1 - l, mye - myb);
+        const uint32_t searching = __ballot_sync(kFull, mysearch);
+        const int npairs = mysearch ? d - 1 - l : 0;
+        int incl = npairs;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (l >= o) incl += y;
+        }
+        const int excl = incl - npairs;
+        const int total = __shfl_sync(kFull, incl, 31);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + l;
+            int o = 0;
+#pragma unroll
+            for (int sft = 16; sft >= 1; sft >>= 1) {
+                const int e = __shfl_sync(kFull, excl, o + sft);
+                if (e <= t) o += sft;
+            }
+            const int64_t rb = __shfl_sync(kFull, myb, o), re = __shfl_sync(kFull, mye, o);
+            const int oe = __shfl_sync(kFull, excl, o);
+            if (t < total) {
+                const int j = o + 1 + (t - oe);
+                const int64_t p = find_in_range(colsp, rb, (int)(re - rb), sL[w][j]);
+                if (p >= 0) {
+                    atomicAdd(&te[p], 1u);  // arc (L[o], L[j]): top edge of triangle (u, L[o], L[j])
+                    atomicOr(&sRow[w][o], 1u << j);
+                }
+            }
+        }
+        // the other rows probe their ranges
         for (int i = 0; i < d - 1; ++i) {
+            if ((searching >> i) & 1u) continue;
             const int64_t b = __shfl_sync(kFull, myb, i), e = __shfl_sync(kFull, mye, i);
             uint32_t row = 0;
             probe_filtered(colsp, b, e, fc.use(),
@@ -327,10 +383,11 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
                            });
             row = __reduce_or_sync(kFull, row);
             fc.add(e - b, (uint32_t)__popc(row));  // each set bit is one hit
-            col += (row >> l) & 1u;
             if (l == i) sRow[w][i] = row;
         }
         __syncwarp();
+        uint32_t col = 0;  // # rows with bit l
+        for (int i = 0; i < d - 1; ++i) col += (sRow[w][i] >> l) & 1u;
         const uint32_t myrow = sRow[w][l];
         const uint32_t own = (l < d) ? (uint32_t)__popc(myrow) + col : 0u;
         if (own) atomicAdd(&te[ub + l], own);
@@ -474,18 +531,32 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
             }
             uint32_t* Ri = &s.R[i * WS];
             uint32_t hits = 0;
-            probe_filtered(colsp, b, e, fc.use(), [&](int32_t y) { return filter_may_hold<S::FB>(s.filt, y); },
-                           [&](int32_t y, int64_t p) {
-                               const int j = BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
-                               if (j >= 0) {
-                                   atomicAdd(&te[p], 1u);  // arc (L[i], y): top edge of triangle (u, L[i], y)
-                                   atomicOr(&Ri[j >> 5], 1u << (j & 31));
-                                   atomicAdd(&s.own[j], 1u);
-                                   ++hits;
-                               }
-                           });
-            hits = warp_sum(hits);
-            fc.add(e - b, hits);
+            if (row_searches(d - 1 - i, e - b)) {  // the keys after L[i] searched in the range
+                const int len = (int)(e - b);
+                for (int j = i + 1 + l; j < d; j += 32) {
+                    const int64_t p = find_in_range(colsp, b, len, s.L[j]);
+                    if (p >= 0) {
+                        atomicAdd(&te[p], 1u);  // arc (L[i], L[j]): top edge of triangle (u, L[i], L[j])
+                        atomicOr(&Ri[j >> 5], 1u << (j & 31));
+                        atomicAdd(&s.own[j], 1u);
+                        ++hits;
+                    }
+                }
+                hits = warp_sum(hits);
+            } else {
+                probe_filtered(colsp, b, e, fc.use(), [&](int32_t y) { return filter_may_hold<S::FB>(s.filt, y); },
+                               [&](int32_t y, int64_t p) {
+                                   const int j = BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
+                                   if (j >= 0) {
+                                       atomicAdd(&te[p], 1u);  // arc (L[i], y): top edge of triangle (u, L[i], y)
+                                       atomicOr(&Ri[j >> 5], 1u << (j & 31));
+                                       atomicAdd(&s.own[j], 1u);
+                                       ++hits;
+                                   }
+                               });
+                hits = warp_sum(hits);
+                fc.add(e - b, hits);
+            }
             if (l == 0 && hits) atomicAdd(&s.own[i], hits);
         }
         __syncthreads();
