@@ -38,9 +38,11 @@ namespace harp {
 namespace {
 
 constexpr int kCta1 = 256;
-// Resident blocks per SM of the 256 mode: 5 (48 registers a thread) measured 10 % faster than 4
-// (64 registers) on R-MAT scale 20; 6 spills.
-constexpr int kCta1Blocks = 5;
+// Block shape of the 256 mode: 192 threads, 7 resident blocks per SM (48 registers a thread).  On
+// R-MAT scale 20 it measured 5.49 ms against 5.77 ms for 256 x 5 and 6.09 ms for 128 x 9: an anchor's
+// rows spread over fewer warps wait less at its block barriers, and more blocks share each SM.
+constexpr int kCta1Threads = 192;
+constexpr int kCta1Blocks = 7;
 constexpr int kCta2 = 512;
 constexpr int kCtaMax = 1024;
 constexpr int kInf = 0x7fffffff;
@@ -894,8 +896,8 @@ harp_status launch_tiers(const harp_csr* g, Workspace& ws, int wmax, int cmax, i
     else k_tri_warp<false><<<wgrid, kWarpThreads, 0, s>>>(ws.offp, ws.colsp, ws.deg, ws.q_tri, qcnt, reuse, ws.te, sink);
     HARP_LAUNCHED();
     HARP_CK(prof_mark(s, SEG_TRI_WARP));
-    if (bs1) HARP_TRY((launch_cta<kCta1, 256, kCta1Blocks, true>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
-    else HARP_TRY((launch_cta<kCta1, 256, kCta1Blocks, false>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
+    if (bs1) HARP_TRY((launch_cta<kCta1, kCta1Threads, kCta1Blocks, true>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
+    else HARP_TRY((launch_cta<kCta1, kCta1Threads, kCta1Blocks, false>(g, ws, 1, T_TRI_S, wmax, cmax, bmax, reuse, s)));
     HARP_CK(prof_mark(s, SEG_TRI_CTA_S));
     if (bs2) HARP_TRY((launch_cta<kCta2, 256, 4, true>(g, ws, 2, T_TRI_M, wmax, cmax, bmax, reuse, s)));
     else HARP_TRY((launch_cta<kCta2, 256, 4, false>(g, ws, 2, T_TRI_M, wmax, cmax, bmax, reuse, s)));
