@@ -452,8 +452,16 @@ struct CtaSmem {
     int32_t L[DMAX];
     uint32_t own[DMAX];
     uint32_t R[DMAX * WS];
-    int32_t hk[1 << HB];
-    uint16_t hv[1 << HB];
+    // membership of y in L: a direct table indexed by y - L[0] when L's span fits (tab[y - L[0]] = index
+    // + 1, 0 = absent; 3 * 2^HB entries), else a hash of 2^HB slots in the same bytes
+    static constexpr int TAB = 3 << HB;
+    union {
+        struct {
+            int32_t hk[1 << HB];
+            uint16_t hv[1 << HB];
+        } h;
+        uint16_t tab[TAB];
+    } m;
     uint32_t filt[(1 << FB) / 32];
     // row i probes colsp[rb[i], re[i]): the elements of N+(L[i]) in [L[i+1], max L]
     int64_t rb[PRE ? DMAX : 1];
@@ -492,18 +500,30 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
         if (tri_class(d, wmax, cmax, bmax) != cls) continue;
         const int W = (d + 31) >> 5;
         const int WS = W | 1;
+        // the direct table where L's span fits (dense anchors: high ranks, close together), the hash else
+        const int32_t L0 = colsp[ub];
+        const uint32_t span = (uint32_t)(colsp[ub + d - 1] - L0) + 1u;
+        const bool direct = !BS && span <= (uint32_t)S::TAB;
         for (int i = threadIdx.x; i < d; i += THREADS) {
             s.L[i] = colsp[ub + i];
             s.own[i] = 0;
         }
         for (int i = threadIdx.x; i < d * WS; i += THREADS) s.R[i] = 0;
-        for (int i = threadIdx.x; i < (1 << S::HB); i += THREADS) s.hk[i] = kNoKey;
-        for (int i = threadIdx.x; i < (1 << S::FB) / 32; i += THREADS) s.filt[i] = 0;
+        if (direct) {
+            for (int i = threadIdx.x; i < (int)span; i += THREADS) s.m.tab[i] = 0;
+        } else {
+            for (int i = threadIdx.x; i < (1 << S::HB); i += THREADS) s.m.h.hk[i] = kNoKey;
+            for (int i = threadIdx.x; i < (1 << S::FB) / 32; i += THREADS) s.filt[i] = 0;
+        }
         __syncthreads();
         for (int i = threadIdx.x; i < d; i += THREADS) {
-            if (!BS) hash_put(s.hk, s.hv, S::HB, s.L[i], i);
-            const uint32_t h = hash32((uint32_t)s.L[i]) >> (32 - S::FB);
-            atomicOr(&s.filt[h >> 5], 1u << (h & 31));
+            if (direct) {
+                s.m.tab[s.L[i] - L0] = (uint16_t)(i + 1);
+            } else {
+                if (!BS) hash_put(s.m.h.hk, s.m.h.hv, S::HB, s.L[i], i);
+                const uint32_t h = hash32((uint32_t)s.L[i]) >> (32 - S::FB);
+                atomicOr(&s.filt[h >> 5], 1u << (h & 31));
+            }
             if (S::PRE && i < d - 1) {  // every row's probe range at once: dependent loads overlap across rows
                 const int32_t v = s.L[i];
                 const int64_t b = offp[v], e = offp[v + 1];
@@ -514,9 +534,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
         }
         __syncthreads();
         const int32_t last = s.L[d - 1];
+        // index of y in L, or -1
+        auto find = [&](int32_t y) {
+            if (direct) {
+                const uint32_t o = (uint32_t)(y - L0);
+                return o < span ? (int)s.m.tab[o] - 1 : -1;
+            }
+            return BS ? find_sorted(s.L, d, y) : hash_get(s.m.h.hk, s.m.h.hv, S::HB, y);
+        };
         auto lookup = [&](int32_t y) {
-            if (!filter_may_hold<S::FB>(s.filt, y)) return -1;
-            return BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
+            if (!direct && !filter_may_hold<S::FB>(s.filt, y)) return -1;
+            return find(y);
         };
         // rows: warp per row, ordered intersection of N+(L[i]) with L over the exact range of N+(L[i]) in
         // [L[i+1], max L] (no smaller element can be in L after L[i], no larger one at all)
@@ -546,9 +574,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
                 }
                 hits = warp_sum(hits);
             } else {
-                probe_filtered(colsp, b, e, fc.use(), [&](int32_t y) { return filter_may_hold<S::FB>(s.filt, y); },
+                // the filter is built and used only with the hash or the binary search
+                probe_filtered(colsp, b, e, !direct && fc.use(),
+                               [&](int32_t y) { return filter_may_hold<S::FB>(s.filt, y); },
                                [&](int32_t y, int64_t p) {
-                                   const int j = BS ? find_sorted(s.L, d, y) : hash_get(s.hk, s.hv, S::HB, y);
+                                   const int j = find(y);
                                    if (j >= 0) {
                                        atomicAdd(&te[p], 1u);  // arc (L[i], y): top edge of triangle (u, L[i], y)
                                        atomicOr(&Ri[j >> 5], 1u << (j & 31));
