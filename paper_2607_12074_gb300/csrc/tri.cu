@@ -446,8 +446,9 @@ struct CtaSmem {
     // filter: 64 bits per key (2, 4 and 8 KB); false positives at most d / 2^FB <= 1 / 64
     static constexpr int FB = HB + 4;
     // The 256 and 1024 modes resolve every row's exact probe range up front (one binary search per
-    // thread per bound); the 512 mode finds each row's range with the warp-wide search when the row
-    // is taken: the two range arrays would cost it a resident block per SM.
+    // thread per bound); the 512 mode does so only for direct-table anchors (in the filter's bytes,
+    // below) and otherwise finds each row's range with the warp-wide search when the row is taken:
+    // two more range arrays would cost it a resident block per SM.
     static constexpr bool PRE = DMAX <= 256 || DMAX >= 1024;
     int32_t L[DMAX];
     uint32_t own[DMAX];
@@ -462,7 +463,14 @@ struct CtaSmem {
         } h;
         uint16_t tab[TAB];
     } m;
-    uint32_t filt[(1 << FB) / 32];
+    // the filter (hash and binary-search anchors) or, for direct-table anchors of the 512 mode, every
+    // row's probe range as offsets into N+(L[i]): lo in rel[i], hi in rel[DMAX + i] (the same 8 * DMAX
+    // bytes)
+    union {
+        uint32_t filt[(1 << FB) / 32];
+        int32_t rel[2 * DMAX];
+    };
+    static_assert((1 << FB) / 32 == 2 * DMAX, "the filter and the relative ranges share their bytes");
     // row i probes colsp[rb[i], re[i]): the elements of N+(L[i]) in [L[i+1], max L]
     int64_t rb[PRE ? DMAX : 1];
     int64_t re[PRE ? DMAX : 1];
@@ -524,6 +532,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
                 const uint32_t h = hash32((uint32_t)s.L[i]) >> (32 - S::FB);
                 atomicOr(&s.filt[h >> 5], 1u << (h & 31));
             }
+            if (!S::PRE && direct && i < d - 1) {  // the same, as offsets into N+(L[i]) (rows are short)
+                const int32_t v = s.L[i];
+                const int64_t b = offp[v], e = offp[v + 1];
+                const int32_t lo = (int32_t)lower_bound_i32(colsp + b, e - b, s.L[i + 1]);
+                s.rel[i] = lo;
+                s.rel[DMAX + i] = lo + (int32_t)lower_bound_i32(colsp + b + lo, e - b - lo, s.L[d - 1] + 1);
+            }
             if (S::PRE && i < d - 1) {  // every row's probe range at once: dependent loads overlap across rows
                 const int32_t v = s.L[i];
                 const int64_t b = offp[v], e = offp[v + 1];
@@ -553,6 +568,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tri_cta(const int64_t* __rest
             if (S::PRE) {
                 b = s.rb[i];
                 e = s.re[i];
+            } else if (direct) {
+                const int64_t o = offp[s.L[i]];
+                b = o + s.rel[i];
+                e = o + s.rel[DMAX + i];
             } else {
                 const int32_t v = s.L[i];
                 const int64_t e0 = offp[v + 1];
