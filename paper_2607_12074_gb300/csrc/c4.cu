@@ -451,7 +451,7 @@ __device__ __forceinline__ uint32_t hash_add(int32_t* keys, uint32_t* cnt, uint3
 }
 
 // ---------------------------------------------------------------------------------------------
-// Classification: every root (warp per root, descending rank so heavy roots are queued first).
+// Classification: every root (a lane per root, descending rank so heavy roots are queued first).
 // ---------------------------------------------------------------------------------------------
 template <int WORDS>
 __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__ loff, const int32_t* __restrict__ lcols,
@@ -470,33 +470,61 @@ __global__ void __launch_bounds__(256) k_c4_classify(const int64_t* __restrict__
     unsigned long long* qcnt_small = (unsigned long long*)&acc[Q_C4_MID];
     unsigned long long* qcnt_mid = (unsigned long long*)&acc[Q_C4_MIDW];
     unsigned long long* qcnt_win = (unsigned long long*)&acc[Q_C4_WIN];
-    for (int64_t k = wid; k < n; k += nw) {  // descending rank: the heaviest roots are queued first
+    // a warp takes 32 ranks, one root per lane, spaced by the number of warps (so the hubs at the top
+    // ranks fall to different warps): a lane sums W(u) itself when u has at most 32 lower neighbours,
+    // the warp sums the larger roots together; queue slots are taken in lane order (descending rank).
+    // A warp per root left most lanes idle on the many small roots of a batch of small graphs.
+    for (int64_t k0 = wid; k0 < n; k0 += nw * 32) {
+        const int64_t k = k0 + (int64_t)l * nw;
         const int32_t u = (int32_t)(n - 1 - k);
-        if (u < own_lo || u >= own_hi) continue;  // the owner rule: only this range's roots
-        const int64_t dm = (int64_t)deg[u] - dplus[u];
-        if (dm < 2) continue;
-        const int64_t ub = loff[u];
+        int64_t dm = 0;
+        if (k < n && u >= own_lo && u < own_hi) dm = (int64_t)deg[u] - dplus[u];  // the owner rule
+        const int64_t ub = dm >= 2 ? loff[u] : 0;
         uint64_t W = 0;
-        for (int64_t a = l; a < dm; a += 32) {
-            const int32_t f = fpos[lcols[ub + a]];
-            const int32_t p = rev[ub + a];
-            W += p > f ? (uint64_t)(p - f) : 0;
+        if (dm >= 2 && dm <= 32) {
+            for (int64_t a = 0; a < dm; ++a) {
+                const int32_t f = fpos[lcols[ub + a]];
+                const int32_t p = rev[ub + a];
+                W += p > f ? (uint64_t)(p - f) : 0;
+            }
         }
-        W = warp_sum(W);
-        if (W > 0 && l == 0) {
-            if (W <= warp_max) {
-                const unsigned long long slot = atomicAdd(qcnt_small, 1ull);
-                q_small[slot] = u;
-                q_small[n + slot] = (int32_t)W;
-            } else if (W <= mid_max) {  // the middle tier fills the same queue from the back
-                const unsigned long long slot = atomicAdd(qcnt_mid, 1ull);
-                q_small[n - 1 - (int64_t)slot] = u;
-                q_small[2 * n - 1 - (int64_t)slot] = (int32_t)W;
-            } else {
-                const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
-                const unsigned long long slot = atomicAdd(qcnt_win, 1ull);
-                q_win[slot] = u;
-                wcount[slot] = (int32_t)windows_below<WORDS>(gi, u);
+        uint32_t big = __ballot_sync(kFull, dm > 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t bdm = __shfl_sync(kFull, dm, src), bub = __shfl_sync(kFull, ub, src);
+            uint64_t bw = 0;
+            for (int64_t a = l; a < bdm; a += 32) {
+                const int32_t f = fpos[lcols[bub + a]];
+                const int32_t p = rev[bub + a];
+                bw += p > f ? (uint64_t)(p - f) : 0;
+            }
+            bw = warp_sum(bw);
+            if (l == src) W = bw;
+        }
+        const int cls = W == 0 ? -1 : (W <= warp_max ? 0 : (W <= mid_max ? 1 : 2));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t mask = __ballot_sync(kFull, cls == c);
+            if (!mask) continue;
+            unsigned long long base = 0;
+            const int leader = __ffs(mask) - 1;
+            unsigned long long* ctr = c == 0 ? qcnt_small : (c == 1 ? qcnt_mid : qcnt_win);
+            if (l == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+            base = __shfl_sync(kFull, base, leader);
+            if (cls == c) {
+                const int64_t slot = (int64_t)(base + __popc(mask & lanemask_lt()));
+                if (c == 0) {
+                    q_small[slot] = u;
+                    q_small[n + slot] = (int32_t)W;
+                } else if (c == 1) {  // the middle tier fills the same queue from the back
+                    q_small[n - 1 - slot] = u;
+                    q_small[2 * n - 1 - slot] = (int32_t)W;
+                } else {
+                    const int64_t* gi = ginfo + (gid ? (int64_t)gid[u] : 0) * kGInfo;
+                    q_win[slot] = u;
+                    wcount[slot] = (int32_t)windows_below<WORDS>(gi, u);
+                }
             }
         }
     }
@@ -865,7 +893,7 @@ harp_status wedge_pass(const harp_csr* g, Workspace& ws, uint32_t warp_max, uint
     k_c4_bpos<WORDS><<<grid_cap(n * kGridCap, 256, (int64_t)sms * 64), 256, 0, s>>>(ws.off, ws.cols, ws.gid, ws.ginfo, n,
                                                                              ws.fpos, ws.bpos);
     HARP_LAUNCHED();
-    k_c4_classify<WORDS><<<grid_cap(n * 32, 256, (int64_t)sms * 32), 256, 0, s>>>(
+    k_c4_classify<WORDS><<<grid_cap(n, 256, (int64_t)sms * 32), 256, 0, s>>>(  // a lane per root
         loff, lcols, ws.deg, ws.dplus, ws.fpos, ws.rev, ws.gid, ws.ginfo, n, ws.own_lo, ws.own_hi, warp_max,
         mid_max, ws.q_mid, ws.q_win, wcount, ws.acc);
     HARP_LAUNCHED();

@@ -328,18 +328,27 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_tri_warp(const int64_t* __r
         auto lookup = [&](int32_t y) {
             return BS ? find_sorted(sL[w], d, y) : hash_get(sHk[w], sHv[w], kWarpHashBits, y);
         };
-        // every row's probe range at once, lane i for row i: N+(L[i]) from its first element >= L[i+1]
-        // (no smaller element can be in L); the lanes' dependent loads overlap
+        // every row at once, lane i for row i (the lanes' dependent loads overlap).  A row that searches
+        // (see row_searches, judged on the whole of N+(L[i])) looks its keys up in the whole list: a key
+        // found there is an edge wherever it lies, so the search needs no narrower range.  A row that
+        // probes needs its exact range [myb, mye): the elements of N+(L[i]) in [L[i+1], max L] (a
+        // smaller element could be a member of L before L[i+1])
         int64_t myb = 0, mye = 0;
-        if (l < d - 1) {  // [myb, mye): the elements of N+(L[l]) in [L[l+1], max L]
+        bool mysearch = false;
+        if (l < d - 1) {
             const int64_t b0 = offp[x], e0 = offp[x + 1];
-            myb = b0 + lower_bound_i32(colsp + b0, e0 - b0, sL[w][l + 1]);
-            mye = myb + lower_bound_i32(colsp + myb, e0 - myb, sL[w][d - 1] + 1);
+            mysearch = row_searches(d - 1 - l, e0 - b0);
+            if (mysearch) {
+                myb = b0;
+                mye = e0;
+            } else {
+                myb = b0 + lower_bound_i32(colsp + b0, e0 - b0, sL[w][l + 1]);
+                mye = myb + lower_bound_i32(colsp + myb, e0 - myb, sL[w][d - 1] + 1);
+            }
         }
-        // rows that search (see row_searches): their (row, key) pairs are flattened over the lanes, so
-        // one round of binary searches covers several short rows; pair t belongs to the last row whose
-        // first pair is at or before t
-        const bool mysearch = l < d - 1 && row_searches(d - 1 - l, mye - myb);
+        // the searching rows' (row, key) pairs are flattened over the lanes, so one round of binary
+        // searches covers several short rows; pair t belongs to the last row whose first pair is at or
+        // before t
         const uint32_t searching = __ballot_sync(kFull, mysearch);
         const int npairs = mysearch ? d - 1 - l : 0;
         int incl = npairs;
