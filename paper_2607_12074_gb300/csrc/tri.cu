@@ -14,16 +14,18 @@
 //                  per set bit (global atomic at the position where the intersection found it)
 //   * 4-cliques:   K4_u = sum over set bits (i, j) of popc(row_i & row_j)   (the X_3 extension)
 //   * paw sums:    sum over triangles of (d_a + d_b + d_c)
-// The intersection walks N+(L[i]) from L[i+1] (found by a warp-parallel 32-ary search when the list
-// is long) up to the largest element of L, and looks each element up in L (its index j).
+// The intersection either probes the exact range of N+(L[i]) in [L[i+1], max L] (16-byte loads, a
+// membership filter while hits are rare, then the index j of each element in L), or, where few keys
+// of L remain after L[i], searches each of those keys in N+(L[i]) (row_searches).
 // Warp-local mode: d <= tri_warp_max (<= 32), rows are single words, one warp per anchor.
 // CTA mode: up to tri_cta_max (<= 1024) in three sizes (256 / 512 / 1024), rows in shared memory, one
-// block per anchor.  Global-staged mode (up to tri_big_max <= 4096, hubs of very large skewed
+// block per anchor; the 4-clique sum is dealt to the block as (word, row) units of the bitmap.  Global-staged mode (up to tri_big_max <= 4096, hubs of very large skewed
 // graphs): the same rows in a per-block scratch that stays in L2 (d^2 / 8 bytes), each row built in
 // a per-warp shared buffer and written out once.  Fallback (larger d): per out-arc ordered
 // intersections through global memory with binary-searched membership; 4-cliques by binary search
 // in N+(w).  Membership of y in L is a hash lookup (HARP_PROBE_HASH) or a binary search of the
-// sorted L in shared memory (HARP_PROBE_BSEARCH).
+// sorted L in shared memory (HARP_PROBE_BSEARCH); with the hash, a CTA anchor whose L spans few ranks
+// uses a direct table indexed by y - L[0] in the hash's bytes instead.
 //
 // Signature reuse (Section III-C): the extension of (u, v, w) to a 4-clique needs
 // |N+(w) n S_uv|, and since S_uv is a subset of L this is popc(row_v & row_w): the staged frontier of
