@@ -100,7 +100,52 @@ __global__ void k_relabel(const uint64_t* __restrict__ keys, int64_t n, int b, i
     }
 }
 
-// Tier A: rows with 1 <= d <= 32, one warp per row, bitonic network in registers.
+// Tier A: rows with 1 <= d <= 32, 32 consecutive rows per warp (consecutive ranks have similar
+// degrees).  A row of at most 16 neighbours is sorted by its own lane, a bitonic network over 8 or 16
+// registers padded with +inf; the warp then sorts its rows of 17..32 together, a bitonic network over
+// the lanes.  A warp per row left most lanes idle on the many short rows of sparse graphs.
+template <int P>
+__device__ __forceinline__ void sort_regs(int32_t (&a)[P]) {
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const int32_t lo = min(a[i], a[p]), hi = max(a[i], a[p]);
+                    const bool up = (i & k) == 0;
+                    a[i] = up ? lo : hi;
+                    a[p] = up ? hi : lo;
+                }
+            }
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void lane_sort_row(int64_t i, int d, const int64_t* __restrict__ goff,
+                                              const int32_t* __restrict__ gcols, const int32_t* __restrict__ order,
+                                              const int32_t* __restrict__ perm, const int64_t* __restrict__ off,
+                                              int32_t* __restrict__ cols, int32_t* __restrict__ dplus) {
+    const int64_t src = goff[order[i]];
+    int32_t a[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) a[r] = r < d ? perm[gcols[src + r]] : 0x7fffffff;
+    sort_regs<P>(a);
+    const int64_t ob = off[i];
+    int above = 0;
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        if (r < d) {
+            cols[ob + r] = a[r];
+            above += a[r] > (int32_t)i;
+        }
+    }
+    dplus[i] = above;
+}
+
 __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restrict__ goff,
                                                         const int32_t* __restrict__ gcols,
                                                         const int32_t* __restrict__ order,
@@ -112,28 +157,34 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(const int64_t* __restric
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = wid; i < n; i += nw) {
-        const int d = deg[i];
-        if (d > kTierA) continue;  // CTA and hub rows are sorted by the queued kernels
-        if (d == 0) {
-            if (l == 0) dplus[i] = 0;
-            continue;
-        }
-        const int64_t src = goff[order[i]];
-        int32_t v = (l < d) ? perm[gcols[src + l]] : 0x7fffffff;
+    for (int64_t i0 = wid * 32; i0 < n; i0 += nw * 32) {
+        const int64_t i = i0 + l;
+        const int d = i < n ? deg[i] : -1;  // CTA and hub rows (d > 32) are sorted by the queued kernels
+        if (d == 0) dplus[i] = 0;
+        else if (d >= 1 && d <= 8) lane_sort_row<8>(i, d, goff, gcols, order, perm, off, cols, dplus);
+        else if (d > 8 && d <= 16) lane_sort_row<16>(i, d, goff, gcols, order, perm, off, cols, dplus);
+        uint32_t rest = __ballot_sync(kFull, d > 16 && d <= kTierA);
+        while (rest) {
+            const int src = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int64_t r = i0 + src;
+            const int dr = __shfl_sync(kFull, d, src);
+            const int64_t rsrc = goff[order[r]];
+            int32_t v = (l < dr) ? perm[gcols[rsrc + l]] : 0x7fffffff;
 #pragma unroll
-        for (int k = 2; k <= 32; k <<= 1) {
+            for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                int32_t o = __shfl_xor_sync(kFull, v, j);
-                bool up = (l & k) == 0;
-                bool lower = (l & j) == 0;
-                v = (lower == up) ? min(v, o) : max(v, o);
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    int32_t o = __shfl_xor_sync(kFull, v, j);
+                    bool up = (l & k) == 0;
+                    bool lower = (l & j) == 0;
+                    v = (lower == up) ? min(v, o) : max(v, o);
+                }
             }
+            if (l < dr) cols[off[r] + l] = v;
+            uint32_t above = __ballot_sync(kFull, l < dr && v > (int32_t)r);
+            if (l == 0) dplus[r] = __popc(above);
         }
-        if (l < d) cols[off[i] + l] = v;
-        uint32_t above = __ballot_sync(kFull, l < d && v > (int32_t)i);
-        if (l == 0) dplus[i] = __popc(above);
     }
 }
 
@@ -342,8 +393,10 @@ __global__ void __launch_bounds__(kHubThreads) k_sort_rows_hub(const int64_t* __
     }
 }
 
-// colsp[offp[i] + k] = the k-th neighbour of i ranked above i (the row suffix), one warp per row.
-// The same pass accumulates sum over edges of (d_u - 1)(d_v - 1) (3-edge paths + 3T).
+// colsp[offp[i] + k] = the k-th neighbour of i ranked above i (the row suffix), 32 consecutive rows
+// per warp: a lane copies its own row when the suffix has at most 32 entries, the warp copies the
+// longer ones together.  The same pass accumulates sum over edges of (d_u - 1)(d_v - 1) (3-edge paths
+// + 3T).
 __global__ void __launch_bounds__(256) k_out_csr(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                                                  const int32_t* __restrict__ dplus,
                                                  const int32_t* __restrict__ deg,
@@ -354,23 +407,43 @@ __global__ void __launch_bounds__(256) k_out_csr(const int64_t* __restrict__ off
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint64_t pw = 0;
-    for (int64_t i = wid; i < n; i += nw) {
-        const int64_t dp = dplus[i];
-        if (dp == 0) continue;
-        const int64_t srcb = off[i + 1] - dp;
-        const int64_t dstb = offp[i];
-        const uint64_t di1 = (uint64_t)deg[i] - 1;
-        uint64_t row_pw = 0;
-        for (int64_t k = l; k < dp; k += 32) {
-            const int32_t v = cols[srcb + k];
-            colsp[dstb + k] = v;
-            row_pw += di1 * ((uint64_t)deg[v] - 1);
+    for (int64_t i0 = wid * 32; i0 < n; i0 += nw * 32) {
+        const int64_t i = i0 + l;
+        const int64_t dp = i < n ? dplus[i] : 0;
+        if (dp > 0 && dp <= 32) {
+            const int64_t srcb = off[i + 1] - dp;
+            const int64_t dstb = offp[i];
+            const uint64_t di1 = (uint64_t)deg[i] - 1;
+            uint64_t row_pw = 0;
+            for (int64_t k = 0; k < dp; ++k) {
+                const int32_t v = cols[srcb + k];
+                colsp[dstb + k] = v;
+                row_pw += di1 * ((uint64_t)deg[v] - 1);
+            }
+            if (sink.batch()) sink_add(sink, (int32_t)i, G_PW, row_pw);
+            else pw += row_pw;
         }
-        if (sink.batch()) {
-            row_pw = warp_sum(row_pw);
-            if (l == 0) sink_add(sink, (int32_t)i, G_PW, row_pw);
-        } else {
-            pw += row_pw;
+        uint32_t rest = __ballot_sync(kFull, dp > 32);
+        while (rest) {
+            const int src = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int64_t r = i0 + src;
+            const int64_t rdp = __shfl_sync(kFull, dp, src);
+            const int64_t srcb = off[r + 1] - rdp;
+            const int64_t dstb = offp[r];
+            const uint64_t di1 = (uint64_t)deg[r] - 1;
+            uint64_t row_pw = 0;
+            for (int64_t k = l; k < rdp; k += 32) {
+                const int32_t v = cols[srcb + k];
+                colsp[dstb + k] = v;
+                row_pw += di1 * ((uint64_t)deg[v] - 1);
+            }
+            if (sink.batch()) {
+                row_pw = warp_sum(row_pw);
+                if (l == 0) sink_add(sink, (int32_t)r, G_PW, row_pw);
+            } else {
+                pw += row_pw;
+            }
         }
     }
     pw = block_sum_u64(pw, red);
@@ -402,7 +475,8 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     HARP_LAUNCHED();
     HARP_TRY(exclusive_scan_i32_to_i64(ws.deg, ws.off, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {
-        k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
+        // 32 rows per warp
+        k_sort_rows_warp<<<grid_for(n, 256), 256, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
                                                                 ws.off, n, ws.cols, ws.dplus);
         HARP_LAUNCHED();
         k_sort_rows_mid<<<num_sms() * 8, kMidWarps * 32, 0, s>>>(g->off, g->cols, ws.order, ws.perm, ws.deg,
@@ -421,7 +495,8 @@ harp_status orient(const harp_csr* g, Workspace& ws, cudaStream_t s) {
     HARP_TRY(exclusive_scan_i32_to_i64(ws.dplus, ws.offp, n, ws.scan_tmp, ws.scan_tmp_len, s));
     if (m > 0) {
         const Sink sink{ws.acc, ws.gid, ws.accG};
-        k_out_csr<<<grid_for(n * 32, 256), 256, 0, s>>>(ws.off, ws.cols, ws.dplus, ws.deg, ws.offp, n, ws.colsp,
+        // 32 rows per warp
+        k_out_csr<<<grid_for(n, 256), 256, 0, s>>>(ws.off, ws.cols, ws.dplus, ws.deg, ws.offp, n, ws.colsp,
                                                          sink);
         HARP_LAUNCHED();
         HARP_CK(cudaMemsetAsync(ws.te, 0, (size_t)m * sizeof(uint32_t), s));
