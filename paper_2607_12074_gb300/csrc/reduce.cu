@@ -62,19 +62,47 @@ __global__ void __launch_bounds__(256) k_reduce_close(const uint32_t* __restrict
     acc[OUT_STATS + HARP_STAT_EDGES] = (uint64_t)m;
 }
 
-// Batch mode: sum_e C(t_e, 2) per graph (warp per row of the out-CSR; gid[u] is the row's graph).
+// Batch mode: sum_e C(t_e, 2) per graph over the out-CSR rows, 32 consecutive rows per warp.  A lane
+// sums its own row when it has at most 32 out-arcs, the warp sums the longer rows together; then one
+// atomic per graph present among the warp's rows (ranks are ordered by graph first, so consecutive
+// rows almost always share one) instead of one per row.
 __global__ void __launch_bounds__(256) k_reduce_rows_batch(const int64_t* __restrict__ offp,
                                                            const uint32_t* __restrict__ te, int64_t n, Sink sink) {
     const int l = lane_id();
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = wid; u < n; u += nw) {
-        const int64_t b = offp[u], e = offp[u + 1];
-        if (b == e) continue;
+    for (int64_t u0 = wid * 32; u0 < n; u0 += nw * 32) {
+        const int64_t u = u0 + l;
+        int64_t b = 0, e = 0;
+        int32_t g = -1;
         uint64_t d = 0;
-        for (int64_t a = b + l; a < e; a += 32) d += choose2_u64((uint64_t)te[a]);
-        d = warp_sum(d);
-        if (l == 0) sink_add(sink, (int32_t)u, G_D, d);
+        if (u < n) {
+            b = offp[u];
+            e = offp[u + 1];
+            g = sink.gid[u];
+            if (e - b <= 32)
+                for (int64_t a = b; a < e; ++a) d += choose2_u64((uint64_t)te[a]);
+        }
+        uint32_t big = __ballot_sync(kFull, e - b > 32);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t rb = __shfl_sync(kFull, b, src), re = __shfl_sync(kFull, e, src);
+            uint64_t rd = 0;
+            for (int64_t a = rb + l; a < re; a += 32) rd += choose2_u64((uint64_t)te[a]);
+            rd = warp_sum(rd);
+            if (l == src) d = rd;
+        }
+        uint32_t left = __ballot_sync(kFull, d != 0);
+        while (left) {  // one graph per round: the first lane still holding a sum names it
+            const int src = __ffs(left) - 1;
+            const int32_t gs = __shfl_sync(kFull, g, src);
+            const bool mine = ((left >> l) & 1u) && g == gs;
+            const uint64_t sum = warp_sum(mine ? d : (uint64_t)0);
+            if (l == src)
+                atomicAdd((unsigned long long*)&sink.accG[(int64_t)gs * kGStride + G_D], (unsigned long long)sum);
+            left &= ~__ballot_sync(kFull, mine);
+        }
     }
 }
 
@@ -115,7 +143,7 @@ __global__ void k_close_batch(const uint64_t* __restrict__ accG, int64_t G, uint
 
 harp_status reduce_and_close_batch(const harp_csr* g, Workspace& ws, int64_t G, uint64_t* d_out, cudaStream_t s) {
     const Sink sink{ws.acc, ws.gid, ws.accG};
-    int64_t blocks = (g->n * 32 + 255) / 256;
+    int64_t blocks = (g->n + 255) / 256;  // a lane per row
     if (blocks < 1) blocks = 1;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (g->m > 0) {
