@@ -117,6 +117,8 @@ harp_status harp_csr_arrays(const harp_csr* g, const int64_t** offsets, const in
  * Single graphs only (harp_count4, harp_count4_stats, harp_count4_async). */
 #define HARP_BASIS_LITERAL 1u
 
+/* Frontier membership probes.  With HARP_PROBE_HASH a CTA-mode anchor whose N+(u) spans few ranks
+ * uses a direct table indexed by the rank offset from min N+(u) instead of the hash (exact either way). */
 #define HARP_PROBE_HASH 1u     /* frontier membership by a shared-memory hash of N+(u)             */
 #define HARP_PROBE_BSEARCH 2u  /* frontier membership by binary search in the sorted N+(u)         */
 
