@@ -9,10 +9,11 @@
 // Output (workspace): deg, order (new -> old), perm (old -> new), off/cols (relabelled CSR with
 // every row sorted), dplus, offp/colsp (out-CSR: only N+), te zeroed, S = sum_v C(d_v, 3).
 //
-// Rows are sorted by four kernels chosen by degree: a warp bitonic network in registers for d <= 32
-// (every row is visited), a warp bitonic sort in the warp's shared buffer for d <= 256, a block
-// bitonic sort in shared memory for d <= 4096 and a per-row LSD radix sort through global memory for
-// hubs (the last three from queues filled by the relabel pass; the warp and block sorts share one).
+// Rows are sorted by four kernels chosen by degree: for d <= 32 a lane's bitonic network in registers
+// (d <= 16) or the warp's over its lanes (every row is visited), a warp bitonic sort in the warp's
+// shared buffer for d <= 256, a block bitonic sort in shared memory for d <= 4096 and a per-row LSD
+// radix sort through global memory for hubs (the last three from queues filled by the relabel pass;
+// the warp and block sorts share one).
 #include "harp_internal.cuh"
 
 namespace harp {
